@@ -1,0 +1,249 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle tests and the benchmark.
+
+This module draws random numbers and evaluates the closed-form boundary data of the
+synthetic workloads. It holds none of the Mosaic Flow arithmetic (no gather, no SDNet,
+no scatter, no convergence test), so both the CUDA path and the CPU oracle can take
+their inputs from it without sharing any of the method.
+
+Random numbers come from SplitMix64 (Steele, Lea and Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014), used as a counter-based generator:
+draw k of a stream with initial state s is mix(s + k * GAMMA). Uniform doubles take the
+top 53 bits; normals use the Box-Muller transform (cosine branch only).
+
+Workload presets mirror the five synthetic configurations of the sweep engine
+(tiny / mid / large single problems, a batch of problems, and the training batch). The
+paper (Section 5.1) builds its boundary data from Gaussian-process samples solved by
+pyAMG; that data is not available, so closed-form harmonic boundary data with the
+paper's domain shapes stand in for it.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+# Stream tags: one independent SplitMix64 stream per purpose and seed.
+TAG_WEIGHTS = 1
+TAG_BC = 2
+TAG_COLLOCATION = 3
+TAG_SIDES = 4
+TAG_TEST = 5
+
+POINTS_PER_UNIT = 32  # grid intervals per unit length (33 points per unit subdomain side)
+
+
+def _mix(z: np.ndarray) -> np.ndarray:
+    z = z.astype(np.uint64, copy=True)
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+    return z ^ (z >> np.uint64(31))
+
+
+def splitmix64(state: int, n: int, offset: int = 0) -> np.ndarray:
+    """Draws offset+1 .. offset+n of the SplitMix64 stream that starts at `state`."""
+    k = np.arange(offset + 1, offset + n + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(state & 0xFFFFFFFFFFFFFFFF) + k * GAMMA
+    return _mix(z)
+
+
+def stream_state(seed: int, tag: int) -> int:
+    return (int(seed) + (int(tag) << 32)) & 0xFFFFFFFFFFFFFFFF
+
+
+class Stream:
+    """Sequential reader over one SplitMix64 stream."""
+
+    def __init__(self, seed: int, tag: int):
+        self.state = stream_state(seed, tag)
+        self.pos = 0
+
+    def u64(self, n: int) -> np.ndarray:
+        out = splitmix64(self.state, n, self.pos)
+        self.pos += n
+        return out
+
+    def uniform(self, n: int) -> np.ndarray:
+        """n doubles in [0, 1) from the top 53 bits of each draw."""
+        return (self.u64(n) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+    def normal(self, n: int) -> np.ndarray:
+        """n standard normals, Box-Muller, two uniforms per normal."""
+        u = self.uniform(2 * n).reshape(n, 2)
+        r = np.sqrt(-2.0 * np.log1p(-u[:, 0]))
+        return r * np.cos(2.0 * math.pi * u[:, 1])
+
+    def integers(self, n: int, k: int) -> np.ndarray:
+        """n integers uniform in [0, k) (floor of k * uniform)."""
+        return np.minimum((self.uniform(n) * k).astype(np.int64), k - 1)
+
+
+# ---------------------------------------------------------------------------
+# SDNet weights: packed FP32 layout shared by the library and the tests.
+#   W0[H][130] (columns 0..127 boundary block, 128..129 coordinate block), b0[H],
+#   then for each of the depth-1 hidden-to-hidden layers: W[H][H], b[H],
+#   then w_out[H], b_out[1].
+# ---------------------------------------------------------------------------
+N_BDRY = 128
+N_COORD = 2
+
+
+@dataclass
+class SDNetShape:
+    width: int = 128  # H
+    depth: int = 6    # number of tanh layers (first layer + depth-1 hidden layers)
+
+    @property
+    def n_params(self) -> int:
+        h = self.width
+        return h * (N_BDRY + N_COORD) + h + (self.depth - 1) * (h * h + h) + h + 1
+
+
+def xavier_sdnet(shape: SDNetShape, seed: int, bias_scale: float = 0.0) -> np.ndarray:
+    """Xavier-uniform weights U(+-sqrt(6/(fan_in+fan_out))), drawn in packed order.
+
+    Biases are zero unless bias_scale > 0 (then U(+-bias_scale), used by tests to
+    exercise the bias paths). Values are rounded to FP32; the FP32 array is canonical.
+    """
+    h, d = shape.width, shape.depth
+    st = Stream(seed, TAG_WEIGHTS)
+    parts = []
+
+    def mat(rows, cols):
+        bound = math.sqrt(6.0 / (rows + cols))
+        return (2.0 * st.uniform(rows * cols) - 1.0) * bound
+
+    def bias(n):
+        if bias_scale > 0:
+            return (2.0 * st.uniform(n) - 1.0) * bias_scale
+        return np.zeros(n)
+
+    parts.append(mat(h, N_BDRY + N_COORD))
+    parts.append(bias(h))
+    for _ in range(d - 1):
+        parts.append(mat(h, h))
+        parts.append(bias(h))
+    parts.append(mat(1, h))
+    parts.append(bias(1))
+    w = np.concatenate(parts).astype(np.float32)
+    assert w.size == shape.n_params
+    return w
+
+
+# ---------------------------------------------------------------------------
+# Boundary data (Dirichlet values on the global boundary), counter-clockwise from
+# the corner (0, 0): bottom edge ix = 0..nx-2 (iy = 0), right edge iy = 0..ny-2
+# (ix = nx-1), top edge ix = nx-1..1 (iy = ny-1), left edge iy = ny-1..1 (ix = 0).
+# ---------------------------------------------------------------------------
+
+def boundary_points(nx: int, ny: int) -> np.ndarray:
+    """(ix, iy) of the global boundary points in counter-clockwise order."""
+    pts = []
+    pts += [(ix, 0) for ix in range(0, nx - 1)]
+    pts += [(nx - 1, iy) for iy in range(0, ny - 1)]
+    pts += [(ix, ny - 1) for ix in range(nx - 1, 0, -1)]
+    pts += [(0, iy) for iy in range(ny - 1, 0, -1)]
+    return np.array(pts, dtype=np.int64)
+
+
+def mode_field(coeffs, lx: float, ly: float):
+    """u(x,y) = sum_k a_k sin(k pi x/lx) sinh(k pi y/lx) / sinh(k pi ly/lx), harmonic.
+
+    The sinh ratio is evaluated as exp(kpi(y-ly)/lx)(1-exp(-2kpi y/lx))/(1-exp(-2kpi ly/lx))
+    so that large k*ly/lx does not overflow.
+    """
+    coeffs = np.asarray(coeffs, dtype=np.float64)
+
+    def f(x, y):
+        x = np.asarray(x, dtype=np.float64)
+        y = np.asarray(y, dtype=np.float64)
+        out = np.zeros(np.broadcast(x, y).shape)
+        for k, a in enumerate(coeffs, start=1):
+            kp = k * math.pi / lx
+            ratio = np.exp(kp * (y - ly)) * (-np.expm1(-2.0 * kp * y)) / (-math.expm1(-2.0 * kp * ly))
+            out = out + a * np.sin(kp * x) * ratio
+        return out
+
+    return f
+
+
+def bc_values(lx: int, ly: int, field_fn) -> np.ndarray:
+    """FP64 boundary values of field_fn on the (32lx+1) x (32ly+1) grid, CCW order."""
+    nx, ny = POINTS_PER_UNIT * lx + 1, POINTS_PER_UNIT * ly + 1
+    pts = boundary_points(nx, ny)
+    h = 1.0 / POINTS_PER_UNIT
+    return np.asarray(field_fn(pts[:, 0] * h, pts[:, 1] * h), dtype=np.float64)
+
+
+def mode_coeffs(seed: int, n_modes: int = 8) -> np.ndarray:
+    return Stream(seed, TAG_BC).normal(n_modes)
+
+
+# ---------------------------------------------------------------------------
+# Workload presets.
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Problem:
+    lx: int
+    ly: int
+    bc: np.ndarray  # FP64 CCW boundary values
+    name: str = ""
+
+
+@dataclass
+class Workload:
+    name: str
+    problems: list
+    shape: SDNetShape
+    weight_seed: int
+    sweeps: int
+    eps: float
+    precision: str  # "fp32" or "bf16"
+    extra: dict = field(default_factory=dict)
+
+    def weights(self, bias_scale: float = 0.0) -> np.ndarray:
+        return xavier_sdnet(self.shape, self.weight_seed, bias_scale)
+
+
+def tiny() -> Workload:
+    """Global [0,2]^2, 3x3 unit subdomains at half overlap, grid 65x65, SDNet 4x64,
+    BC sin(pi x) sinh(pi y) / sinh(2 pi), 20 sweeps, FP32."""
+    f = lambda x, y: np.sin(math.pi * x) * np.sinh(math.pi * y) / math.sinh(2 * math.pi)
+    p = Problem(2, 2, bc_values(2, 2, f), "tiny")
+    return Workload("tiny_L2_fp32", [p], SDNetShape(64, 4), 0, 20, 0.0, "fp32")
+
+
+def mid() -> Workload:
+    """Global [0,16]^2, 31x31 subdomains, grid 513x513, SDNet 6x128 seed 1,
+    8-mode harmonic BC a_k ~ N(0,1) seed 1, up to 200 sweeps, stop at 1e-6."""
+    p = Problem(16, 16, bc_values(16, 16, mode_field(mode_coeffs(1), 16, 16)), "mid")
+    return Workload("mid_L16_fp32", [p], SDNetShape(128, 6), 1, 200, 1e-6, "fp32")
+
+
+def large() -> Workload:
+    """Global [0,64]^2 (4096x the unit subdomain area), 127x127 = 16129 subdomains,
+    grid 2049x2049, SDNet 6x128 seed 2, 8-mode harmonic BC seed 2, BF16 with FP32
+    refinement."""
+    p = Problem(64, 64, bc_values(64, 64, mode_field(mode_coeffs(2), 64, 64)), "large")
+    return Workload("large_L64_bf16", [p], SDNetShape(128, 6), 2, 200, 1e-6, "bf16")
+
+
+def batched(n_problems: int = 256) -> Workload:
+    """n independent square problems, sides uniform in {2,4,8,16,32} (seed 4),
+    problem q with 8-mode BC seed 1000+q; shared SDNet 6x128 (seed 4)."""
+    sides = np.array([2, 4, 8, 16, 32])[Stream(4, TAG_SIDES).integers(n_problems, 5)]
+    probs = []
+    for q, s in enumerate(sides):
+        s = int(s)
+        probs.append(Problem(s, s, bc_values(s, s, mode_field(mode_coeffs(1000 + q), s, s)), f"q{q}"))
+    return Workload("batched_256", probs, SDNetShape(128, 6), 4, 200, 1e-6, "bf16")
+
+
+WORKLOADS = {"tiny": tiny, "mid": mid, "large": large, "batched": batched}
