@@ -1,0 +1,151 @@
+/*
+ * mosaicflow.h -- C ABI of the GB300 Mosaic Flow sweep engine.
+ *
+ * Mosaic Flow (Feeney, Li, Bostanabad, Chandramowlishwaran, SC '23) solves the 2-D
+ * Laplace equation with Dirichlet data (Section 2.1, Eq. 2) on a large domain by
+ * iterating a pre-trained subdomain network (SDNet, Section 2.4 and Section 3) over
+ * overlapping unit subdomains (Section 2.4, Figure 3), batching the non-overlapping
+ * ("atomic") subdomains of one iteration (Section 4.1) and stopping on the relative
+ * change of the boundary values (Algorithm 2).
+ *
+ * Conventions shared by every call:
+ *  - Domain [0, lx] x [0, ly] in units of the subdomain side; 32 grid intervals per
+ *    unit, so the grid has nx = 32 lx + 1 columns and ny = 32 ly + 1 rows, stored
+ *    row-major as FP32, element (iy, ix) at offset iy * nx + ix, x = ix / 32.
+ *  - Subdomain (a, b), a in [0, 2lx-2], b in [0, 2ly-2], covers grid points
+ *    [16a, 16a+32] x [16b, 16b+32] (lattice spacing 1/2, Section 4.2). Its 128
+ *    boundary values are read counter-clockwise from its corner (16a, 16b): bottom
+ *    (i = 0..31), right (j = 0..31), top (i = 32..1), left (j = 32..1). Its 961
+ *    interior points p = py * 31 + px have local coordinates ((px+1)/32, (py+1)/32).
+ *  - Colour c = (a mod 2) + 2 (b mod 2); subdomains of one colour have disjoint
+ *    interiors and are predicted as one batch.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *    Calls enqueue their GPU work on it and return; calls that hand a host scalar
+ *    back synchronise that stream first, as stated per call.
+ *  - Every call returns an mf_status; nothing throws across the ABI. A call that
+ *    fails validation returns MF_ERR_INVALID_ARG before any GPU work is enqueued.
+ *    mf_last_error() gives a message for the calling thread's last failure.
+ *  - The library owns the device memory behind handles; the caller owns host
+ *    buffers and streams. There is no CPU fallback: without a usable CUDA device
+ *    every call that needs one returns MF_ERR_CUDA.
+ */
+#ifndef MOSAICFLOW_H
+#define MOSAICFLOW_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int mf_status;
+#define MF_OK 0
+#define MF_ERR_INVALID_ARG (-1)  /* bad pointer, size, shape or option */
+#define MF_ERR_CUDA (-2)         /* a CUDA runtime call failed (message has the CUDA error) */
+#define MF_ERR_OUT_OF_MEMORY (-3)
+#define MF_ERR_DIVERGED (-4)     /* delta became NaN or infinite */
+#define MF_ERR_TIMEOUT (-5)      /* a bounded wait inside a kernel gave up; results invalid */
+#define MF_ERR_UNSUPPORTED (-6)  /* valid request this build or device cannot serve */
+
+#define MF_PREC_FP32 0  /* FP32 weights and activations, SIMT FMA, accurate tanh */
+#define MF_PREC_BF16 1  /* BF16 weights/activations on tcgen05 tensor cores, FP32 accumulate */
+
+#define MF_SCHEDULE_MULTIPLICATIVE 0 /* colours 0..3 in turn, each reads the latest grid */
+#define MF_SCHEDULE_ADDITIVE 1       /* all colours read the old grid; overlaps averaged */
+
+typedef struct mf_sdnet mf_sdnet; /* device-resident SDNet weights (both precisions) */
+typedef struct mf_grid mf_grid;   /* device grid of one problem plus its sweep scratch */
+
+typedef struct {
+  int width; /* hidden width H: 64 or 128 */
+  int depth; /* number of tanh layers (first layer + depth-1 hidden H x H layers), 2..6 */
+} mf_sdnet_desc;
+
+typedef struct {
+  int lx; /* domain width in unit subdomain lengths, 1..128 */
+  int ly; /* domain height, 1..128 */
+} mf_grid_desc;
+
+typedef struct {
+  int n_sweeps;    /* maximum number of sweeps, >= 0 */
+  int schedule;    /* MF_SCHEDULE_* */
+  int precision;   /* MF_PREC_* */
+  int colours;     /* bitmask of colours applied each sweep, in order 0..3; 0 means all */
+  double eps;      /* stop once delta < eps (eps <= 0: run all n_sweeps, no mid-run sync) */
+  int check_every; /* delta computed after every check_every-th sweep and the last (>= 1) */
+} mf_sweep_opts;
+
+typedef struct {
+  int sweeps_done; /* sweeps applied */
+  double delta;    /* delta of the last checked sweep (Algorithm 2), -1 if none checked */
+} mf_sweep_result;
+
+/* Message describing the calling thread's most recent failed call ("" if none). */
+const char* mf_last_error(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int mf_version(void);
+
+/* mf_load_sdnet -- copy an SDNet to the current device (Section 3.1-3.2).
+ * `weights` is a host array of FP32 values packed as
+ *   W0[H][130], b0[H], { W_l[H][H], b_l[H] } for l = 1..depth-1, w_out[H], b_out
+ * where columns 0..127 of W0 are the boundary block W1 and columns 128..129 the
+ * coordinate block W2 of the input-split first layer (Eq. 7-8); rows are output
+ * units. The array is read during the call and not retained. The handle keeps an
+ * FP32 copy and a BF16 (round-to-nearest-even) copy laid out for the tensor cores.
+ * Errors: MF_ERR_INVALID_ARG for a null pointer or unsupported width/depth,
+ * MF_ERR_OUT_OF_MEMORY / MF_ERR_CUDA from the device. Synchronous. */
+mf_status mf_load_sdnet(const mf_sdnet_desc* desc, const float* weights, mf_sdnet** out);
+mf_status mf_free_sdnet(mf_sdnet* net);
+
+/* mf_create_grid -- allocate the global grid of one Laplace problem (Eq. 2) on the
+ * current device and set it up: boundary from `bc_ccw`, interior zero.
+ * `bc_ccw` is a host array of 2(nx-1) + 2(ny-1) FP64 Dirichlet values in
+ * counter-clockwise order from (0,0): bottom ix = 0..nx-2, right iy = 0..ny-2,
+ * top ix = nx-1..1, left iy = ny-1..1. Values are rounded to FP32. Synchronous.
+ * Errors: MF_ERR_INVALID_ARG (null pointer, lx or ly outside 1..128),
+ * MF_ERR_OUT_OF_MEMORY, MF_ERR_CUDA. */
+mf_status mf_create_grid(const mf_grid_desc* desc, const double* bc_ccw, mf_grid** out);
+mf_status mf_destroy_grid(mf_grid* grid);
+
+/* Grid dimensions (points): *nx = 32 lx + 1, *ny = 32 ly + 1. */
+mf_status mf_grid_dims(const mf_grid* grid, int* nx, int* ny);
+
+/* Overwrite the whole grid (ny x nx FP32, boundary included) from `src`, a host
+ * (src_on_device = 0) or device (1) pointer. Asynchronous on `stream`; a host
+ * source should be pinned for the copy to overlap, and must stay valid until the
+ * stream reaches the copy. */
+mf_status mf_grid_upload(mf_grid* grid, const float* src, int src_on_device, void* stream);
+
+/* Copy the whole grid to `dst` (host or device). Asynchronous like mf_grid_upload. */
+mf_status mf_grid_download(const mf_grid* grid, float* dst, int dst_on_device, void* stream);
+
+/* mf_sweep -- run Mosaic Flow predictor sweeps on the grid (Section 2.4, Section 4.1,
+ * Algorithm 2). Each sweep, for each selected colour in order 0..3: gather the 128
+ * boundary values of every subdomain of the colour, evaluate the SDNet at its 961
+ * interior points with the input-split first layer (Eq. 8), and write the
+ * predictions into the grid. MF_SCHEDULE_MULTIPLICATIVE writes them directly, so
+ * later colours see earlier colours' results. MF_SCHEDULE_ADDITIVE makes every
+ * colour read the grid as it was before the sweep and sets each interior point to
+ * the average of the predictions of the subdomains that contain it.
+ * After each checked sweep, delta = ||u_k - u_{k-1}||_2 / ||u_{k-1}||_2 over all grid
+ * points is computed in FP64 (0/0 = 0). With eps > 0 the call synchronises `stream`
+ * after each checked sweep and stops once delta < eps. The call always synchronises
+ * `stream` before returning to fill `result` (which may be NULL).
+ * Errors: MF_ERR_INVALID_ARG (null handle/opts, bad option), MF_ERR_DIVERGED (delta
+ * not finite; the grid holds the diverged state), MF_ERR_TIMEOUT, MF_ERR_CUDA. */
+mf_status mf_sweep(mf_grid* grid, const mf_sdnet* net, const mf_sweep_opts* opts,
+                   mf_sweep_result* result, void* stream);
+
+/* Block the calling host thread until all work enqueued on `stream` has finished. */
+mf_status mf_synchronize(void* stream);
+
+/* mf_residual -- 5-point Laplace residual r = u_E + u_W + u_N + u_S - 4u over the
+ * interior points (grid units, no 1/h^2), accumulated in FP64 in a fixed order (the
+ * result does not depend on timing). Writes max |r| and the root mean square of r
+ * to the host doubles; synchronises `stream`. Either output pointer may be NULL. */
+mf_status mf_residual(const mf_grid* grid, double* max_abs, double* rms, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MOSAICFLOW_H */

@@ -1,0 +1,357 @@
+// C ABI of the Mosaic Flow sweep engine: handles, validation, weight packing and the
+// sweep driver (Section 2.4, Section 4.1, Algorithm 2). All arithmetic of the sweep
+// runs in the kernels of this library; this file only validates, allocates, packs and
+// enqueues.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mosaicflow.h"
+#include "mf_internal.cuh"
+
+struct mf_sdnet {
+  int device = 0;
+  mf::DevNet d{};
+  void* dmem = nullptr;           // one device allocation for every weight array
+  std::vector<float> h_bh, h_wout, h_W2;
+};
+
+struct mf_grid {
+  int device = 0;
+  int lx = 0, ly = 0, nx = 0, ny = 0;
+  float* u = nullptr;       // current grid
+  float* prev = nullptr;    // grid before the sweep (delta, additive reads)
+  float* B = nullptr;       // [max colour subdomains][128] first-layer term
+  double* partial = nullptr;
+  double* out = nullptr;    // 16 doubles: [0..4] sweep reduction + delta, [8..12] residual
+  int* status = nullptr;    // kernel status word
+  double* h_out = nullptr;  // pinned host mirror of out (16 doubles)
+  int* h_status = nullptr;  // pinned host mirror of status
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+mf_status fail(mf_status code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+mf_status cuda_fail(cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return fail(e == cudaErrorMemoryAllocation ? MF_ERR_OUT_OF_MEMORY : MF_ERR_CUDA, m);
+}
+
+#define MF_CUDA(call, what)                     \
+  do {                                          \
+    cudaError_t e_ = (call);                    \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+uint16_t bf16_rne(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u && (u & 0x007fffffu)) return (uint16_t)((u >> 16) | 0x40u);  // NaN
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+
+// BF16 image of one H x H matrix W[n][k] (row n = output unit) as the B operand of
+// tcgen05.mma: K-major, 128-byte swizzle: K blocks of 64 elements, each block holds
+// H rows of 128 bytes, 16-byte chunk c of row n stored at chunk c ^ (n mod 8).
+void pack_sw128(const float* W, int H, uint16_t* img) {
+  for (int n = 0; n < H; ++n)
+    for (int k = 0; k < H; ++k) {
+      const int kb = k / 64, w = k % 64, chunk = w / 8, e = w % 8;
+      const size_t off = (size_t)kb * H * 64 + (size_t)n * 64 + (size_t)((chunk ^ (n & 7)) * 8) + e;
+      img[off] = bf16_rne(W[(size_t)n * H + k]);
+    }
+}
+
+mf::ColourGeom colour_geom(const mf_grid* g, int c) {
+  mf::ColourGeom cg{};
+  cg.nx = g->nx;
+  cg.ca = c & 1;
+  cg.cb = c >> 1;
+  cg.nsx = 2 * g->lx - 1;
+  cg.nsy = 2 * g->ly - 1;
+  const int n_a = (cg.nsx - cg.ca + 1) / 2;
+  const int n_b = (cg.nsy - cg.cb + 1) / 2;
+  cg.n_a = n_a;
+  cg.n_c = n_a * n_b;
+  return cg;
+}
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+extern "C" {
+
+const char* mf_last_error(void) { return g_err.c_str(); }
+
+int mf_version(void) { return 100; }
+
+mf_status mf_load_sdnet(const mf_sdnet_desc* desc, const float* w, mf_sdnet** out) {
+  if (!desc || !w || !out) return fail(MF_ERR_INVALID_ARG, "mf_load_sdnet: null argument");
+  *out = nullptr;
+  const int H = desc->width, D = desc->depth;
+  if (H != 64 && H != 128) return fail(MF_ERR_INVALID_ARG, "mf_load_sdnet: width must be 64 or 128");
+  if (D < 2 || D > 6) return fail(MF_ERR_INVALID_ARG, "mf_load_sdnet: depth must be in 2..6");
+  const int NH = D - 1;
+  for (size_t i = 0, n = (size_t)H * 131 + (size_t)NH * (H * H + H) + H + 1; i < n; ++i)
+    if (!std::isfinite(w[i])) return fail(MF_ERR_INVALID_ARG, "mf_load_sdnet: non-finite weight");
+
+  // unpack the FP32 layout W0[H][130], b0, {W[H][H], b}, w_out, b_out
+  const float* p = w;
+  const float* W0 = p;  p += (size_t)H * 130;
+  const float* b0 = p;  p += H;
+  std::vector<float> W1t((size_t)128 * H), W2((size_t)H * 2), WhT((size_t)NH * H * H), bh((size_t)NH * H);
+  for (int j = 0; j < H; ++j) {
+    for (int k = 0; k < 128; ++k) W1t[(size_t)k * H + j] = W0[(size_t)j * 130 + k];
+    W2[2 * j] = W0[(size_t)j * 130 + 128];
+    W2[2 * j + 1] = W0[(size_t)j * 130 + 129];
+  }
+  std::vector<uint16_t> img((size_t)NH * H * H);
+  for (int l = 0; l < NH; ++l) {
+    const float* Wl = p;  p += (size_t)H * H;
+    const float* bl = p;  p += H;
+    for (int n = 0; n < H; ++n)
+      for (int k = 0; k < H; ++k) WhT[(size_t)l * H * H + (size_t)k * H + n] = Wl[(size_t)n * H + k];
+    std::memcpy(&bh[(size_t)l * H], bl, sizeof(float) * H);
+    pack_sw128(Wl, H, &img[(size_t)l * H * H]);
+  }
+  const float* wout = p;  p += H;
+  const float bout = *p;
+
+  mf_sdnet* net = new mf_sdnet();
+  cudaGetDevice(&net->device);
+  // one allocation: W1t | W2 | b0 | WhT | bh | wout | BF16 images (each 256-byte aligned)
+  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t sz_W1t = up(W1t.size() * 4), sz_W2 = up(W2.size() * 4), sz_b0 = up((size_t)H * 4),
+               sz_WhT = up(WhT.size() * 4), sz_bh = up(bh.size() * 4), sz_wout = up((size_t)H * 4),
+               sz_img = up(img.size() * 2);
+  const size_t total = sz_W1t + sz_W2 + sz_b0 + sz_WhT + sz_bh + sz_wout + sz_img;
+  cudaError_t e = cudaMalloc(&net->dmem, total);
+  if (e != cudaSuccess) {
+    delete net;
+    return cuda_fail(e, "mf_load_sdnet: cudaMalloc");
+  }
+  char* base = static_cast<char*>(net->dmem);
+  size_t o = 0;
+  auto place = [&](const void* src, size_t bytes, size_t slot) -> void* {
+    void* dst = base + o;
+    o += slot;
+    if (cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return nullptr;
+    return dst;
+  };
+  net->d.W1t = (const float*)place(W1t.data(), W1t.size() * 4, sz_W1t);
+  net->d.W2 = (const float*)place(W2.data(), W2.size() * 4, sz_W2);
+  net->d.b0 = (const float*)place(b0, (size_t)H * 4, sz_b0);
+  net->d.WhT = (const float*)place(WhT.data(), WhT.size() * 4, sz_WhT);
+  net->d.bh = (const float*)place(bh.data(), bh.size() * 4, sz_bh);
+  net->d.wout = (const float*)place(wout, (size_t)H * 4, sz_wout);
+  net->d.wimg_bf16 = place(img.data(), img.size() * 2, sz_img);
+  if (!net->d.W1t || !net->d.W2 || !net->d.b0 || !net->d.WhT || !net->d.bh || !net->d.wout || !net->d.wimg_bf16) {
+    cudaError_t err = cudaGetLastError();
+    cudaFree(net->dmem);
+    delete net;
+    return cuda_fail(err == cudaSuccess ? cudaErrorUnknown : err, "mf_load_sdnet: upload");
+  }
+  net->d.width = H;
+  net->d.depth = D;
+  net->d.n_hidden = NH;
+  net->d.bout = bout;
+  net->d.wimg_bytes = img.size() * 2;
+  net->h_bh = bh;
+  net->h_wout.assign(wout, wout + H);
+  net->h_W2 = W2;
+  net->d.h_bh = net->h_bh.data();
+  net->d.h_wout = net->h_wout.data();
+  net->d.h_W2 = net->h_W2.data();
+  *out = net;
+  return MF_OK;
+}
+
+mf_status mf_free_sdnet(mf_sdnet* net) {
+  if (!net) return MF_OK;
+  cudaSetDevice(net->device);
+  cudaFree(net->dmem);
+  delete net;
+  return MF_OK;
+}
+
+mf_status mf_destroy_grid(mf_grid* g) {
+  if (!g) return MF_OK;
+  cudaSetDevice(g->device);
+  cudaFree(g->u);
+  cudaFree(g->prev);
+  cudaFree(g->B);
+  cudaFree(g->partial);
+  cudaFree(g->out);
+  cudaFree(g->status);
+  cudaFreeHost(g->h_out);
+  cudaFreeHost(g->h_status);
+  delete g;
+  return MF_OK;
+}
+
+mf_status mf_create_grid(const mf_grid_desc* desc, const double* bc, mf_grid** out) {
+  if (!desc || !bc || !out) return fail(MF_ERR_INVALID_ARG, "mf_create_grid: null argument");
+  *out = nullptr;
+  if (desc->lx < 1 || desc->lx > 128 || desc->ly < 1 || desc->ly > 128)
+    return fail(MF_ERR_INVALID_ARG, "mf_create_grid: lx and ly must be in 1..128");
+  mf_grid* g = new mf_grid();
+  MF_CUDA(cudaGetDevice(&g->device), "mf_create_grid: cudaGetDevice");
+  g->lx = desc->lx;
+  g->ly = desc->ly;
+  g->nx = mf::kPts * g->lx + 1;
+  g->ny = mf::kPts * g->ly + 1;
+  const size_t npts = (size_t)g->nx * g->ny;
+  const size_t nbc = 2 * (size_t)(g->nx - 1) + 2 * (size_t)(g->ny - 1);
+  const size_t max_colour = (size_t)g->lx * g->ly;  // colour (0,0) is the largest
+  double* dbc = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMalloc(&g->u, npts * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&g->prev, npts * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&g->B, max_colour * 128 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&g->partial, mf::kReduceBlocks * 4 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&g->out, 16 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&g->status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost(&g->h_out, 16 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost(&g->h_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&dbc, nbc * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpy(dbc, bc, nbc * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = mf::launch_init_grid(g->u, g->nx, g->ny, dbc, nullptr);
+  if (e == cudaSuccess) e = cudaMemset(g->status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(g->out, 0, 16 * sizeof(double));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (dbc) cudaFree(dbc);
+  if (e != cudaSuccess) {
+    mf_destroy_grid(g);
+    return cuda_fail(e, "mf_create_grid");
+  }
+  *out = g;
+  return MF_OK;
+}
+
+mf_status mf_grid_dims(const mf_grid* g, int* nx, int* ny) {
+  if (!g) return fail(MF_ERR_INVALID_ARG, "mf_grid_dims: null grid");
+  if (nx) *nx = g->nx;
+  if (ny) *ny = g->ny;
+  return MF_OK;
+}
+
+mf_status mf_grid_upload(mf_grid* g, const float* src, int on_device, void* stream) {
+  if (!g || !src) return fail(MF_ERR_INVALID_ARG, "mf_grid_upload: null argument");
+  MF_CUDA(cudaSetDevice(g->device), "mf_grid_upload: cudaSetDevice");
+  MF_CUDA(cudaMemcpyAsync(g->u, src, (size_t)g->nx * g->ny * sizeof(float),
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, as_stream(stream)),
+          "mf_grid_upload: cudaMemcpyAsync");
+  return MF_OK;
+}
+
+mf_status mf_grid_download(const mf_grid* g, float* dst, int on_device, void* stream) {
+  if (!g || !dst) return fail(MF_ERR_INVALID_ARG, "mf_grid_download: null argument");
+  MF_CUDA(cudaSetDevice(g->device), "mf_grid_download: cudaSetDevice");
+  MF_CUDA(cudaMemcpyAsync(dst, g->u, (size_t)g->nx * g->ny * sizeof(float),
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, as_stream(stream)),
+          "mf_grid_download: cudaMemcpyAsync");
+  return MF_OK;
+}
+
+mf_status mf_sweep(mf_grid* g, const mf_sdnet* net, const mf_sweep_opts* o, mf_sweep_result* res,
+                   void* stream) {
+  if (!g || !net || !o) return fail(MF_ERR_INVALID_ARG, "mf_sweep: null argument");
+  if (o->n_sweeps < 0) return fail(MF_ERR_INVALID_ARG, "mf_sweep: n_sweeps < 0");
+  if (o->schedule != MF_SCHEDULE_MULTIPLICATIVE && o->schedule != MF_SCHEDULE_ADDITIVE)
+    return fail(MF_ERR_INVALID_ARG, "mf_sweep: unknown schedule");
+  if (o->precision != MF_PREC_FP32 && o->precision != MF_PREC_BF16)
+    return fail(MF_ERR_INVALID_ARG, "mf_sweep: unknown precision");
+  if (o->colours < 0 || o->colours > 15) return fail(MF_ERR_INVALID_ARG, "mf_sweep: colours must be a 4-bit mask");
+  if (o->check_every < 1) return fail(MF_ERR_INVALID_ARG, "mf_sweep: check_every must be >= 1");
+  if (!std::isfinite(o->eps)) return fail(MF_ERR_INVALID_ARG, "mf_sweep: eps must be finite");
+  if (o->precision == MF_PREC_BF16 && !mf::bf16_supported(net->d))
+    return fail(MF_ERR_UNSUPPORTED, "mf_sweep: BF16 path needs 1..5 hidden layers");
+  if (net->device != g->device) return fail(MF_ERR_INVALID_ARG, "mf_sweep: grid and SDNet on different devices");
+  if (res) {
+    res->sweeps_done = 0;
+    res->delta = -1.0;
+  }
+  MF_CUDA(cudaSetDevice(g->device), "mf_sweep: cudaSetDevice");
+  cudaStream_t st = as_stream(stream);
+  const int mask = o->colours == 0 ? 15 : o->colours;
+  const bool additive = o->schedule == MF_SCHEDULE_ADDITIVE;
+  const size_t bytes = (size_t)g->nx * g->ny * sizeof(float);
+  MF_CUDA(cudaMemsetAsync(g->status, 0, sizeof(int), st), "mf_sweep: reset status");
+
+  int done = 0;
+  bool checked = false;
+  for (int k = 0; k < o->n_sweeps; ++k) {
+    const bool check = ((k + 1) % o->check_every == 0) || (k + 1 == o->n_sweeps);
+    if (check || additive)
+      MF_CUDA(cudaMemcpyAsync(g->prev, g->u, bytes, cudaMemcpyDeviceToDevice, st), "mf_sweep: snapshot");
+    if (additive) MF_CUDA(mf::launch_zero_interior(g->u, g->nx, g->ny, st), "mf_sweep: zero interior");
+    for (int c = 0; c < 4; ++c) {
+      if (!((mask >> c) & 1)) continue;
+      const mf::ColourGeom cg = colour_geom(g, c);
+      if (cg.n_c == 0) continue;
+      MF_CUDA(mf::launch_gather_boundary(additive ? g->prev : g->u, cg, net->d, g->B, st), "mf_sweep: gather");
+      if (o->precision == MF_PREC_BF16)
+        MF_CUDA(mf::launch_mlp_bf16(g->B, cg, net->d, g->u, additive ? 1 : 0, g->status, st), "mf_sweep: bf16 mlp");
+      else
+        MF_CUDA(mf::launch_mlp_fp32(g->B, cg, net->d, g->u, additive ? 1 : 0, st), "mf_sweep: fp32 mlp");
+    }
+    done = k + 1;
+    if (check) {
+      MF_CUDA(mf::launch_reduce(g->u, g->prev, g->nx, g->ny, g->partial, g->out, st), "mf_sweep: reduce");
+      checked = true;
+      if (o->eps > 0.0) {
+        MF_CUDA(cudaMemcpyAsync(g->h_out, g->out, 5 * sizeof(double), cudaMemcpyDeviceToHost, st), "mf_sweep: read delta");
+        MF_CUDA(cudaMemcpyAsync(g->h_status, g->status, sizeof(int), cudaMemcpyDeviceToHost, st), "mf_sweep: read status");
+        MF_CUDA(cudaStreamSynchronize(st), "mf_sweep: synchronize");
+        if (*g->h_status != mf::kDevErrNone) return fail(MF_ERR_TIMEOUT, "mf_sweep: a kernel wait timed out");
+        const double d = g->h_out[4];
+        if (res) { res->sweeps_done = done; res->delta = d; }
+        if (!std::isfinite(d)) return fail(MF_ERR_DIVERGED, "mf_sweep: delta is not finite");
+        if (d < o->eps) break;
+      }
+    }
+  }
+  MF_CUDA(cudaMemcpyAsync(g->h_out, g->out, 5 * sizeof(double), cudaMemcpyDeviceToHost, st), "mf_sweep: read delta");
+  MF_CUDA(cudaMemcpyAsync(g->h_status, g->status, sizeof(int), cudaMemcpyDeviceToHost, st), "mf_sweep: read status");
+  MF_CUDA(cudaStreamSynchronize(st), "mf_sweep: synchronize");
+  if (*g->h_status != mf::kDevErrNone) return fail(MF_ERR_TIMEOUT, "mf_sweep: a kernel wait timed out");
+  if (res) {
+    res->sweeps_done = done;
+    res->delta = checked ? g->h_out[4] : -1.0;
+  }
+  if (checked && !std::isfinite(g->h_out[4])) return fail(MF_ERR_DIVERGED, "mf_sweep: delta is not finite");
+  return MF_OK;
+}
+
+mf_status mf_synchronize(void* stream) {
+  MF_CUDA(cudaStreamSynchronize(as_stream(stream)), "mf_synchronize");
+  return MF_OK;
+}
+
+mf_status mf_residual(const mf_grid* g, double* max_abs, double* rms, void* stream) {
+  if (!g) return fail(MF_ERR_INVALID_ARG, "mf_residual: null grid");
+  MF_CUDA(cudaSetDevice(g->device), "mf_residual: cudaSetDevice");
+  cudaStream_t st = as_stream(stream);
+  MF_CUDA(mf::launch_reduce(g->u, nullptr, g->nx, g->ny, g->partial, g->out + 8, st), "mf_residual: reduce");
+  MF_CUDA(cudaMemcpyAsync(g->h_out + 8, g->out + 8, 5 * sizeof(double), cudaMemcpyDeviceToHost, st),
+          "mf_residual: read");
+  MF_CUDA(cudaStreamSynchronize(st), "mf_residual: synchronize");
+  const double n_int = (double)(g->nx - 2) * (double)(g->ny - 2);
+  if (max_abs) *max_abs = g->h_out[10];
+  if (rms) *rms = std::sqrt(g->h_out[11] / n_int);
+  return MF_OK;
+}
+
+}  // extern "C"

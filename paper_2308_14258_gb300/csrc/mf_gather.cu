@@ -1,0 +1,125 @@
+// K0 grid set-up and K1 boundary gather + per-subdomain first-layer term.
+//
+// K1 reads, for every subdomain of one colour, its 128 boundary values from the global
+// grid (the in-device form of Algorithm 2's boundary exchange) and forms the left
+// operand of the input-split first layer (Eq. 8): B[s][:] = W1 g_s + b0, with W1 the
+// boundary block of the first-layer weights. The per-point coordinate term X W2^T is
+// added later, per row, inside the MLP kernels, so the boundary GEMM runs once per
+// subdomain instead of once per point (Section 3.2).
+#include "mf_internal.cuh"
+
+namespace mf {
+
+namespace {
+
+constexpr int kGatherThreads = 256;
+constexpr int kSubPerBlock = 16;  // subdomains per block (one warp gathers two)
+
+template <int H>
+__global__ void __launch_bounds__(kGatherThreads)
+gather_boundary_kernel(const float* __restrict__ u, ColourGeom g, const float* __restrict__ W1t,
+                       const float* __restrict__ b0, float* __restrict__ B) {
+  __shared__ float gs[kSubPerBlock][kNbdry];
+  const int s0 = blockIdx.x * kSubPerBlock;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  // Gather: bottom and top strips are 32 consecutive floats (one 128-byte coalesced
+  // request per warp); the left and right strips are one value per grid row.
+  for (int i = warp; i < kSubPerBlock; i += kGatherThreads / 32) {
+    const int s = s0 + i;
+    if (s < g.n_c) {
+      const int a = g.ca + 2 * (s % g.n_a);
+      const int b = g.cb + 2 * (s / g.n_a);
+      const size_t nx = (size_t)g.nx;
+      const float* o = u + (size_t)(kHalf * b) * nx + (size_t)(kHalf * a);
+      gs[i][lane] = __ldg(o + lane);                                   // (lane, 0)
+      gs[i][32 + lane] = __ldg(o + (size_t)lane * nx + kPts);          // (32, lane)
+      gs[i][64 + lane] = __ldg(o + (size_t)kPts * nx + (kPts - lane)); // (32 - lane, 32)
+      gs[i][96 + lane] = __ldg(o + (size_t)(kPts - lane) * nx);        // (0, 32 - lane)
+    } else {
+      gs[i][lane] = gs[i][32 + lane] = gs[i][64 + lane] = gs[i][96 + lane] = 0.f;
+    }
+  }
+  __syncthreads();
+
+  // B[s][j] = sum_k W1[j][k] g_s[k] + b0[j]; W1t is k-major so the weight reads of a
+  // warp are one contiguous row segment.
+  constexpr int kGroups = kGatherThreads / H;
+  constexpr int kPer = kSubPerBlock / kGroups;
+  const int j = threadIdx.x % H, grp = threadIdx.x / H;
+  float acc[kPer];
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) acc[i] = 0.f;
+#pragma unroll 4
+  for (int k = 0; k < kNbdry; ++k) {
+    const float w = __ldg(W1t + k * H + j);
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) acc[i] = fmaf(w, gs[grp + i * kGroups][k], acc[i]);
+  }
+  const float bj = __ldg(b0 + j);
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) {
+    const int s = s0 + grp + i * kGroups;
+    if (s < g.n_c) B[(size_t)s * H + j] = acc[i] + bj;
+  }
+}
+
+// K0: boundary from the CCW Dirichlet list (rounded to FP32), interior zero.
+__global__ void init_grid_kernel(float* __restrict__ u, int nx, int ny, const double* __restrict__ bc) {
+  const size_t n = (size_t)nx * ny;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int iy = (int)(i / nx), ix = (int)(i % nx);
+    float v = 0.f;
+    if (iy == 0) {
+      v = (float)bc[ix == nx - 1 ? (nx - 1) : ix];             // bottom, corner (nx-1,0) starts the right edge
+    } else if (ix == nx - 1) {
+      v = (float)bc[(nx - 1) + (iy == ny - 1 ? (ny - 1) : iy)]; // right, corner (nx-1,ny-1) starts the top
+    } else if (iy == ny - 1) {
+      v = (float)bc[(nx - 1) + (ny - 1) + (nx - 1 - ix)];       // top, ix = nx-1..1
+    } else if (ix == 0) {
+      v = (float)bc[2 * (nx - 1) + (ny - 1) + (ny - 1 - iy)];   // left, iy = ny-1..1
+    }
+    u[i] = v;
+  }
+}
+
+__global__ void zero_interior_kernel(float* __restrict__ u, int nx, int ny) {
+  const int mx = nx - 2;
+  const size_t n = (size_t)mx * (ny - 2);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t iy = 1 + i / mx, ix = 1 + i % mx;
+    u[iy * nx + ix] = 0.f;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_gather_boundary(const float* u, const ColourGeom& g, const DevNet& net, float* B,
+                                   cudaStream_t st) {
+  if (g.n_c <= 0) return cudaSuccess;
+  const int blocks = (g.n_c + kSubPerBlock - 1) / kSubPerBlock;
+  if (net.width == 128)
+    gather_boundary_kernel<128><<<blocks, kGatherThreads, 0, st>>>(u, g, net.W1t, net.b0, B);
+  else
+    gather_boundary_kernel<64><<<blocks, kGatherThreads, 0, st>>>(u, g, net.W1t, net.b0, B);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_grid(float* u, int nx, int ny, const double* bc, cudaStream_t st) {
+  const size_t n = (size_t)nx * ny;
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  init_grid_kernel<<<blocks, 256, 0, st>>>(u, nx, ny, bc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero_interior(float* u, int nx, int ny, cudaStream_t st) {
+  const size_t n = (size_t)(nx - 2) * (ny - 2);
+  if (n == 0) return cudaSuccess;
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  zero_interior_kernel<<<blocks, 256, 0, st>>>(u, nx, ny);
+  return cudaGetLastError();
+}
+
+}  // namespace mf

@@ -1,0 +1,118 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mf {
+
+// Geometry of the unit subdomain: 32 intervals per side, lattice spacing 16 points.
+constexpr int kPts = 32;        // intervals per unit length
+constexpr int kHalf = 16;       // spacing of subdomain origins (1/2 unit)
+constexpr int kNi = 31;         // interior points per side
+constexpr int kNint = 961;      // interior points per subdomain
+constexpr int kNbdry = 128;     // boundary values per subdomain
+constexpr int kTileRows = 128;  // rows (subdomain, point) per MLP tile
+
+// Device error codes written to the status word by kernels whose bounded waits give up.
+constexpr int kDevErrNone = 0;
+constexpr int kDevErrTimeout = 1;
+
+// One colour of one problem, as seen by the kernels.
+struct ColourGeom {
+  int nx;       // grid row length (points)
+  int ca, cb;   // colour parity in x and y
+  int n_a;      // subdomains of this colour along x
+  int n_c;      // subdomains of this colour
+  int nsx, nsy; // subdomains along x and y (all colours)
+};
+
+// SDNet weights resident on the device (plus host copies of the small vectors that
+// the tensor-core kernel takes as launch parameters).
+struct DevNet {
+  int width, depth;      // H and number of tanh layers
+  int n_hidden;          // depth - 1 hidden H x H layers
+  const float* W1t;      // [128][H] boundary block of W0, transposed (k-major)
+  const float* W2;       // [H][2] coordinate block of W0
+  const float* b0;       // [H]
+  const float* WhT;      // [n_hidden][H(k)][H(n)] hidden weights, transposed (k-major)
+  const float* bh;       // [n_hidden][H]
+  const float* wout;     // [H]
+  float bout;
+  const void* wimg_bf16; // [n_hidden] BF16 images in the tensor-core shared-memory layout
+  size_t wimg_bytes;     // bytes of all images
+  const float* h_bh;     // host copies: hidden biases [n_hidden][H]
+  const float* h_wout;   // [H]
+  const float* h_W2;     // [H][2]
+};
+
+// K1: gather the boundary of every subdomain of the colour from `u` and form the
+// per-subdomain first-layer term B[s][:] = W1 g_s + b0 (Eq. 8, left operand).
+cudaError_t launch_gather_boundary(const float* u, const ColourGeom& g, const DevNet& net,
+                                   float* B, cudaStream_t st);
+
+// K3f: FP32 SDNet on every interior point of every subdomain of the colour, fused with
+// the scatter into `u` (store, or weighted add for the additive schedule).
+cudaError_t launch_mlp_fp32(const float* B, const ColourGeom& g, const DevNet& net,
+                            float* u, int additive, cudaStream_t st);
+
+// K3: BF16 tcgen05 SDNet with TMEM accumulators, same contract as launch_mlp_fp32.
+cudaError_t launch_mlp_bf16(const float* B, const ColourGeom& g, const DevNet& net,
+                            float* u, int additive, int* dev_status, cudaStream_t st);
+bool bf16_supported(const DevNet& net);
+
+// K5: FP64 reductions over the grid. partial must hold kReduceBlocks * 4 doubles and
+// out 5 doubles: {sum (u-prev)^2, sum prev^2, max |r|, sum r^2, delta}.
+constexpr int kReduceBlocks = 512;
+cudaError_t launch_reduce(const float* u, const float* prev, int nx, int ny, double* partial,
+                          double* out, cudaStream_t st);
+
+// K0 grid set-up: boundary from the FP64 counter-clockwise list `bc` (device), interior 0.
+cudaError_t launch_init_grid(float* u, int nx, int ny, const double* bc, cudaStream_t st);
+cudaError_t launch_zero_interior(float* u, int nx, int ny, cudaStream_t st);
+
+}  // namespace mf
+
+namespace mf {
+
+// Row r of a colour's batch is interior point p = r mod 961 of subdomain s = r / 961
+// (colour-local index, row-major over the colour's subdomains).
+struct RowSite {
+  int s;      // colour-local subdomain index
+  size_t idx; // grid offset of the point
+  int px, py; // local interior indices 0..30
+  int ix, iy; // global grid indices
+};
+
+__device__ __forceinline__ RowSite row_site(const ColourGeom& g, int row) {
+  RowSite r;
+  r.s = row / kNint;
+  const int p = row - r.s * kNint;
+  r.py = p / kNi;
+  r.px = p - r.py * kNi;
+  const int a = g.ca + 2 * (r.s % g.n_a);
+  const int b = g.cb + 2 * (r.s / g.n_a);
+  r.ix = kHalf * a + 1 + r.px;
+  r.iy = kHalf * b + 1 + r.py;
+  r.idx = (size_t)r.iy * (size_t)g.nx + (size_t)r.ix;
+  return r;
+}
+
+// Number of subdomains along one axis whose open interior holds grid coordinate i.
+__device__ __forceinline__ int axis_cover(int i, int n_sub) {
+  int c = 0;
+  const int a1 = (i - 1) / kHalf;  // largest origin index with 16a < i
+#pragma unroll
+  for (int d = 0; d < 2; ++d) {
+    const int a = a1 - d;
+    if (a >= 0 && a < n_sub && kHalf * a < i && i < kHalf * a + kPts) ++c;
+  }
+  return c;
+}
+
+// Additive schedule: weight 1/cover of the point (exact in FP32: 1, 1/2 or 1/4).
+__device__ __forceinline__ float cover_weight(const ColourGeom& g, int ix, int iy) {
+  return 1.0f / (float)(axis_cover(ix, g.nsx) * axis_cover(iy, g.nsy));
+}
+
+}  // namespace mf

@@ -1,0 +1,193 @@
+"""ctypes binding of libmosaicflow.so: the mf_* calls with Python argument marshalling.
+
+Every step of the sweep runs in the library's sm_103a kernels; this module only converts
+arguments (NumPy arrays, torch tensors, streams) to the C ABI and raises MFError on a
+non-zero status. There is no CPU fallback: if the library is missing or cannot be
+loaded, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+MF_OK = 0
+MF_ERR_INVALID_ARG = -1
+MF_ERR_CUDA = -2
+MF_ERR_OUT_OF_MEMORY = -3
+MF_ERR_DIVERGED = -4
+MF_ERR_TIMEOUT = -5
+MF_ERR_UNSUPPORTED = -6
+
+PREC = {"fp32": 0, "bf16": 1}
+SCHEDULE = {"M": 0, "multiplicative": 0, "A": 1, "additive": 1}
+
+# Every exported symbol the header declares (checked by the CPU test suite).
+EXPORTS = ["mf_last_error", "mf_version", "mf_load_sdnet", "mf_free_sdnet", "mf_create_grid",
+           "mf_destroy_grid", "mf_grid_dims", "mf_grid_upload", "mf_grid_download", "mf_sweep",
+           "mf_residual", "mf_synchronize"]
+
+
+class MFError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"mosaicflow status {status}: {msg}")
+        self.status = status
+
+
+class SDNetDesc(C.Structure):
+    _fields_ = [("width", C.c_int), ("depth", C.c_int)]
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("lx", C.c_int), ("ly", C.c_int)]
+
+
+class SweepOpts(C.Structure):
+    _fields_ = [("n_sweeps", C.c_int), ("schedule", C.c_int), ("precision", C.c_int),
+                ("colours", C.c_int), ("eps", C.c_double), ("check_every", C.c_int)]
+
+
+class SweepResult(C.Structure):
+    _fields_ = [("sweeps_done", C.c_int), ("delta", C.c_double)]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None) -> C.CDLL:
+    """Load the library (once). Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libmosaicflow.so not found at {path}; run __graft_entry__.build() first")
+    lib = C.CDLL(path)
+    vp, i = C.c_void_p, C.c_int
+    lib.mf_last_error.restype = C.c_char_p
+    lib.mf_version.restype = i
+    lib.mf_load_sdnet.argtypes = [C.POINTER(SDNetDesc), vp, C.POINTER(vp)]
+    lib.mf_free_sdnet.argtypes = [vp]
+    lib.mf_create_grid.argtypes = [C.POINTER(GridDesc), vp, C.POINTER(vp)]
+    lib.mf_destroy_grid.argtypes = [vp]
+    lib.mf_grid_dims.argtypes = [vp, C.POINTER(i), C.POINTER(i)]
+    lib.mf_grid_upload.argtypes = [vp, vp, i, vp]
+    lib.mf_grid_download.argtypes = [vp, vp, i, vp]
+    lib.mf_sweep.argtypes = [vp, vp, C.POINTER(SweepOpts), C.POINTER(SweepResult), vp]
+    lib.mf_residual.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
+    lib.mf_synchronize.argtypes = [vp]
+    for name in EXPORTS:
+        if name not in ("mf_last_error", "mf_version"):
+            getattr(lib, name).restype = i
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != MF_OK:
+        raise MFError(status, load().mf_last_error().decode())
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+def _buffer(arr):
+    """(pointer, on_device, nbytes) of a contiguous float32 NumPy array or torch tensor."""
+    if isinstance(arr, np.ndarray):
+        if arr.dtype != np.float32 or not arr.flags["C_CONTIGUOUS"]:
+            raise TypeError("expected a C-contiguous float32 array")
+        return arr.ctypes.data, 0, arr.nbytes
+    import torch  # torch tensors: device memory or (pinned) host memory
+    if arr.dtype != torch.float32 or not arr.is_contiguous():
+        raise TypeError("expected a contiguous float32 tensor")
+    return arr.data_ptr(), 1 if arr.is_cuda else 0, arr.numel() * 4
+
+
+class SDNet:
+    """mf_load_sdnet / mf_free_sdnet."""
+
+    def __init__(self, weights: np.ndarray, width: int, depth: int):
+        w = np.ascontiguousarray(weights, dtype=np.float32)
+        self.width, self.depth = width, depth
+        self._h = C.c_void_p()
+        _check(load().mf_load_sdnet(C.byref(SDNetDesc(width, depth)), w.ctypes.data, C.byref(self._h)))
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.mf_free_sdnet(self._h)
+            self._h = None
+
+
+@dataclass
+class SweepOutcome:
+    sweeps_done: int
+    delta: float
+
+
+class Grid:
+    """mf_create_grid / mf_grid_* / mf_sweep / mf_residual for one problem."""
+
+    def __init__(self, lx: int, ly: int, bc_ccw: np.ndarray):
+        bc = np.ascontiguousarray(bc_ccw, dtype=np.float64)
+        self.lx, self.ly = lx, ly
+        self.nx, self.ny = 32 * lx + 1, 32 * ly + 1
+        if bc.size != 2 * (self.nx - 1) + 2 * (self.ny - 1):
+            raise ValueError("bc_ccw has the wrong length")
+        self._h = C.c_void_p()
+        _check(load().mf_create_grid(C.byref(GridDesc(lx, ly)), bc.ctypes.data, C.byref(self._h)))
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.mf_destroy_grid(self._h)
+            self._h = None
+
+    @property
+    def shape(self):
+        return (self.ny, self.nx)
+
+    def upload(self, src, stream=None):
+        ptr, dev, nbytes = _buffer(src)
+        if nbytes != self.nx * self.ny * 4:
+            raise ValueError("grid size mismatch")
+        _check(load().mf_grid_upload(self._h, ptr, dev, _stream_ptr(stream)))
+
+    def download(self, dst=None, stream=None, sync=True):
+        if dst is None:
+            dst = np.empty(self.shape, dtype=np.float32)
+        ptr, dev, nbytes = _buffer(dst)
+        if nbytes != self.nx * self.ny * 4:
+            raise ValueError("grid size mismatch")
+        _check(load().mf_grid_download(self._h, ptr, dev, _stream_ptr(stream)))
+        if sync:
+            synchronize(stream)
+        return dst
+
+    def sweep(self, net: SDNet, n_sweeps: int = 1, schedule: str = "M", precision: str = "fp32",
+              colours: int = 0, eps: float = 0.0, check_every: int = 1, stream=None) -> SweepOutcome:
+        opts = SweepOpts(n_sweeps, SCHEDULE[schedule], PREC[precision], colours, eps, check_every)
+        res = SweepResult()
+        _check(load().mf_sweep(self._h, net._h, C.byref(opts), C.byref(res), _stream_ptr(stream)))
+        return SweepOutcome(res.sweeps_done, res.delta)
+
+    def residual(self, stream=None):
+        mx, rms = C.c_double(), C.c_double()
+        _check(load().mf_residual(self._h, C.byref(mx), C.byref(rms), _stream_ptr(stream)))
+        return mx.value, rms.value
+
+
+def synchronize(stream=None):
+    """mf_synchronize: wait for the work enqueued on `stream` (None = default stream)."""
+    _check(load().mf_synchronize(_stream_ptr(stream)))

@@ -1,0 +1,216 @@
+"""GPU path against the FP64 oracle, through the C ABI (ctypes binding).
+
+Error measure (per sweep, from an identical FP32 input state):
+    e = max |u_gpu - u_oracle| / max |u_oracle| over the whole grid.
+Tolerances: FP32 path 1e-5, BF16 path 3e-2 per sweep.
+"""
+import numpy as np
+import pytest
+
+from oracle import mosaic_flow as orc
+from paper_2308_14258_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-5, "bf16": 3e-2}
+
+
+@pytest.fixture(scope="module")
+def m():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2308_14258_gb300 import mosaicflow
+    return mosaicflow
+
+
+def random_state(lx, ly, bc, seed, scale=0.3):
+    u = orc.make_grid(lx, ly, bc)
+    ny, nx = u.shape
+    u[1:-1, 1:-1] = I.Stream(seed, I.TAG_TEST).normal((ny - 2) * (nx - 2)).reshape(ny - 2, nx - 2) * scale
+    return u.astype(np.float32)
+
+
+def rel_err(got, ref):
+    return float(np.abs(got.astype(np.float64) - ref).max() / np.abs(ref).max())
+
+
+def problem(lx, ly, seed):
+    return I.bc_values(lx, ly, I.mode_field(I.mode_coeffs(seed), lx, ly))
+
+
+def one_sweep_case(m, lx, ly, width, depth, prec, schedule="M", seed=0, colours=0, bias=0.1):
+    w = I.xavier_sdnet(I.SDNetShape(width, depth), seed, bias_scale=bias)
+    bc = problem(lx, ly, seed + 100)
+    u0 = random_state(lx, ly, bc, seed + 200)
+    net = m.SDNet(w, width, depth)
+    g = m.Grid(lx, ly, bc)
+    g.upload(u0)
+    g.sweep(net, 1, schedule, prec, colours=colours)
+    got = g.download()
+    solver = orc.Solver(orc.unpack_sdnet(w, width, depth))
+    cols = [c for c in range(4) if colours == 0 or (colours >> c) & 1]
+    if schedule == "M":
+        ref = orc.sweep_multiplicative(u0.astype(np.float64), lx, ly, solver, colours=cols)
+    else:
+        ref = orc.sweep_additive(u0.astype(np.float64), lx, ly, solver)
+    return got, ref, u0
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("lx,ly,width,depth", [
+    (2, 2, 64, 4),     # tiny workload shape
+    (1, 1, 128, 6),    # one subdomain: 961 rows = 7 full tiles + a ragged tail of 65
+    (2, 3, 128, 6),    # rectangular
+    (3, 1, 64, 2),     # one hidden layer
+    (1, 4, 128, 3),
+])
+def test_one_sweep_multiplicative(m, prec, lx, ly, width, depth):
+    got, ref, _ = one_sweep_case(m, lx, ly, width, depth, prec)
+    assert rel_err(got, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_one_sweep_additive(m, prec):
+    got, ref, _ = one_sweep_case(m, 3, 2, 128, 6, prec, schedule="A", seed=3)
+    assert rel_err(got, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("colours", [1, 2, 4, 8, 5, 10])
+def test_colour_masks(m, colours):
+    got, ref, u0 = one_sweep_case(m, 3, 3, 64, 4, "fp32", colours=colours, seed=7)
+    assert rel_err(got, ref) <= TOL["fp32"]
+    # points outside the selected colours' interiors are untouched, bit for bit
+    touched = np.zeros(got.shape, dtype=bool)
+    for c in range(4):
+        if (colours >> c) & 1:
+            for (a, b) in orc.subdomains_of_colour(3, 3, c):
+                touched[16 * b + 1:16 * b + 32, 16 * a + 1:16 * a + 32] = True
+    assert np.array_equal(got[~touched], u0[~touched])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_mid_one_sweep(m, prec):
+    """961 subdomains, grid 513x513, SDNet 6x128 (the mid workload), from a random state."""
+    w = I.mid()
+    p = w.problems[0]
+    weights = w.weights(bias_scale=0.05)
+    u0 = random_state(p.lx, p.ly, p.bc, 31)
+    net = m.SDNet(weights, 128, 6)
+    g = m.Grid(p.lx, p.ly, p.bc)
+    g.upload(u0)
+    g.sweep(net, 1, "M", prec)
+    got = g.download()
+    solver = orc.Solver(orc.unpack_sdnet(weights, 128, 6))
+    ref = orc.sweep_multiplicative(u0.astype(np.float64), p.lx, p.ly, solver)
+    assert rel_err(got, ref) <= TOL[prec]
+
+
+def test_tiny_trajectory(m):
+    """The tiny workload as specified: 20 sweeps from the zero interior, FP32.
+
+    With random weights the sweep settles on an attracting two-cycle, so per-sweep
+    errors do not compound; the trajectory stays within 1e-5 of the oracle's."""
+    w = I.tiny()
+    p = w.problems[0]
+    weights = w.weights()
+    net = m.SDNet(weights, 64, 4)
+    g = m.Grid(2, 2, p.bc)
+    out = g.sweep(net, 20, "M", "fp32")
+    got = g.download()
+    solver = orc.Solver(orc.unpack_sdnet(weights, 64, 4))
+    u0 = orc.make_grid(2, 2, p.bc.astype(np.float32).astype(np.float64))
+    ref, hist = orc.run(u0, 2, 2, solver, 20)
+    assert out.sweeps_done == 20
+    assert rel_err(got, ref) <= 1e-5
+    assert abs(out.delta - hist[-1]) <= 1e-5 * hist[-1]
+
+
+def test_grid_setup_matches_oracle(m):
+    bc = problem(3, 2, 5)
+    g = m.Grid(3, 2, bc)
+    got = g.download()
+    ref = orc.make_grid(3, 2, bc.astype(np.float32).astype(np.float64))
+    assert np.array_equal(got.astype(np.float64), ref)
+
+
+def test_residual_and_delta_match_oracle(m):
+    bc = problem(4, 3, 6)
+    u0 = random_state(4, 3, bc, 8)
+    g = m.Grid(4, 3, bc)
+    g.upload(u0)
+    r_max, r_rms = g.residual()
+    o_max, o_rms = orc.residual(u0.astype(np.float64))
+    assert r_max == o_max                       # same per-point FP64 sums, max is exact
+    assert abs(r_rms - o_rms) <= 1e-12 * o_rms
+    w = I.xavier_sdnet(I.SDNetShape(64, 3), 2)
+    out = g.sweep(m.SDNet(w, 64, 3), 1, "M", "fp32")
+    u1 = g.download()
+    d = orc.delta(u1.astype(np.float64), u0.astype(np.float64))
+    assert abs(out.delta - d) <= 1e-12 * d
+
+
+def test_residual_of_discrete_harmonic_field(m):
+    ny, nx = orc.grid_shape(2, 2)
+    iy, ix = np.mgrid[0:ny, 0:nx]
+    u = ((ix - 7.0) * (iy + 3.0)).astype(np.float32)  # exactly representable, discrete-harmonic
+    g = m.Grid(2, 2, np.zeros(4 * 64))
+    g.upload(u)
+    r_max, r_rms = g.residual()
+    assert r_max == 0.0 and r_rms == 0.0
+
+
+def test_zero_sweeps_and_stop_rule(m):
+    w = I.tiny()
+    p = w.problems[0]
+    net = m.SDNet(w.weights(), 64, 4)
+    g = m.Grid(2, 2, p.bc)
+    before = g.download()
+    out = g.sweep(net, 0)
+    assert out.sweeps_done == 0 and out.delta == -1.0
+    assert np.array_equal(g.download(), before)
+    out = g.sweep(net, 5, eps=1e9)       # first checked sweep already below eps
+    assert out.sweeps_done == 1
+
+
+def test_invalid_arguments_raise(m):
+    w = I.tiny()
+    net = m.SDNet(w.weights(), 64, 4)
+    g = m.Grid(2, 2, w.problems[0].bc)
+    with pytest.raises(m.MFError) as e:
+        g.sweep(net, 1, check_every=0)
+    assert e.value.status == m.MF_ERR_INVALID_ARG
+    with pytest.raises(m.MFError):
+        g.sweep(net, -1)
+
+
+def test_large_sampled_per_colour(m):
+    """The 2049x2049 grid with 16129 subdomains and SDNet 6x128 (the benchmark's
+    workload) in the benchmark's launch configuration, BF16 and FP32: each colour is
+    run alone from the state the previous colour left; sampled subdomains of that
+    colour are recomputed by the oracle from the same state, and every point outside
+    the colour's interiors must be unchanged."""
+    w = I.large()
+    p = w.problems[0]
+    weights = w.weights()
+    solver = orc.Solver(orc.unpack_sdnet(weights, 128, 6))
+    net = m.SDNet(weights, 128, 6)
+    rng = np.random.default_rng(0)
+    for prec in ("bf16", "fp32"):
+        g = m.Grid(p.lx, p.ly, p.bc)
+        g.sweep(net, 1, "M", prec)          # one full sweep to reach a non-trivial state
+        for c in range(4):
+            pre = g.download()
+            g.sweep(net, 1, "M", prec, colours=1 << c)
+            post = g.download()
+            subs = orc.subdomains_of_colour(p.lx, p.ly, c)
+            pick = [subs[i] for i in rng.choice(len(subs), 24, replace=False)] + [subs[0], subs[-1]]
+            G = np.stack([orc.gather(pre.astype(np.float64), a, b) for (a, b) in pick])
+            V = solver.solve_batch(G)
+            scale = np.abs(pre).max()
+            for (a, b), v in zip(pick, V):
+                blk = post[16 * b + 1:16 * b + 32, 16 * a + 1:16 * a + 32].astype(np.float64).ravel()
+                assert np.abs(blk - v).max() / scale <= TOL[prec], (prec, c, a, b)
+            mask = np.ones(pre.shape, dtype=bool)
+            for (a, b) in subs:
+                mask[16 * b + 1:16 * b + 32, 16 * a + 1:16 * a + 32] = False
+            assert np.array_equal(pre[mask], post[mask])
