@@ -1,0 +1,404 @@
+#!/usr/bin/env python
+"""Benchmark: Mosaic Flow predictor sweeps on one GB300 (or N independent replicas).
+
+Workload (default): global domain [0,64]^2, 127 x 127 = 16,129 unit subdomains at half
+overlap, grid 2049 x 2049, SDNet 6 x 128 tanh (Xavier-uniform, seed 2), 8-mode harmonic
+Dirichlet data (seed 2): the strong-scaling domain shape of the paper (4096 atomic
+subdomains per colour) at 4096x the subdomain area.
+
+One step = one multiplicative sweep: for each of the four colours, the boundary gather
+and the SDNet on all 961 interior points of every subdomain of the colour with the
+scatter into the grid, then the FP64 delta/residual reduction. `value` is BF16
+point-evaluations/s with the grid resident on the device; the FP32 path on the same
+workload is reported beside it. L2 is flushed (a 256 MiB write) between timed steps,
+outside the timed events.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank runs its own replica (no data-path collective);
+value = all ranks' point-evaluations / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MF sweep point-evals/s, BF16 vs FP32 at <=1e-3 err; PINN train steps/s"
+UNIT = "point-evals/s"
+FLOP_PER_EVAL = 5 * 2 * 128 * 128 + 2 * 128  # hidden H x H layers + output, per point
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+# DRAM traffic of one SDNet (tensor-core) launch from an ncu capture, valid only while
+# the kernel source is unchanged (keyed by the source hash).
+NCU_TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
+    ap.add_argument("--L", type=int, default=64, help="domain side in unit subdomains (64 = the benchmark workload; "
+                                                      "smaller values only for profiling captures)")
+    ap.add_argument("--fp32-steps", type=int, default=-1)
+    ap.add_argument("--e2e-steps", type=int, default=-1)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ distributed
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if _cuda_ok() else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def _cuda_ok():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        loaded = [s for s in sm if mx and s >= 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ helpers
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+def blas_threads():
+    """Threads the oracle's BLAS uses (OpenBLAS query where available)."""
+    import ctypes
+    import re
+    try:
+        maps = open("/proc/self/maps").read()
+        for lib in sorted(set(re.findall(r"(/\S*openblas\S*\.so\S*)", maps))):
+            h = ctypes.CDLL(lib)
+            for name in ("scipy_openblas_get_num_threads64_", "scipy_openblas_get_num_threads",
+                         "openblas_get_num_threads64_", "openblas_get_num_threads"):
+                f = getattr(h, name, None)
+                if f is not None:
+                    return int(f())
+    except Exception:
+        pass
+    return os.cpu_count()
+
+
+def source_hash():
+    p = os.path.join(ROOT, "paper_2308_14258_gb300", "csrc", "mf_mlp_bf16.cu")
+    with open(p, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+
+def oracle_sample(seconds: float, u_state=None, return_values=False, chunk=256):
+    """Time the FP64 oracle on whole subdomains of the large workload (colour 0): the
+    boundary gather, the batched SDNet on all 961 interior points and the write-back,
+    in batches of `chunk` subdomains until about `seconds` have passed."""
+    import numpy as np
+    from oracle import mosaic_flow as orc
+    from paper_2308_14258_gb300 import inputs as I
+    w = I.large()
+    p = w.problems[0]
+    P = orc.unpack_sdnet(w.weights(), 128, 6)
+    u = orc.make_grid(p.lx, p.ly, p.bc) if u_state is None else u_state.astype(np.float64)
+    subs = orc.subdomains_of_colour(p.lx, p.ly, 0)
+    X = orc.interior_coords()
+    uu = u.copy()
+    done, Vs = 0, []
+    t0 = time.perf_counter()
+    n = 8
+    while done < len(subs):
+        batch = subs[done:done + n]
+        G = np.stack([orc.gather(u, a, b) for (a, b) in batch])
+        V = orc.sdnet_batched(P, G, X)
+        for (a, b), v in zip(batch, V):
+            orc.write_interior(uu, a, b, v)
+        if return_values:
+            Vs.append(V)
+        done += len(batch)
+        n = chunk
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    out = {"evals": done * orc.N_INT, "seconds": dt, "subdomains": done,
+           "value": done * orc.N_INT / dt, "threads": blas_threads()}
+    if return_values:
+        out["V"], out["subs"] = np.concatenate(Vs), subs[:done]
+    return out
+
+
+def run_reference(args, world, rank):
+    """The oracle as the reference arm: K timed bounded samples on the host cores."""
+    if rank != 0:
+        return
+    samples = []
+    budget = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample(budget / 4)
+    tot_e, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        s = oracle_sample(budget)
+        tot_e += s["evals"]
+        tot_t += s["seconds"]
+        samples.append(s)
+    v = tot_e / tot_t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": "large_L64: 2049x2049 grid, 16129 subdomains, SDNet 6x128 tanh",
+                                         "precision": "fp64 oracle (numpy)"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": samples[-1]["threads"], "kind": "oracle",
+                         "sample": f"{samples[-1]['subdomains']} whole subdomains of colour 0 per step "
+                                   f"(gather + SDNet on 961 points + write), FP64 NumPy"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def main():
+    args = parse()
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2308_14258_gb300 import inputs as I
+    from paper_2308_14258_gb300 import mosaicflow as m
+
+    w = I.large()
+    p = w.problems[0]
+    if args.L != 64:
+        p = I.Problem(args.L, args.L, I.bc_values(args.L, args.L, I.mode_field(I.mode_coeffs(2), args.L, args.L)))
+        args.no_cpu_baseline = True
+    weights = w.weights()
+    net = m.SDNet(weights, 128, 6)
+    grid = m.Grid(p.lx, p.ly, p.bc)
+    n_sub = (2 * p.lx - 1) * (2 * p.ly - 1)
+    evals_per_sweep = n_sub * 961
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def timed_steps(prec, k, profile=True):
+        ms, mlp_ms, mlp_launch, launches = [], 0.0, 0, 0
+        for _ in range(k):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = grid.sweep(net, 1, "M", prec, stream=stream, profile=profile)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            mlp_ms += out.ms_mlp
+            mlp_launch += out.mlp_launches
+            launches += out.kernel_launches
+        return ms, mlp_ms, mlp_launch, launches
+
+    # warm-up (both precisions), then the timed BF16 region with clocks sampled
+    for _ in range(args.warmup):
+        grid.sweep(net, 1, "M", "bf16", stream=stream)
+    grid.sweep(net, 1, "M", "fp32", stream=stream)
+    sampler = ClockSampler(local)
+    torch.cuda.synchronize()
+    barrier(world)
+    sampler.start()
+    ms, mlp_ms, mlp_launch, launches = timed_steps("bf16", args.steps)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    barrier(world)
+    total_s = max_over_ranks(sum(ms) / 1e3, world)
+    value = world * evals_per_sweep * args.steps / total_s
+
+    # FP32 path on the same workload (fewer steps: ~13x slower)
+    k32 = max(2, args.steps // 8) if args.fp32_steps < 0 else args.fp32_steps
+    ms32, mlp32, _, _ = timed_steps("fp32", k32)
+    fp32_value = evals_per_sweep * k32 / (sum(ms32) / 1e3) if k32 > 0 else None
+
+    # end to end through the public API: pinned host grid -> upload -> sweep -> download
+    host_in = torch.empty(grid.shape, dtype=torch.float32).pin_memory()
+    host_out = torch.empty(grid.shape, dtype=torch.float32).pin_memory()
+    grid.download(host_in, stream=stream)
+    k_e2e = max(3, min(args.steps, 10)) if args.e2e_steps < 0 else max(1, args.e2e_steps)
+    e2e_ms = []
+    for _ in range(k_e2e):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        stream.synchronize()
+        t0 = time.perf_counter()
+        grid.upload(host_in, stream=stream)
+        grid.sweep(net, 1, "M", "bf16", stream=stream)
+        grid.download(host_out, stream=stream, sync=True)
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_s = max_over_ranks(sum(e2e_ms) / 1e3, world)
+    e2e_value = world * evals_per_sweep * k_e2e / e2e_s
+    nbytes = grid.nx * grid.ny * 4
+
+    # accuracy of this run's BF16 sweep against the FP64 oracle on sampled subdomains
+    err = None
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        state = grid.download()
+        grid.sweep(net, 1, "M", "bf16", colours=1, stream=stream)
+        after = grid.download()
+        cpu = oracle_sample(args.cpu_seconds, u_state=state, return_values=True)
+        scale = float(np.abs(state).max())
+        e = 0.0
+        for (a, b), v in zip(cpu["subs"], cpu["V"]):
+            blk = after[16 * b + 1:16 * b + 32, 16 * a + 1:16 * a + 32].astype(np.float64).ravel()
+            e = max(e, float(np.abs(blk - v).max()))
+        err = e / scale
+
+    peaks, peak_src = load_peaks()
+    peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+    per_launch_ms = mlp_ms / max(1, mlp_launch)
+    flops_per_launch = evals_per_sweep * FLOP_PER_EVAL / 4.0
+    achieved = flops_per_launch / (per_launch_ms / 1e3) / 1e12
+    h = source_hash()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": (f"large_L64: [0,64]^2, 127x127=16129 subdomains, grid 2049x2049, "
+                                "SDNet 6x128 tanh (Xavier seed 2), 8-mode harmonic BC seed 2") if args.L == 64
+                   else f"profiling case L={args.L} (not the benchmark workload)",
+                   "schedule": "multiplicative 4-colour", "step": "one sweep + FP64 delta/residual",
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "evals_per_step": evals_per_sweep * world,
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "sweeps_per_s": world * args.steps / total_s,
+        "fp32": {"value": fp32_value, "unit": UNIT, "ms_per_step": sum(ms32) / k32 if k32 else None,
+                 "speedup_bf16_over_fp32": value / world / fp32_value if fp32_value else None},
+        "err_vs_oracle_bf16_sweep": err,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "gpu_launches": launches,
+        "roofline": {"kernel": "mlp_bf16_kernel<128,5>", "bound": "tensor", "achieved": achieved,
+                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "peak_source": f"{peak_src} bf16_tflops_sustained",
+                     "traffic": NCU_TRAFFIC.get(h), "per_launch_ms": per_launch_ms,
+                     "flops_per_launch": flops_per_launch},
+        "clocks": clocks,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = {"value": cpu["value"], "unit": UNIT, "cores": cpu["threads"], "kind": "oracle",
+                                "sample": f"{cpu['subdomains']} whole subdomains of colour 0 of the same grid "
+                                          f"(gather + SDNet on 961 points + write), FP64 NumPy, "
+                                          f"{cpu['seconds']:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

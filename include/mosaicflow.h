@@ -71,11 +71,17 @@ typedef struct {
   int colours;     /* bitmask of colours applied each sweep, in order 0..3; 0 means all */
   double eps;      /* stop once delta < eps (eps <= 0: run all n_sweeps, no mid-run sync) */
   int check_every; /* delta computed after every check_every-th sweep and the last (>= 1) */
+  int profile;     /* nonzero: time each phase with CUDA events recorded on `stream` */
 } mf_sweep_opts;
 
 typedef struct {
-  int sweeps_done; /* sweeps applied */
-  double delta;    /* delta of the last checked sweep (Algorithm 2), -1 if none checked */
+  int sweeps_done;     /* sweeps applied */
+  double delta;        /* delta of the last checked sweep (Algorithm 2), -1 if none checked */
+  int kernel_launches; /* kernels this call launched */
+  int mlp_launches;    /* of which SDNet (gather-fed MLP + scatter) kernels */
+  double ms_gather;    /* profile only: summed event time of the boundary-gather kernels */
+  double ms_mlp;       /* profile only: summed event time of the SDNet + scatter kernels */
+  double ms_reduce;    /* profile only: summed event time of snapshot copies and reductions */
 } mf_sweep_result;
 
 /* Message describing the calling thread's most recent failed call ("" if none). */

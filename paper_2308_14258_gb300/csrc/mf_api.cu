@@ -31,6 +31,7 @@ struct mf_grid {
   int* status = nullptr;    // kernel status word
   double* h_out = nullptr;  // pinned host mirror of out (16 doubles)
   int* h_status = nullptr;  // pinned host mirror of status
+  std::vector<cudaEvent_t> events;  // profiling events, grown on demand
 };
 
 namespace {
@@ -88,6 +89,39 @@ mf::ColourGeom colour_geom(const mf_grid* g, int c) {
 }
 
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Phase timer: consecutive events on the launching stream; each interval is charged to
+// the phase named when its closing event was recorded.
+struct PhaseTimer {
+  mf_grid* g;
+  cudaStream_t st;
+  bool on;
+  size_t n = 0;
+  std::vector<int> phase;  // phase of interval i (between event i and i+1)
+  cudaError_t mark(int next_phase_of_previous) {
+    if (!on) return cudaSuccess;
+    if (n == g->events.size()) {
+      cudaEvent_t ev;
+      cudaError_t e = cudaEventCreate(&ev);
+      if (e != cudaSuccess) return e;
+      g->events.push_back(ev);
+    }
+    if (n > 0) phase.push_back(next_phase_of_previous);
+    return cudaEventRecord(g->events[n++], st);
+  }
+  cudaError_t totals(double ms[3]) {
+    ms[0] = ms[1] = ms[2] = 0.0;
+    if (!on) return cudaSuccess;
+    for (size_t i = 0; i + 1 < n; ++i) {
+      float t = 0.f;
+      cudaError_t e = cudaEventElapsedTime(&t, g->events[i], g->events[i + 1]);
+      if (e != cudaSuccess) return e;
+      ms[phase[i]] += t;
+    }
+    return cudaSuccess;
+  }
+};
+enum { kPhaseGather = 0, kPhaseMlp = 1, kPhaseReduce = 2 };
 
 }  // namespace
 
@@ -197,6 +231,7 @@ mf_status mf_destroy_grid(mf_grid* g) {
   cudaFree(g->status);
   cudaFreeHost(g->h_out);
   cudaFreeHost(g->h_status);
+  for (cudaEvent_t ev : g->events) cudaEventDestroy(ev);
   delete g;
   return MF_OK;
 }
@@ -279,16 +314,16 @@ mf_status mf_sweep(mf_grid* g, const mf_sdnet* net, const mf_sweep_opts* o, mf_s
   if (o->precision == MF_PREC_BF16 && !mf::bf16_supported(net->d))
     return fail(MF_ERR_UNSUPPORTED, "mf_sweep: BF16 path needs 1..5 hidden layers");
   if (net->device != g->device) return fail(MF_ERR_INVALID_ARG, "mf_sweep: grid and SDNet on different devices");
-  if (res) {
-    res->sweeps_done = 0;
-    res->delta = -1.0;
-  }
+  if (res) *res = mf_sweep_result{0, -1.0, 0, 0, 0.0, 0.0, 0.0};
   MF_CUDA(cudaSetDevice(g->device), "mf_sweep: cudaSetDevice");
   cudaStream_t st = as_stream(stream);
   const int mask = o->colours == 0 ? 15 : o->colours;
   const bool additive = o->schedule == MF_SCHEDULE_ADDITIVE;
   const size_t bytes = (size_t)g->nx * g->ny * sizeof(float);
+  PhaseTimer pt{g, st, o->profile != 0};
+  int launches = 0, mlp_launches = 0;
   MF_CUDA(cudaMemsetAsync(g->status, 0, sizeof(int), st), "mf_sweep: reset status");
+  MF_CUDA(pt.mark(kPhaseReduce), "mf_sweep: event");
 
   int done = 0;
   bool checked = false;
@@ -296,20 +331,30 @@ mf_status mf_sweep(mf_grid* g, const mf_sdnet* net, const mf_sweep_opts* o, mf_s
     const bool check = ((k + 1) % o->check_every == 0) || (k + 1 == o->n_sweeps);
     if (check || additive)
       MF_CUDA(cudaMemcpyAsync(g->prev, g->u, bytes, cudaMemcpyDeviceToDevice, st), "mf_sweep: snapshot");
-    if (additive) MF_CUDA(mf::launch_zero_interior(g->u, g->nx, g->ny, st), "mf_sweep: zero interior");
+    if (additive) {
+      MF_CUDA(mf::launch_zero_interior(g->u, g->nx, g->ny, st), "mf_sweep: zero interior");
+      ++launches;
+    }
+    MF_CUDA(pt.mark(kPhaseReduce), "mf_sweep: event");
     for (int c = 0; c < 4; ++c) {
       if (!((mask >> c) & 1)) continue;
       const mf::ColourGeom cg = colour_geom(g, c);
       if (cg.n_c == 0) continue;
       MF_CUDA(mf::launch_gather_boundary(additive ? g->prev : g->u, cg, net->d, g->B, st), "mf_sweep: gather");
+      MF_CUDA(pt.mark(kPhaseGather), "mf_sweep: event");
       if (o->precision == MF_PREC_BF16)
         MF_CUDA(mf::launch_mlp_bf16(g->B, cg, net->d, g->u, additive ? 1 : 0, g->status, st), "mf_sweep: bf16 mlp");
       else
         MF_CUDA(mf::launch_mlp_fp32(g->B, cg, net->d, g->u, additive ? 1 : 0, st), "mf_sweep: fp32 mlp");
+      MF_CUDA(pt.mark(kPhaseMlp), "mf_sweep: event");
+      launches += 2;
+      mlp_launches += 1;
     }
     done = k + 1;
     if (check) {
       MF_CUDA(mf::launch_reduce(g->u, g->prev, g->nx, g->ny, g->partial, g->out, st), "mf_sweep: reduce");
+      MF_CUDA(pt.mark(kPhaseReduce), "mf_sweep: event");
+      launches += 2;
       checked = true;
       if (o->eps > 0.0) {
         MF_CUDA(cudaMemcpyAsync(g->h_out, g->out, 5 * sizeof(double), cudaMemcpyDeviceToHost, st), "mf_sweep: read delta");
@@ -327,9 +372,16 @@ mf_status mf_sweep(mf_grid* g, const mf_sdnet* net, const mf_sweep_opts* o, mf_s
   MF_CUDA(cudaMemcpyAsync(g->h_status, g->status, sizeof(int), cudaMemcpyDeviceToHost, st), "mf_sweep: read status");
   MF_CUDA(cudaStreamSynchronize(st), "mf_sweep: synchronize");
   if (*g->h_status != mf::kDevErrNone) return fail(MF_ERR_TIMEOUT, "mf_sweep: a kernel wait timed out");
+  double ms[3];
+  MF_CUDA(pt.totals(ms), "mf_sweep: event timing");
   if (res) {
     res->sweeps_done = done;
     res->delta = checked ? g->h_out[4] : -1.0;
+    res->kernel_launches = launches;
+    res->mlp_launches = mlp_launches;
+    res->ms_gather = ms[kPhaseGather];
+    res->ms_mlp = ms[kPhaseMlp];
+    res->ms_reduce = ms[kPhaseReduce];
   }
   if (checked && !std::isfinite(g->h_out[4])) return fail(MF_ERR_DIVERGED, "mf_sweep: delta is not finite");
   return MF_OK;

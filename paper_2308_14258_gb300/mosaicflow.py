@@ -48,11 +48,14 @@ class GridDesc(C.Structure):
 
 class SweepOpts(C.Structure):
     _fields_ = [("n_sweeps", C.c_int), ("schedule", C.c_int), ("precision", C.c_int),
-                ("colours", C.c_int), ("eps", C.c_double), ("check_every", C.c_int)]
+                ("colours", C.c_int), ("eps", C.c_double), ("check_every", C.c_int),
+                ("profile", C.c_int)]
 
 
 class SweepResult(C.Structure):
-    _fields_ = [("sweeps_done", C.c_int), ("delta", C.c_double)]
+    _fields_ = [("sweeps_done", C.c_int), ("delta", C.c_double), ("kernel_launches", C.c_int),
+                ("mlp_launches", C.c_int), ("ms_gather", C.c_double), ("ms_mlp", C.c_double),
+                ("ms_reduce", C.c_double)]
 
 
 _lib = None
@@ -135,6 +138,11 @@ class SDNet:
 class SweepOutcome:
     sweeps_done: int
     delta: float
+    kernel_launches: int = 0
+    mlp_launches: int = 0
+    ms_gather: float = 0.0
+    ms_mlp: float = 0.0
+    ms_reduce: float = 0.0
 
 
 class Grid:
@@ -176,11 +184,14 @@ class Grid:
         return dst
 
     def sweep(self, net: SDNet, n_sweeps: int = 1, schedule: str = "M", precision: str = "fp32",
-              colours: int = 0, eps: float = 0.0, check_every: int = 1, stream=None) -> SweepOutcome:
-        opts = SweepOpts(n_sweeps, SCHEDULE[schedule], PREC[precision], colours, eps, check_every)
+              colours: int = 0, eps: float = 0.0, check_every: int = 1, stream=None,
+              profile: bool = False) -> SweepOutcome:
+        opts = SweepOpts(n_sweeps, SCHEDULE[schedule], PREC[precision], colours, eps, check_every,
+                         1 if profile else 0)
         res = SweepResult()
         _check(load().mf_sweep(self._h, net._h, C.byref(opts), C.byref(res), _stream_ptr(stream)))
-        return SweepOutcome(res.sweeps_done, res.delta)
+        return SweepOutcome(res.sweeps_done, res.delta, res.kernel_launches, res.mlp_launches,
+                            res.ms_gather, res.ms_mlp, res.ms_reduce)
 
     def residual(self, stream=None):
         mx, rms = C.c_double(), C.c_double()
