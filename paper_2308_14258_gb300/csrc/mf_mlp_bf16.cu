@@ -11,17 +11,13 @@
 // prediction to its grid point.
 //
 // Persistent CTA per SM, 18 warps:
-//   warps 0-15 epilogue: warp w owns TMEM lanes / tile rows 32(w mod 4)..+31 and output
-//              columns (w/4)*H/4..+H/4-1, and serves the two tile slots in alternation
-//   warp 16    TMEM allocation; lane 0 loads the weights (bulk async copy) and issues
-//              the MMAs of slot 0
-//   warp 17    lane 0 issues the MMAs of slot 1
-// Each issuing lane blocks on its own slot's barriers, and its tcgen05.commit tracks
-// exactly its slot's MMAs, so the two slots run independently and one slot's epilogue
-// overlaps the other slot's MMAs.
+//   warps 0-15  epilogue: warp w serves tile slot w/8, column member (w/4) mod 2 and TMEM
+//               lanes / tile rows 32(w mod 4)..+31
+//   warps 16-17 lane 0 issues the MMAs of slot w-16; warp 16 also allocates TMEM and
+//               loads the weights (bulk async copy)
 // Shared memory: all hidden weight matrices resident (n_hidden x H x H BF16) plus one
-// 128 x H BF16 activation tile per slot, all in the 128-byte-swizzled K-major layout
-// the MMA descriptors name. TMEM: H FP32 columns per slot.
+// 128 x H BF16 activation tile per slot, in the 128-byte-swizzled K-major layout the MMA
+// descriptors name. TMEM: two H-column FP32 accumulators per slot.
 //
 // Every mbarrier wait is bounded (about one second of %globaltimer); a wait that gives
 // up records kDevErrTimeout in the status word, raises a CTA-wide abort flag so the
@@ -36,7 +32,7 @@ namespace mf {
 namespace {
 
 constexpr int kMaxHidden = 5;
-constexpr int kEpiWarps = 16;                     // 4 row quadrants x 4 column quarters
+constexpr int kEpiWarps = 16;                     // 2 tile slots x 2 column halves x 4 row quadrants
 constexpr int kThreadsBf16 = (kEpiWarps + 2) * 32;  // + one MMA-issuing warp per slot
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s
 
@@ -134,11 +130,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
         "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
       : "r"(taddr));
 }
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* v) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-               : "r"(taddr));
-}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
@@ -230,31 +221,34 @@ __device__ __forceinline__ bool wait_warp(uint32_t bar, uint32_t parity, volatil
 
 // ---------------------------------------------------------------- kernel
 //
-// Scheduling. The 16 epilogue warps serve one tile slot at a time and alternate:
-// epilogue phase m of slot 0, then phase m of slot 1, then phase m+1 of slot 0, ...
-// (phase 0 is the first layer, phase m the output of hidden layer m). Warp w owns TMEM
-// lanes / tile rows 32(w mod 4)..+31 and columns (w/4)*H/4 .. +H/4-1, so each SM
-// sub-partition runs four warps of the current phase. A slot's MMAs for layer m+1 are
-// issued as soon as its phase m has written the activations and run while the warps
-// work on the other slot, so the tensor core and the MUFU (tanh) unit overlap without
-// any cross-slot signal: the alternation is just program order. Accumulators are
-// double-buffered per slot in TMEM (layer parity picks the buffer) because the MMAs of
-// layer m+1 start on the first column quarter while other warps still read layer m.
+// Scheduling. Two tiles are in flight per SM (slots 0 and 1), each with eight epilogue
+// warps and one MMA-issuing thread. The epilogue (tanh on the MUFU unit) is the
+// bottleneck and each tile's layers are strictly serial (MMA -> epilogue -> MMA), so
+// the slots take turns: epilogue phase n of slot 1 runs after phase n of slot 0, and
+// phase n of slot 0 after phase n-1 of slot 1 (phase 0 = first layer, phase m = hidden
+// layer m), handed over through two token mbarriers. While one slot's warps own the
+// MUFU, the other slot's MMAs run. Left to themselves the slots fall into step (fair
+// sharing lets a lagging slot catch up) and then both wait on their MMAs together.
+// Within a phase each warp pair first writes K half 0, signals it, then K half 1, so the
+// next layer's first MMAs start before the phase ends; accumulators are therefore
+// double-buffered per slot in TMEM (layer parity picks the buffer). All waits on this
+// path spin (see wait_spin): a suspended wait wakes hundreds of cycles late.
 
-constexpr int kQuarters = 4;
+constexpr int kSlots = 2;
 
 template <int H, int NH>
 struct Bf16Cfg {
-  static constexpr int kGW = H / kQuarters;                         // columns per warp (one K quarter)
-  static constexpr int kKStepsGroup = kGW / 16;                     // K=16 steps per quarter
+  static constexpr int kHH = H / 2;                                 // K half
+  static constexpr int kCW = H / 4;                                 // columns per warp per K half
+  static constexpr int kKStepsHalf = kHH / 16;                      // K=16 steps per K half
   static constexpr uint32_t kWBytes = (uint32_t)NH * H * H * 2;     // resident hidden weights
   static constexpr uint32_t kABytes = (uint32_t)kTileRows * H * 2;  // one activation tile
   static constexpr uint32_t kTmemCols = 4 * H;                      // 2 slots x 2 buffers x H
-  static constexpr uint32_t kBarBytes = 192;
-  static constexpr uint32_t kSumBytes = 3 * kTileRows * 4 + 64;     // output partial sums + flags
+  static constexpr uint32_t kBarBytes = 128;
+  static constexpr uint32_t kSumBytes = 2 * kTileRows * 4 + 64;     // output half-sums + pair flags
   static constexpr size_t kSmem = 1024 + kWBytes + 2 * kABytes + kBarBytes + kSumBytes;
   static constexpr uint32_t kIdesc = idesc_bf16(kTileRows, H);
-  static_assert(kKStepsGroup >= 1 && kGW % 8 == 0, "quarter geometry");
+  static_assert(kCW % 8 == 0 && kKStepsHalf >= 1, "half geometry");
 };
 
 // Byte offset, within a K-major SW128 operand of `rows` rows, of K step `ks` (16 elements).
@@ -271,8 +265,9 @@ __device__ __forceinline__ uint64_t desc_add(uint64_t d, uint32_t bytes) {
   return r;
 }
 
+// D (TMEM) += A (shared memory) x B (shared memory)
 template <uint32_t ACC>
-__device__ __forceinline__ void mma_bf16_c(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc) {
+__device__ __forceinline__ void mma_ss(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
@@ -281,21 +276,21 @@ __device__ __forceinline__ void mma_bf16_c(uint32_t d_tmem, uint64_t a_desc, uin
       : "memory");
 }
 
-__device__ __forceinline__ bool slot_has_tile(const Bf16Params& P, int round, int slot) {
-  return ((round * (int)gridDim.x + (int)blockIdx.x) * 2 + slot) < P.n_tiles;
+__device__ __forceinline__ int slot_tile(const Bf16Params& P, int round, int slot) {
+  return (round * (int)gridDim.x + (int)blockIdx.x) * kSlots + slot;
 }
 
-// MMA issue for one slot (a single thread): per tile and hidden layer m, for each K
-// quarter the quarter's K steps once its activations are written, then one commit for
-// the whole accumulator. Every descriptor is a base plus a compile-time offset.
+// MMA issue for one slot (a single thread): per tile and hidden layer m, the K steps of
+// K half 0 once that half of the activations is written, then K half 1, then one commit.
 template <int H, int NH>
 __device__ __forceinline__ void mma_issuer(const Bf16Params& P, int s, uint32_t tmem, uint32_t sA, uint32_t sW,
-                                           uint32_t bar_act, uint32_t bar_acc, volatile int* abort_flag) {
+                                           uint32_t bar_act0, uint32_t bar_act1, uint32_t bar_acc,
+                                           volatile int* abort_flag) {
   using C = Bf16Cfg<H, NH>;
   const uint32_t acc0 = tmem + (uint32_t)(s * 2 * H);
-  uint32_t ph = 0u;  // bit g: phase parity of quarter g's barrier
+  uint32_t ph0 = 0u, ph1 = 0u;
   bool ok = true;
-  for (int k = 0; ok && slot_has_tile(P, k, s); ++k) {
+  for (int k = 0; ok && slot_tile(P, k, s) < P.n_tiles; ++k) {
     // rebuilt every tile (an opaque copy of the base) so the compiler does not hoist all
     // NH x H/16 descriptors out of the loop into registers
     uint32_t a_base = sA + (uint32_t)s * C::kABytes, w_base = sW;
@@ -306,18 +301,18 @@ __device__ __forceinline__ void mma_issuer(const Bf16Params& P, int s, uint32_t 
     for (int m = 1; m <= NH; ++m) {
       const uint32_t acc = acc0 + (uint32_t)((m & 1) * H);
 #pragma unroll
-      for (int g = 0; g < kQuarters; ++g) {
-        ok = wait_spin(bar_act + 8u * (uint32_t)g, (ph >> g) & 1u, abort_flag, P.status);
+      for (int h = 0; h < 2; ++h) {
+        ok = wait_spin(h == 0 ? bar_act0 : bar_act1, h == 0 ? ph0 : ph1, abort_flag, P.status);
         if (!ok) break;
-        ph ^= 1u << g;
+        if (h == 0) ph0 ^= 1u; else ph1 ^= 1u;
         tc_fence_after();
 #pragma unroll
-        for (int kk = 0; kk < C::kKStepsGroup; ++kk) {
-          const int ks = g * C::kKStepsGroup + kk;
+        for (int kk = 0; kk < C::kKStepsHalf; ++kk) {
+          const int ks = h * C::kKStepsHalf + kk;
           const uint64_t ad = desc_add(a0, kstep_off(kTileRows, ks));
           const uint64_t bd = desc_add(w0, (uint32_t)(m - 1) * H * H * 2 + kstep_off(H, ks));
-          if (ks == 0) mma_bf16_c<0>(acc, ad, bd, C::kIdesc);
-          else mma_bf16_c<1>(acc, ad, bd, C::kIdesc);
+          if (ks == 0) mma_ss<0>(acc, ad, bd, C::kIdesc);
+          else mma_ss<1>(acc, ad, bd, C::kIdesc);
         }
       }
       if (!ok) break;
@@ -326,135 +321,143 @@ __device__ __forceinline__ void mma_issuer(const Bf16Params& P, int s, uint32_t 
   }
 }
 
-template <int N>
-__device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t* v) {
-  if constexpr (N == 32) tmem_ld32(taddr, *reinterpret_cast<uint32_t(*)[32]>(v));
-  else if constexpr (N == 16) tmem_ld16(taddr, v);
-  else tmem_ld8(taddr, v);
-}
-
-// Epilogue of warp (row quadrant q, column quarter G): TMEM lanes 32q..32q+31, columns
-// G*H/4 .. G*H/4 + H/4 - 1, for both tile slots in alternation.
-template <int H, int NH, int G>
-__device__ __forceinline__ void epilogue(const Bf16Params& P, int q, int lane, uint32_t tmem, uint32_t sA,
-                                         uint32_t bar_act_base, uint32_t bar_acc_base, float* part,
-                                         volatile int* quad_ok, volatile int* abort_flag) {
+// Epilogue of one warp: slot s, row quadrant q (TMEM lanes / tile rows 32q..32q+31),
+// member JJ of the column pair (in K half h it owns columns h*H/2 + JJ*H/4 .. + H/4 - 1).
+template <int H, int NH, int JJ>
+__device__ __forceinline__ void epilogue(const Bf16Params& P, int s, int q, int lane, uint32_t tmem, uint32_t sA,
+                                         uint32_t bar_act0, uint32_t bar_act1, uint32_t bar_acc, uint32_t tok_wait,
+                                         uint32_t tok_give, float* half_sum, volatile int* pair_ok,
+                                         volatile int* abort_flag) {
   using C = Bf16Cfg<H, NH>;
-  constexpr int GW = C::kGW;
-  constexpr int c0 = G * GW;  // first column of this warp
+  constexpr int HH = C::kHH, CW = C::kCW;
   const int rloc = 32 * q + lane;
+  const uint32_t lane_off = (uint32_t)(32 * q) << 16;
+  const uint32_t a_row = sA + (uint32_t)s * C::kABytes + (uint32_t)rloc * 128u;
   const uint32_t swz = (uint32_t)(rloc & 7) << 4;
-  const int named = 1 + q;    // named barrier of the four column-quarter warps of these rows
-  uint32_t acc_ph = 0u;       // bit s: phase parity of slot s's accumulator barrier
+  const int named = 1 + s * 4 + q;  // named barrier of the warp pair of these rows
+  uint32_t acc_ph = 0u, tok_ph = 0u;
   bool ok = true;
 
-  auto a_row = [&](int s) { return sA + (uint32_t)s * C::kABytes + (uint32_t)rloc * 128u; };
-  auto st_cols = [&](int s, const uint32_t* pk) {  // this warp's GW columns of row rloc
+  auto put = [&](int c0, const uint32_t* pk) {  // CW columns from c0 of this row
 #pragma unroll
-    for (int i = 0; i < GW / 8; ++i) {
-      const int c = c0 / 8 + i;
-      const uint32_t addr = a_row(s) + (uint32_t)(c >> 3) * (kTileRows * 128u) + (((uint32_t)(c & 7) << 4) ^ swz);
+    for (int i = 0; i < CW / 8; ++i) {
+      const int ch = c0 / 8 + i;  // 16-byte chunk along K
+      const uint32_t addr = a_row + (uint32_t)(ch >> 3) * (kTileRows * 128u) + (((uint32_t)(ch & 7) << 4) ^ swz);
       st_shared_v4(addr, pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
     }
   };
-  auto signal = [&](int s) {  // this warp's quarter of slot s's activations is written
+  auto signal = [&](uint32_t b) {  // this warp's share of a K half is written
     fence_proxy_async_smem();
     __syncwarp();
-    if (lane == 0) mbar_arrive(bar_act_base + 8u * (uint32_t)(kQuarters * s + G));
+    if (lane == 0) mbar_arrive(b);
+  };
+  auto give_turn = [&]() {
+    __syncwarp();
+    if (lane == 0) mbar_arrive(tok_give);
+  };
+  // wait for the other slot's turn to end: slot 1 phase n needs slot 0 phase n; slot 0
+  // phase n needs slot 1 phase n-1 when that phase exists
+  auto take_turn = [&](int k, int e) -> bool {
+    const bool need = (s == 1) || (e > 0 ? slot_tile(P, k, 1) < P.n_tiles
+                                         : (k > 0 && slot_tile(P, k - 1, 1) < P.n_tiles));
+    if (!need) return true;
+    const bool r = wait_warp(tok_wait, tok_ph, abort_flag, P.status);
+    tok_ph ^= 1u;
+    return r;
   };
 
-  for (int k = 0; ok && slot_has_tile(P, k, 0); ++k) {
-    const int nslots = slot_has_tile(P, k, 1) ? 2 : 1;
-    float uacc[2] = {0.f, 0.f};
-    // row of slot s in this round (clamped to the last row for the ragged tail)
-    auto row_of = [&](int s) { return ((k * (int)gridDim.x + (int)blockIdx.x) * 2 + s) * kTileRows + rloc; };
+  for (int k = 0; ok; ++k) {
+    const int tile = slot_tile(P, k, s);
+    if (tile >= P.n_tiles) break;
+    const int row = tile * kTileRows + rloc;
+    const bool valid = row < P.n_rows;
+    const RowSite site = row_site(P.g, valid ? row : P.n_rows - 1);
+    const float x = (float)(site.px + 1) * (1.0f / kPts), y = (float)(site.py + 1) * (1.0f / kPts);
+    const float* Bs = P.B + (size_t)site.s * H;
 
-    // phase 0 (first layer, Eq. 8): FP32 sum B[s] + W2 x, rounded to BF16, tanh
+    // phase 0: first layer (Eq. 8), FP32 sum B[s] + W2 x, rounded to BF16, tanh
+    {
+      float2 bb[CW / 2];  // half 0 is loaded before the turn is taken, overlapping the wait
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      if (s >= nslots) break;
-      const RowSite site = row_site(P.g, min(row_of(s), P.n_rows - 1));
-      const float x = (float)(site.px + 1) * (1.0f / kPts), y = (float)(site.py + 1) * (1.0f / kPts);
-      const float2* Bs = reinterpret_cast<const float2*>(P.B + (size_t)site.s * H + c0);
-      float2 bb[GW / 2];
+      for (int i = 0; i < CW / 2; ++i) bb[i] = __ldg(reinterpret_cast<const float2*>(Bs + JJ * CW) + i);
+      ok = take_turn(k, 0);
+      if (ok) {
 #pragma unroll
-      for (int i = 0; i < GW / 2; ++i) bb[i] = __ldg(Bs + i);
-      uint32_t pk[GW / 2];
+        for (int h = 0; h < 2; ++h) {
+          const int c0 = h * HH + JJ * CW;
+          if (h == 1) {
 #pragma unroll
-      for (int i = 0; i < GW / 2; ++i) {
-        const int col = c0 + 2 * i;
-        const float a0 = fmaf(P.w2[col][1], y, fmaf(P.w2[col][0], x, bb[i].x));
-        const float a1 = fmaf(P.w2[col + 1][1], y, fmaf(P.w2[col + 1][0], x, bb[i].y));
-        pk[i] = tanh_bf16x2(pack_bf16x2(a0, a1));
+            for (int i = 0; i < CW / 2; ++i) bb[i] = __ldg(reinterpret_cast<const float2*>(Bs + c0) + i);
+          }
+          uint32_t pk[CW / 2];
+#pragma unroll
+          for (int i = 0; i < CW / 2; ++i) {
+            const int col = c0 + 2 * i;
+            const float a0 = fmaf(P.w2[col][1], y, fmaf(P.w2[col][0], x, bb[i].x));
+            const float a1 = fmaf(P.w2[col + 1][1], y, fmaf(P.w2[col + 1][0], x, bb[i].y));
+            pk[i] = tanh_bf16x2(pack_bf16x2(a0, a1));
+          }
+          put(c0, pk);
+          signal(h == 0 ? bar_act0 : bar_act1);
+        }
+        give_turn();
       }
-      st_cols(s, pk);
-      signal(s);
     }
 
-    // phases 1..NH
+    float uacc = 0.f;
 #pragma unroll
     for (int m = 1; m <= NH; ++m) {
+      if (!ok) break;
+      ok = wait_warp(bar_acc, acc_ph, abort_flag, P.status);
+      if (!ok) break;
+      acc_ph ^= 1u;
+      ok = take_turn(k, m);
+      if (!ok) break;
+      tc_fence_after();
+      const uint32_t t_buf = tmem + (uint32_t)(s * 2 * H + (m & 1) * H) + lane_off;
 #pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        if (s >= nslots || !ok) break;
-        ok = wait_warp(bar_acc_base + 8u * (uint32_t)s, (acc_ph >> s) & 1u, abort_flag, P.status);
-        if (!ok) break;
-        acc_ph ^= 1u << s;
-        tc_fence_after();
-        uint32_t pk[GW / 2];
-        const uint32_t taddr = tmem + (uint32_t)(s * 2 * H + (m & 1) * H + c0) + ((uint32_t)(32 * q) << 16);
+      for (int h = 0; h < 2; ++h) {
+        const int c0 = h * HH + JJ * CW;
+        uint32_t v[CW];
+        if constexpr (CW == 32) tmem_ld32(t_buf + (uint32_t)c0, *reinterpret_cast<uint32_t(*)[32]>(v));
+        else tmem_ld16(t_buf + (uint32_t)c0, v);
+        tmem_wait_ld();
+        uint32_t pk[CW / 2];
 #pragma unroll
-        for (int h = 0; h < GW / 16 || h == 0; ++h) {  // 16-column pieces keep registers low
-          constexpr int PW = GW < 16 ? GW : 16;
-          uint32_t v[PW];
-          tmem_ld<PW>(taddr + (uint32_t)(h * PW), v);
-          tmem_wait_ld();
-#pragma unroll
-          for (int i = 0; i < PW / 2; ++i) {
-            const int col = c0 + h * PW + 2 * i;
-            const float a0 = __uint_as_float(v[2 * i]) + P.bias[m - 1][col];
-            const float a1 = __uint_as_float(v[2 * i + 1]) + P.bias[m - 1][col + 1];
-            pk[h * PW / 2 + i] = tanh_bf16x2(pack_bf16x2(a0, a1));
-          }
+        for (int i = 0; i < CW / 2; ++i) {
+          const float a0 = __uint_as_float(v[2 * i]) + P.bias[m - 1][c0 + 2 * i];
+          const float a1 = __uint_as_float(v[2 * i + 1]) + P.bias[m - 1][c0 + 2 * i + 1];
+          pk[i] = tanh_bf16x2(pack_bf16x2(a0, a1));
         }
-        tc_fence_before();
+        if (h == 1) tc_fence_before();
         if (m < NH) {
-          st_cols(s, pk);
-          signal(s);
+          put(c0, pk);
+          signal(h == 0 ? bar_act0 : bar_act1);
         } else {
-          float u = 0.f;
 #pragma unroll
-          for (int i = 0; i < GW / 2; ++i) {
-            u = fmaf(bf16_lo(pk[i]), P.wout[c0 + 2 * i], u);
-            u = fmaf(bf16_hi(pk[i]), P.wout[c0 + 2 * i + 1], u);
+          for (int i = 0; i < CW / 2; ++i) {
+            uacc = fmaf(bf16_lo(pk[i]), P.wout[c0 + 2 * i], uacc);
+            uacc = fmaf(bf16_hi(pk[i]), P.wout[c0 + 2 * i + 1], uacc);
           }
-          uacc[s] = u;
         }
       }
+      give_turn();
     }
-
-    // output: the four column-quarter warps of these rows add their partial sums (in a
-    // fixed order) and agree on whether to continue, so no warp leaves while the others
-    // wait at the named barrier
+    // output: partner warps combine their partial sums; the continue decision is taken
+    // jointly so that neither warp of the pair can leave while the other waits
+    if (JJ == 1) half_sum[s * kTileRows + rloc] = uacc;
     const bool ok_warp = __all_sync(0xffffffffu, ok);
-    if (lane == 0) quad_ok[q * 4 + G] = ok_warp ? 1 : 0;
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      if (G > 0) part[(G - 1) * kTileRows + rloc] = uacc[s];
-      named_barrier_sync(named, 128);
-      const bool ok_all = quad_ok[q * 4 + 0] && quad_ok[q * 4 + 1] && quad_ok[q * 4 + 2] && quad_ok[q * 4 + 3];
-      const int row = row_of(s);
-      if (G == 0 && ok_all && s < nslots && row < P.n_rows) {
-        const RowSite site = row_site(P.g, row);
-        const float val = ((uacc[s] + part[rloc]) + part[kTileRows + rloc]) + part[2 * kTileRows + rloc] + P.bout;
-        if (P.additive)
-          P.u[site.idx] += cover_weight(P.g, site.ix, site.iy) * val;
-        else
-          P.u[site.idx] = val;
-      }
-      named_barrier_sync(named, 128);
-      ok = ok_all;
+    if (lane == 0) pair_ok[(s * 4 + q) * 2 + JJ] = ok_warp ? 1 : 0;
+    named_barrier_sync(named, 64);
+    ok = pair_ok[(s * 4 + q) * 2 + 0] && pair_ok[(s * 4 + q) * 2 + 1];
+    if (JJ == 0 && ok && valid) {
+      const float val = uacc + half_sum[s * kTileRows + rloc] + P.bout;
+      if (P.additive)
+        P.u[site.idx] += cover_weight(P.g, site.ix, site.iy) * val;
+      else
+        P.u[site.idx] = val;
     }
+    named_barrier_sync(named, 64);
   }
 }
 
@@ -468,20 +471,21 @@ __global__ void __launch_bounds__(kThreadsBf16, 1) mlp_bf16_kernel(const __grid_
   const uint32_t sW = base;
   const uint32_t sA = base + C::kWBytes;
   const uint32_t sBar = sA + 2 * C::kABytes;
-  // barriers: 0 weights loaded; 1 + 4*slot + g: quarter g of the slot's activations
-  // written (4 warp arrivals); 9 + slot: accumulator of the slot ready; 11 + slot: MMA
-  // drain of that slot's issuer
+  // barriers: 0 weights loaded; 1 + 2s + h: K half h of slot s's activations written
+  // (8 warp arrivals); 5 + s: slot s's accumulator ready; 7 + s: MMA drain of slot s's
+  // issuer; 9 + s: slot s may run its next epilogue phase (8 arrivals of the other slot)
   auto bar = [&](int i) { return sBar + 8u * (uint32_t)i; };
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(gen + C::kWBytes + 2 * C::kABytes + 160);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(gen + C::kWBytes + 2 * C::kABytes + 168);
-  float* part = reinterpret_cast<float*>(gen + C::kWBytes + 2 * C::kABytes + C::kBarBytes);  // [3][128]
-  volatile int* quad_ok = reinterpret_cast<volatile int*>(part + 3 * kTileRows);              // [4][4]
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(gen + C::kWBytes + 2 * C::kABytes + 96);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(gen + C::kWBytes + 2 * C::kABytes + 104);
+  float* half_sum = reinterpret_cast<float*>(gen + C::kWBytes + 2 * C::kABytes + C::kBarBytes);  // [2][128]
+  volatile int* pair_ok = reinterpret_cast<volatile int*>(half_sum + 2 * kTileRows);             // [2][4][2]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     mbar_init(bar(0), 1);
-    for (int i = 1; i <= 8; ++i) mbar_init(bar(i), 4);
-    for (int i = 9; i <= 12; ++i) mbar_init(bar(i), 1);
+    for (int i = 1; i <= 4; ++i) mbar_init(bar(i), 8);
+    for (int i = 5; i <= 8; ++i) mbar_init(bar(i), 1);
+    for (int i = 9; i <= 10; ++i) mbar_init(bar(i), 8);
     *abort_flag = 0;
     fence_barrier_init();
   }
@@ -505,20 +509,20 @@ __global__ void __launch_bounds__(kThreadsBf16, 1) mlp_bf16_kernel(const __grid_
           bulk_g2s(sW + (uint32_t)l * H * H * 2, P.wimg + (size_t)l * H * H * 2, H * H * 2, bar(0));
       }
       if (wait_bounded(bar(0), 0, abort_flag, P.status, true))
-        mma_issuer<H, NH>(P, s, tmem, sA, sW, bar(1 + 4 * s), bar(9 + s), abort_flag);
+        mma_issuer<H, NH>(P, s, tmem, sA, sW, bar(1 + 2 * s), bar(2 + 2 * s), bar(5 + s), abort_flag);
       // drain: every MMA this thread issued has completed before TMEM is released
-      mma_commit(bar(11 + s));
-      wait_bounded(bar(11 + s), 0, abort_flag, P.status, false);
+      mma_commit(bar(7 + s));
+      wait_bounded(bar(7 + s), 0, abort_flag, P.status, false);
     }
     __syncwarp();
   } else {
-    const int q = warp & 3, g = warp >> 2;
-    switch (g) {
-      case 0: epilogue<H, NH, 0>(P, q, lane, tmem, sA, bar(1), bar(9), part, quad_ok, abort_flag); break;
-      case 1: epilogue<H, NH, 1>(P, q, lane, tmem, sA, bar(1), bar(9), part, quad_ok, abort_flag); break;
-      case 2: epilogue<H, NH, 2>(P, q, lane, tmem, sA, bar(1), bar(9), part, quad_ok, abort_flag); break;
-      default: epilogue<H, NH, 3>(P, q, lane, tmem, sA, bar(1), bar(9), part, quad_ok, abort_flag); break;
-    }
+    const int s = warp >> 3, jj = (warp >> 2) & 1, q = warp & 3;
+    if (jj == 0)
+      epilogue<H, NH, 0>(P, s, q, lane, tmem, sA, bar(1 + 2 * s), bar(2 + 2 * s), bar(5 + s), bar(9 + s),
+                         bar(10 - s), half_sum, pair_ok, abort_flag);
+    else
+      epilogue<H, NH, 1>(P, s, q, lane, tmem, sA, bar(1 + 2 * s), bar(2 + 2 * s), bar(5 + s), bar(9 + s),
+                         bar(10 - s), half_sum, pair_ok, abort_flag);
   }
 
   tc_fence_before();
@@ -559,7 +563,7 @@ cudaError_t launch_t(const Bf16Params& p, cudaStream_t st) {
     if (per_sm > tmem_cap || per_sm < 1) return cudaErrorInvalidConfiguration;
     grid_cap = sms * per_sm;
   }
-  int grid = (p.n_tiles + 1) / 2;
+  int grid = (p.n_tiles + kSlots - 1) / kSlots;
   if (grid > grid_cap) grid = grid_cap;
   if (grid < 1) return cudaSuccess;
   mlp_bf16_kernel<H, NH><<<grid, kThreadsBf16, smem_bytes, st>>>(p);
