@@ -150,6 +150,26 @@ mf_status mf_synchronize(void* stream);
  * to the host doubles; synchronises `stream`. Either output pointer may be NULL. */
 mf_status mf_residual(const mf_grid* grid, double* max_abs, double* rms, void* stream);
 
+/* mf_sweep_noalloc -- the multiplicative sweep of mf_sweep (n_sweeps sweeps, all four
+ * colours, no early stop) for callers that must not allocate device memory during the
+ * call: code whose device memory belongs to another allocator's pool, and loops that
+ * cannot afford the device synchronisation a cudaMalloc/cudaFree implies. The paper
+ * has no counterpart; this is an interface convenience of this library.
+ * `u` is the caller's device grid (ny x nx FP32, row-major, boundary included), read
+ * and updated in place; `net` was loaded earlier with mf_load_sdnet on the current
+ * device; `precision` is MF_PREC_FP32 or MF_PREC_BF16. If `delta` is not NULL it
+ * receives delta of the last sweep (-1 when n_sweeps is 0). The call synchronises
+ * `stream` before returning.
+ * Memory: nothing is allocated. All scratch lives in one fixed array of about 4.7 MB
+ * that every GPU using this library holds until the process exits; grids are limited
+ * to 1 <= lx, ly <= 32 (larger sizes return MF_ERR_INVALID_ARG). The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress); make that first
+ * call before any stream capture. All calls share the one array, so calls whose work
+ * overlaps on the GPU (other streams, other host threads) race and must not be issued.
+ * Errors: as mf_sweep. */
+mf_status mf_sweep_noalloc(float* u, int lx, int ly, const mf_sdnet* net, int precision, int n_sweeps,
+                           double* delta, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

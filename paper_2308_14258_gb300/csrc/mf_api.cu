@@ -125,6 +125,15 @@ enum { kPhaseGather = 0, kPhaseMlp = 1, kPhaseReduce = 2 };
 
 }  // namespace
 
+namespace mf {
+// Internal accessors used by the allocation-free sweep (mf_noalloc.cu).
+const DevNet* devnet_of(const mf_sdnet* net, int* device) {
+  if (device) *device = net->device;
+  return &net->d;
+}
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace mf
+
 extern "C" {
 
 const char* mf_last_error(void) { return g_err.c_str(); }

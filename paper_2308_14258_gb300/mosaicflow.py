@@ -29,7 +29,7 @@ SCHEDULE = {"M": 0, "multiplicative": 0, "A": 1, "additive": 1}
 # Every exported symbol the header declares (checked by the CPU test suite).
 EXPORTS = ["mf_last_error", "mf_version", "mf_load_sdnet", "mf_free_sdnet", "mf_create_grid",
            "mf_destroy_grid", "mf_grid_dims", "mf_grid_upload", "mf_grid_download", "mf_sweep",
-           "mf_residual", "mf_synchronize"]
+           "mf_residual", "mf_synchronize", "mf_sweep_noalloc"]
 
 
 class MFError(RuntimeError):
@@ -87,6 +87,7 @@ def load(path: str | None = None) -> C.CDLL:
     lib.mf_sweep.argtypes = [vp, vp, C.POINTER(SweepOpts), C.POINTER(SweepResult), vp]
     lib.mf_residual.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
     lib.mf_synchronize.argtypes = [vp]
+    lib.mf_sweep_noalloc.argtypes = [vp, i, i, vp, i, i, C.POINTER(C.c_double), vp]
     for name in EXPORTS:
         if name not in ("mf_last_error", "mf_version"):
             getattr(lib, name).restype = i
@@ -197,6 +198,20 @@ class Grid:
         mx, rms = C.c_double(), C.c_double()
         _check(load().mf_residual(self._h, C.byref(mx), C.byref(rms), _stream_ptr(stream)))
         return mx.value, rms.value
+
+
+def sweep_noalloc(u, lx: int, ly: int, net: SDNet, n_sweeps: int = 1, precision: str = "fp32",
+                  stream=None) -> float:
+    """mf_sweep_noalloc on a caller-owned device grid `u` (a contiguous float32 CUDA
+    tensor of shape (32 ly + 1, 32 lx + 1)), updated in place; returns delta."""
+    ptr, on_dev, nbytes = _buffer(u)
+    if not on_dev:
+        raise TypeError("mf_sweep_noalloc needs a device grid")
+    if nbytes != (32 * lx + 1) * (32 * ly + 1) * 4:
+        raise ValueError("grid size mismatch")
+    d = C.c_double()
+    _check(load().mf_sweep_noalloc(ptr, lx, ly, net._h, PREC[precision], n_sweeps, C.byref(d), _stream_ptr(stream)))
+    return d.value
 
 
 def synchronize(stream=None):
