@@ -47,6 +47,7 @@ typedef int mf_status;
 
 #define MF_PREC_FP32 0  /* FP32 weights and activations, SIMT FMA, accurate tanh */
 #define MF_PREC_BF16 1  /* BF16 weights/activations on tcgen05 tensor cores, FP32 accumulate */
+#define MF_PREC_MIXED 2 /* BF16 sweeps until delta < eps_coarse, then FP32 refinement sweeps */
 
 #define MF_SCHEDULE_MULTIPLICATIVE 0 /* colours 0..3 in turn, each reads the latest grid */
 #define MF_SCHEDULE_ADDITIVE 1       /* all colours read the old grid; overlaps averaged */
@@ -72,6 +73,7 @@ typedef struct {
   double eps;      /* stop once delta < eps (eps <= 0: run all n_sweeps, no mid-run sync) */
   int check_every; /* delta computed after every check_every-th sweep and the last (>= 1) */
   int profile;     /* nonzero: time each phase with CUDA events recorded on `stream` */
+  double eps_coarse; /* MF_PREC_MIXED: switch from BF16 to FP32 once delta < eps_coarse (> 0) */
 } mf_sweep_opts;
 
 typedef struct {
@@ -82,6 +84,7 @@ typedef struct {
   double ms_gather;    /* profile only: summed event time of the boundary-gather kernels */
   double ms_mlp;       /* profile only: summed event time of the SDNet + scatter kernels */
   double ms_reduce;    /* profile only: summed event time of snapshot copies and reductions */
+  int sweeps_bf16;     /* of sweeps_done, sweeps run on the BF16 path */
 } mf_sweep_result;
 
 /* Message describing the calling thread's most recent failed call ("" if none). */
@@ -133,9 +136,12 @@ mf_status mf_grid_download(const mf_grid* grid, float* dst, int dst_on_device, v
  * colour read the grid as it was before the sweep and sets each interior point to
  * the average of the predictions of the subdomains that contain it.
  * After each checked sweep, delta = ||u_k - u_{k-1}||_2 / ||u_{k-1}||_2 over all grid
- * points is computed in FP64 (0/0 = 0). With eps > 0 the call synchronises `stream`
- * after each checked sweep and stops once delta < eps. The call always synchronises
- * `stream` before returning to fill `result` (which may be NULL).
+ * points is computed with FP64 accumulation (0/0 = 0). With eps > 0 the call
+ * synchronises `stream` after each checked sweep and stops once delta < eps. The call
+ * always synchronises `stream` before returning to fill `result` (which may be NULL).
+ * MF_PREC_MIXED is iterative refinement of the converged field: BF16 sweeps (checked
+ * every sweep) until delta < eps_coarse, then FP32 sweeps until delta < eps, both
+ * within the n_sweeps budget.
  * Errors: MF_ERR_INVALID_ARG (null handle/opts, bad option), MF_ERR_DIVERGED (delta
  * not finite; the grid holds the diverged state), MF_ERR_TIMEOUT, MF_ERR_CUDA. */
 mf_status mf_sweep(mf_grid* grid, const mf_sdnet* net, const mf_sweep_opts* opts,

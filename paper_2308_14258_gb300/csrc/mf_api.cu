@@ -315,15 +315,17 @@ mf_status mf_sweep(mf_grid* g, const mf_sdnet* net, const mf_sweep_opts* o, mf_s
   if (o->n_sweeps < 0) return fail(MF_ERR_INVALID_ARG, "mf_sweep: n_sweeps < 0");
   if (o->schedule != MF_SCHEDULE_MULTIPLICATIVE && o->schedule != MF_SCHEDULE_ADDITIVE)
     return fail(MF_ERR_INVALID_ARG, "mf_sweep: unknown schedule");
-  if (o->precision != MF_PREC_FP32 && o->precision != MF_PREC_BF16)
+  if (o->precision != MF_PREC_FP32 && o->precision != MF_PREC_BF16 && o->precision != MF_PREC_MIXED)
     return fail(MF_ERR_INVALID_ARG, "mf_sweep: unknown precision");
+  if (o->precision == MF_PREC_MIXED && !(o->eps_coarse > 0.0 && std::isfinite(o->eps_coarse)))
+    return fail(MF_ERR_INVALID_ARG, "mf_sweep: MF_PREC_MIXED needs eps_coarse > 0");
   if (o->colours < 0 || o->colours > 15) return fail(MF_ERR_INVALID_ARG, "mf_sweep: colours must be a 4-bit mask");
   if (o->check_every < 1) return fail(MF_ERR_INVALID_ARG, "mf_sweep: check_every must be >= 1");
   if (!std::isfinite(o->eps)) return fail(MF_ERR_INVALID_ARG, "mf_sweep: eps must be finite");
-  if (o->precision == MF_PREC_BF16 && !mf::bf16_supported(net->d))
+  if (o->precision != MF_PREC_FP32 && !mf::bf16_supported(net->d))
     return fail(MF_ERR_UNSUPPORTED, "mf_sweep: BF16 path needs 1..5 hidden layers");
   if (net->device != g->device) return fail(MF_ERR_INVALID_ARG, "mf_sweep: grid and SDNet on different devices");
-  if (res) *res = mf_sweep_result{0, -1.0, 0, 0, 0.0, 0.0, 0.0};
+  if (res) *res = mf_sweep_result{0, -1.0, 0, 0, 0.0, 0.0, 0.0, 0};
   MF_CUDA(cudaSetDevice(g->device), "mf_sweep: cudaSetDevice");
   cudaStream_t st = as_stream(stream);
   const int mask = o->colours == 0 ? 15 : o->colours;
@@ -334,10 +336,13 @@ mf_status mf_sweep(mf_grid* g, const mf_sdnet* net, const mf_sweep_opts* o, mf_s
   MF_CUDA(cudaMemsetAsync(g->status, 0, sizeof(int), st), "mf_sweep: reset status");
   MF_CUDA(pt.mark(kPhaseReduce), "mf_sweep: event");
 
-  int done = 0;
+  int done = 0, done_bf16 = 0;
   bool checked = false;
+  const bool mixed = o->precision == MF_PREC_MIXED;
+  bool coarse = mixed;  // mixed precision: still in the BF16 phase
   for (int k = 0; k < o->n_sweeps; ++k) {
-    const bool check = ((k + 1) % o->check_every == 0) || (k + 1 == o->n_sweeps);
+    const bool check = coarse || ((k + 1) % o->check_every == 0) || (k + 1 == o->n_sweeps);
+    const bool bf16 = mixed ? coarse : (o->precision == MF_PREC_BF16);
     if (check || additive)
       MF_CUDA(cudaMemcpyAsync(g->prev, g->u, bytes, cudaMemcpyDeviceToDevice, st), "mf_sweep: snapshot");
     if (additive) {
@@ -351,7 +356,7 @@ mf_status mf_sweep(mf_grid* g, const mf_sdnet* net, const mf_sweep_opts* o, mf_s
       if (cg.n_c == 0) continue;
       MF_CUDA(mf::launch_gather_boundary(additive ? g->prev : g->u, cg, net->d, g->B, st), "mf_sweep: gather");
       MF_CUDA(pt.mark(kPhaseGather), "mf_sweep: event");
-      if (o->precision == MF_PREC_BF16)
+      if (bf16)
         MF_CUDA(mf::launch_mlp_bf16(g->B, cg, net->d, g->u, additive ? 1 : 0, g->status, st), "mf_sweep: bf16 mlp");
       else
         MF_CUDA(mf::launch_mlp_fp32(g->B, cg, net->d, g->u, additive ? 1 : 0, st), "mf_sweep: fp32 mlp");
@@ -360,20 +365,25 @@ mf_status mf_sweep(mf_grid* g, const mf_sdnet* net, const mf_sweep_opts* o, mf_s
       mlp_launches += 1;
     }
     done = k + 1;
+    if (bf16) done_bf16 = k + 1;
     if (check) {
       MF_CUDA(mf::launch_reduce(g->u, g->prev, g->nx, g->ny, g->partial, g->out, st), "mf_sweep: reduce");
       MF_CUDA(pt.mark(kPhaseReduce), "mf_sweep: event");
       launches += 2;
       checked = true;
-      if (o->eps > 0.0) {
+      if (o->eps > 0.0 || coarse) {
         MF_CUDA(cudaMemcpyAsync(g->h_out, g->out, 5 * sizeof(double), cudaMemcpyDeviceToHost, st), "mf_sweep: read delta");
         MF_CUDA(cudaMemcpyAsync(g->h_status, g->status, sizeof(int), cudaMemcpyDeviceToHost, st), "mf_sweep: read status");
         MF_CUDA(cudaStreamSynchronize(st), "mf_sweep: synchronize");
         if (*g->h_status != mf::kDevErrNone) return fail(MF_ERR_TIMEOUT, "mf_sweep: a kernel wait timed out");
         const double d = g->h_out[4];
-        if (res) { res->sweeps_done = done; res->delta = d; }
+        if (res) { res->sweeps_done = done; res->delta = d; res->sweeps_bf16 = done_bf16; }
         if (!std::isfinite(d)) return fail(MF_ERR_DIVERGED, "mf_sweep: delta is not finite");
-        if (d < o->eps) break;
+        if (coarse) {
+          if (d < o->eps_coarse) coarse = false;  // switch to FP32 refinement
+        } else if (d < o->eps) {
+          break;
+        }
       }
     }
   }
@@ -391,6 +401,7 @@ mf_status mf_sweep(mf_grid* g, const mf_sdnet* net, const mf_sweep_opts* o, mf_s
     res->ms_gather = ms[kPhaseGather];
     res->ms_mlp = ms[kPhaseMlp];
     res->ms_reduce = ms[kPhaseReduce];
+    res->sweeps_bf16 = done_bf16;
   }
   if (checked && !std::isfinite(g->h_out[4])) return fail(MF_ERR_DIVERGED, "mf_sweep: delta is not finite");
   return MF_OK;

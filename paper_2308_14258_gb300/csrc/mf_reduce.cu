@@ -1,4 +1,4 @@
-// K5: convergence and residual reductions in FP64, in a fixed order.
+// K5: convergence and residual reductions, accumulated in FP64 in a fixed order.
 //
 // One pass over the grid accumulates, per block, sum (u - prev)^2 and sum prev^2 over
 // every grid point (the relative change of Algorithm 2) and max |r|, sum r^2 of the
@@ -25,10 +25,34 @@ __device__ __forceinline__ void warp_reduce(double& a, double& b, double& m, dou
   }
 }
 
+// Error-free sum of two FP32 values (Knuth's TwoSum): a + b = s + e exactly.
+__device__ __forceinline__ float two_sum(float a, float b, float& e) {
+  const float s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+  return s;
+}
+
+// 5-point residual of FP32 values, E + W + N + S - 4C: the partial sums are exact
+// FP32 pairs (TwoSum), so the result is the exact residual rounded about once, with
+// an error relative to r itself rather than to |u| (4C is exact in FP32).
+__device__ __forceinline__ float residual5(float e, float w, float n, float s, float c) {
+  float e1, e2, e3, e4;
+  const float s1 = two_sum(e, w, e1);
+  const float s2 = two_sum(n, s, e2);
+  const float s3 = two_sum(s1, s2, e3);
+  const float s4 = two_sum(s3, -4.0f * c, e4);
+  return s4 + ((e1 + e2) + (e3 + e4));
+}
+
+// Per-point work is FP32 (FP64 throughput is low on this part); every 8 points of a
+// thread are folded into FP64 accumulators, so FP64 carries the long sums.
 __global__ void __launch_bounds__(kThreads)
 reduce_grid_kernel(const float* __restrict__ u, const float* __restrict__ prev, int nx, int ny,
                    double* __restrict__ partial) {
   double sd = 0.0, sp = 0.0, rmax = 0.0, rsq = 0.0;
+  float fd = 0.f, fp = 0.f, fr = 0.f, fmx = 0.f;
+  int n = 0;
   for (int iy = blockIdx.x; iy < ny; iy += gridDim.x) {
     const float* row = u + (size_t)iy * nx;
     const bool inner_row = iy > 0 && iy < ny - 1;
@@ -36,18 +60,24 @@ reduce_grid_kernel(const float* __restrict__ u, const float* __restrict__ prev, 
       const float c = row[ix];
       if (prev) {
         const float p = prev[(size_t)iy * nx + ix];
-        const double d = (double)c - (double)p;
-        sd += d * d;
-        sp += (double)p * (double)p;
+        const float d = c - p;
+        fd = fmaf(d, d, fd);
+        fp = fmaf(p, p, fp);
       }
       if (inner_row && ix > 0 && ix < nx - 1) {
-        const double r = (double)row[ix + 1] + (double)row[ix - 1] + (double)row[ix + nx] +
-                         (double)row[ix - (size_t)nx] - 4.0 * (double)c;
-        rmax = fmax(rmax, fabs(r));
-        rsq += r * r;
+        const float r = residual5(row[ix + 1], row[ix - 1], row[ix + nx], row[ix - (size_t)nx], c);
+        fmx = fmaxf(fmx, fabsf(r));
+        fr = fmaf(r, r, fr);
+      }
+      if (++n == 8) {
+        sd += (double)fd; sp += (double)fp; rsq += (double)fr;
+        fd = fp = fr = 0.f;
+        n = 0;
       }
     }
   }
+  sd += (double)fd; sp += (double)fp; rsq += (double)fr;
+  rmax = (double)fmx;
   __shared__ double sh[4][kThreads / 32];
   warp_reduce(sd, sp, rmax, rsq);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;

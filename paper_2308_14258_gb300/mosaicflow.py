@@ -23,7 +23,7 @@ MF_ERR_DIVERGED = -4
 MF_ERR_TIMEOUT = -5
 MF_ERR_UNSUPPORTED = -6
 
-PREC = {"fp32": 0, "bf16": 1}
+PREC = {"fp32": 0, "bf16": 1, "mixed": 2}
 SCHEDULE = {"M": 0, "multiplicative": 0, "A": 1, "additive": 1}
 
 # Every exported symbol the header declares (checked by the CPU test suite).
@@ -49,13 +49,13 @@ class GridDesc(C.Structure):
 class SweepOpts(C.Structure):
     _fields_ = [("n_sweeps", C.c_int), ("schedule", C.c_int), ("precision", C.c_int),
                 ("colours", C.c_int), ("eps", C.c_double), ("check_every", C.c_int),
-                ("profile", C.c_int)]
+                ("profile", C.c_int), ("eps_coarse", C.c_double)]
 
 
 class SweepResult(C.Structure):
     _fields_ = [("sweeps_done", C.c_int), ("delta", C.c_double), ("kernel_launches", C.c_int),
                 ("mlp_launches", C.c_int), ("ms_gather", C.c_double), ("ms_mlp", C.c_double),
-                ("ms_reduce", C.c_double)]
+                ("ms_reduce", C.c_double), ("sweeps_bf16", C.c_int)]
 
 
 _lib = None
@@ -144,6 +144,7 @@ class SweepOutcome:
     ms_gather: float = 0.0
     ms_mlp: float = 0.0
     ms_reduce: float = 0.0
+    sweeps_bf16: int = 0
 
 
 class Grid:
@@ -186,13 +187,13 @@ class Grid:
 
     def sweep(self, net: SDNet, n_sweeps: int = 1, schedule: str = "M", precision: str = "fp32",
               colours: int = 0, eps: float = 0.0, check_every: int = 1, stream=None,
-              profile: bool = False) -> SweepOutcome:
+              profile: bool = False, eps_coarse: float = 0.0) -> SweepOutcome:
         opts = SweepOpts(n_sweeps, SCHEDULE[schedule], PREC[precision], colours, eps, check_every,
-                         1 if profile else 0)
+                         1 if profile else 0, eps_coarse)
         res = SweepResult()
         _check(load().mf_sweep(self._h, net._h, C.byref(opts), C.byref(res), _stream_ptr(stream)))
         return SweepOutcome(res.sweeps_done, res.delta, res.kernel_launches, res.mlp_launches,
-                            res.ms_gather, res.ms_mlp, res.ms_reduce)
+                            res.ms_gather, res.ms_mlp, res.ms_reduce, res.sweeps_bf16)
 
     def residual(self, stream=None):
         mx, rms = C.c_double(), C.c_double()

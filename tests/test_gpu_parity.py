@@ -140,13 +140,15 @@ def test_residual_and_delta_match_oracle(m):
     g.upload(u0)
     r_max, r_rms = g.residual()
     o_max, o_rms = orc.residual(u0.astype(np.float64))
-    assert r_max == o_max                       # same per-point FP64 sums, max is exact
-    assert abs(r_rms - o_rms) <= 1e-12 * o_rms
+    # per-point residuals are FP32 with error-free partial sums (error ~1 ulp of r);
+    # the sums of squares are FP32 over 8 points, then FP64
+    assert abs(r_max - o_max) <= 1e-6 * o_max
+    assert abs(r_rms - o_rms) <= 1e-6 * o_rms
     w = I.xavier_sdnet(I.SDNetShape(64, 3), 2)
     out = g.sweep(m.SDNet(w, 64, 3), 1, "M", "fp32")
     u1 = g.download()
     d = orc.delta(u1.astype(np.float64), u0.astype(np.float64))
-    assert abs(out.delta - d) <= 1e-12 * d
+    assert abs(out.delta - d) <= 1e-6 * d
 
 
 def test_residual_of_discrete_harmonic_field(m):
@@ -214,3 +216,26 @@ def test_large_sampled_per_colour(m):
             for (a, b) in subs:
                 mask[16 * b + 1:16 * b + 32, 16 * a + 1:16 * a + 32] = False
             assert np.array_equal(pre[mask], post[mask])
+
+
+def test_mixed_precision_refinement_reaches_converged_field(m):
+    """Iterative refinement: BF16 sweeps until delta < 1e-2, then FP32 sweeps until
+    delta < 1e-6 (FP32 rounding keeps delta near 3e-7 at the fixed point), in one call; the result must be within 1e-3 of the FP64 oracle's
+    converged field (4x4 domain, 49 subdomains, SDNet 6x128, whose sweep contracts to
+    a fixed point). The BF16-only fixed point is held to the per-sweep BF16 bound."""
+    L = 4
+    weights = I.xavier_sdnet(I.SDNetShape(128, 6), 1)
+    bc = problem(L, L, 1)
+    solver = orc.Solver(orc.unpack_sdnet(weights, 128, 6))
+    u0 = orc.make_grid(L, L, bc.astype(np.float32).astype(np.float64))
+    ref, hist = orc.run(u0, L, L, solver, 80, eps=1e-13)
+    assert hist[-1] < 1e-12
+    net = m.SDNet(weights, 128, 6)
+    g = m.Grid(L, L, bc)
+    out = g.sweep(net, 200, "M", "mixed", eps=1e-6, eps_coarse=1e-2)
+    assert 0 < out.sweeps_bf16 < out.sweeps_done < 200
+    assert out.delta < 1e-6
+    assert rel_err(g.download(), ref) <= 1e-3
+    g2 = m.Grid(L, L, bc)
+    g2.sweep(net, 60, "M", "bf16")
+    assert rel_err(g2.download(), ref) <= 3e-2
