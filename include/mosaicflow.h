@@ -52,6 +52,9 @@ typedef int mf_status;
 #define MF_SCHEDULE_MULTIPLICATIVE 0 /* colours 0..3 in turn, each reads the latest grid */
 #define MF_SCHEDULE_ADDITIVE 1       /* all colours read the old grid; overlaps averaged */
 
+#define MF_QUERY_FULL 0   /* predict all 961 interior points of every subdomain */
+#define MF_QUERY_CENTRE 1 /* predict only the 61 centre-cross points (interfaces) */
+
 typedef struct mf_sdnet mf_sdnet; /* device-resident SDNet weights (both precisions) */
 typedef struct mf_grid mf_grid;   /* device grid of one problem plus its sweep scratch */
 
@@ -74,6 +77,7 @@ typedef struct {
   int check_every; /* delta computed after every check_every-th sweep and the last (>= 1) */
   int profile;     /* nonzero: time each phase with CUDA events recorded on `stream` */
   double eps_coarse; /* MF_PREC_MIXED: switch from BF16 to FP32 once delta < eps_coarse (> 0) */
+  int query;         /* MF_QUERY_FULL, or MF_QUERY_CENTRE (multiplicative schedule only) */
 } mf_sweep_opts;
 
 typedef struct {
@@ -142,6 +146,12 @@ mf_status mf_grid_download(const mf_grid* grid, float* dst, int dst_on_device, v
  * MF_PREC_MIXED is iterative refinement of the converged field: BF16 sweeps (checked
  * every sweep) until delta < eps_coarse, then FP32 sweeps until delta < eps, both
  * within the n_sweeps budget.
+ * MF_QUERY_CENTRE is the interface-only iteration of Algorithm 2: a subdomain's only
+ * interior points that other subdomains read are its centre lines (x or y on the
+ * 1/2 lattice), so each sweep predicts just those 61 points and leaves the others as
+ * they are; the lattice-line values evolve exactly as with MF_QUERY_FULL. Algorithm 2's
+ * final full prediction averaged over overlaps is then one MF_SCHEDULE_ADDITIVE sweep
+ * with MF_QUERY_FULL.
  * Errors: MF_ERR_INVALID_ARG (null handle/opts, bad option), MF_ERR_DIVERGED (delta
  * not finite; the grid holds the diverged state), MF_ERR_TIMEOUT, MF_ERR_CUDA. */
 mf_status mf_sweep(mf_grid* grid, const mf_sdnet* net, const mf_sweep_opts* opts,

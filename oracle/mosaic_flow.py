@@ -82,6 +82,18 @@ def interior_coords():
     return np.stack([(px.ravel() + 1) / PTS, (py.ravel() + 1) / PTS], axis=1)
 
 
+def centre_cross():
+    """Interior indices p = py*31 + px of the centre lines px = 15 or py = 15 (61 points):
+    the only lattice lines (x, y in multiples of 1/2) strictly inside a unit subdomain,
+    i.e. the only interior points that are other subdomains' boundaries (Figure 3 caption,
+    Algorithm 2). Order: the centre row px = 0..30, then the centre column py = 0..30
+    without its middle point."""
+    c = HALF - 1  # 15
+    row = [c * NI + px for px in range(NI)]
+    col = [py * NI + c for py in range(NI) if py != c]
+    return np.array(row + col)
+
+
 # ---------------------------------------------------------------------------
 # Grid set-up (Eq. 2): boundary from Dirichlet data, interior zero.
 # ---------------------------------------------------------------------------
@@ -235,10 +247,13 @@ class Solver:
         self.X = interior_coords()
         self.Hsub = harmonic_extension() if exact else None
 
-    def solve_batch(self, G: np.ndarray) -> np.ndarray:
+    def solve_batch(self, G: np.ndarray, points=None) -> np.ndarray:
+        """Predictions at the interior points `points` (indices p; default all 961)."""
+        if points is None:
+            points = np.arange(N_INT)
         if self.exact:
-            return G @ self.Hsub.T
-        return sdnet_batched(self.P, G, self.X)
+            return G @ self.Hsub[points].T
+        return sdnet_batched(self.P, G, self.X[points])
 
     def solve_one(self, g: np.ndarray) -> np.ndarray:
         if self.exact:
@@ -246,19 +261,31 @@ class Solver:
         return sdnet(self.P, g, self.X, "split")
 
 
+def write_points(u: np.ndarray, a: int, b: int, points, v: np.ndarray):
+    ox, oy = HALF * a, HALF * b
+    for p, val in zip(points, v):
+        u[oy + 1 + p // NI, ox + 1 + p % NI] = val
+
+
 def sweep_multiplicative(u: np.ndarray, lx: int, ly: int, solver: Solver,
-                         colours=(0, 1, 2, 3)) -> np.ndarray:
+                         colours=(0, 1, 2, 3), query: str = "full") -> np.ndarray:
     """One sweep, colours in order; each colour gathers from the grid as left by the
-    previous colour, predicts its atomic subdomains as one batch and writes them."""
+    previous colour, predicts its atomic subdomains as one batch and writes them.
+    query="center" predicts only each subdomain's centre cross (the interface points,
+    Algorithm 2's per-iteration work); query="full" predicts all interior points."""
     u = u.copy()
+    pts = centre_cross() if query == "center" else None
     for c in colours:
         subs = subdomains_of_colour(lx, ly, c)
         if not subs:
             continue
         G = np.stack([gather(u, a, b) for (a, b) in subs])
-        V = solver.solve_batch(G)
+        V = solver.solve_batch(G, pts)
         for (a, b), v in zip(subs, V):
-            write_interior(u, a, b, v)
+            if pts is None:
+                write_interior(u, a, b, v)
+            else:
+                write_points(u, a, b, pts, v)
     return u
 
 
@@ -324,13 +351,23 @@ def residual(u: np.ndarray):
     return float(np.max(np.abs(r))), float(np.sqrt(np.mean(r ** 2)))
 
 
+def lattice_mask(lx: int, ly: int) -> np.ndarray:
+    """Grid points on the lattice lines x or y in multiples of 1/2 (subdomain boundaries)."""
+    ny, nx = grid_shape(lx, ly)
+    iy, ix = np.mgrid[0:ny, 0:nx]
+    return (ix % HALF == 0) | (iy % HALF == 0)
+
+
 def run(u0: np.ndarray, lx: int, ly: int, solver: Solver, n_sweeps: int,
-        eps: float = 0.0, schedule: str = "M"):
+        eps: float = 0.0, schedule: str = "M", query: str = "full"):
     """Algorithm 2's loop on one device: sweep, then delta; stop when delta < eps."""
     u = u0.copy()
     hist = []
     for k in range(n_sweeps):
-        u_new = (sweep_multiplicative if schedule == "M" else sweep_additive)(u, lx, ly, solver)
+        if schedule == "M":
+            u_new = sweep_multiplicative(u, lx, ly, solver, query=query)
+        else:
+            u_new = sweep_additive(u, lx, ly, solver)
         d = delta(u_new, u)
         u = u_new
         hist.append(d)

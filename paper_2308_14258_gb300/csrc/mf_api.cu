@@ -85,6 +85,8 @@ mf::ColourGeom colour_geom(const mf_grid* g, int c) {
   const int n_b = (cg.nsy - cg.cb + 1) / 2;
   cg.n_a = n_a;
   cg.n_c = n_a * n_b;
+  cg.centre = 0;
+  cg.rows_per_sub = mf::kNint;
   return cg;
 }
 
@@ -321,6 +323,10 @@ mf_status mf_sweep(mf_grid* g, const mf_sdnet* net, const mf_sweep_opts* o, mf_s
     return fail(MF_ERR_INVALID_ARG, "mf_sweep: MF_PREC_MIXED needs eps_coarse > 0");
   if (o->colours < 0 || o->colours > 15) return fail(MF_ERR_INVALID_ARG, "mf_sweep: colours must be a 4-bit mask");
   if (o->check_every < 1) return fail(MF_ERR_INVALID_ARG, "mf_sweep: check_every must be >= 1");
+  if (o->query != MF_QUERY_FULL && o->query != MF_QUERY_CENTRE)
+    return fail(MF_ERR_INVALID_ARG, "mf_sweep: unknown query");
+  if (o->query == MF_QUERY_CENTRE && o->schedule == MF_SCHEDULE_ADDITIVE)
+    return fail(MF_ERR_INVALID_ARG, "mf_sweep: centre-line sweeps use the multiplicative schedule");
   if (!std::isfinite(o->eps)) return fail(MF_ERR_INVALID_ARG, "mf_sweep: eps must be finite");
   if (o->precision != MF_PREC_FP32 && !mf::bf16_supported(net->d))
     return fail(MF_ERR_UNSUPPORTED, "mf_sweep: BF16 path needs 1..5 hidden layers");
@@ -352,8 +358,12 @@ mf_status mf_sweep(mf_grid* g, const mf_sdnet* net, const mf_sweep_opts* o, mf_s
     MF_CUDA(pt.mark(kPhaseReduce), "mf_sweep: event");
     for (int c = 0; c < 4; ++c) {
       if (!((mask >> c) & 1)) continue;
-      const mf::ColourGeom cg = colour_geom(g, c);
+      mf::ColourGeom cg = colour_geom(g, c);
       if (cg.n_c == 0) continue;
+      if (o->query == MF_QUERY_CENTRE) {
+        cg.centre = 1;
+        cg.rows_per_sub = mf::kNcross;
+      }
       MF_CUDA(mf::launch_gather_boundary(additive ? g->prev : g->u, cg, net->d, g->B, st), "mf_sweep: gather");
       MF_CUDA(pt.mark(kPhaseGather), "mf_sweep: event");
       if (bf16)

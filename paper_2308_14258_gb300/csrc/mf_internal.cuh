@@ -20,12 +20,15 @@ constexpr int kDevErrTimeout = 1;
 
 // One colour of one problem, as seen by the kernels.
 struct ColourGeom {
-  int nx;       // grid row length (points)
-  int ca, cb;   // colour parity in x and y
-  int n_a;      // subdomains of this colour along x
-  int n_c;      // subdomains of this colour
-  int nsx, nsy; // subdomains along x and y (all colours)
+  int nx;           // grid row length (points)
+  int ca, cb;       // colour parity in x and y
+  int n_a;          // subdomains of this colour along x
+  int n_c;          // subdomains of this colour
+  int nsx, nsy;     // subdomains along x and y (all colours)
+  int centre;       // 1: predict only each subdomain's centre cross (61 points)
+  int rows_per_sub; // kNint (961) or kNcross (61)
 };
+constexpr int kNcross = 61;  // centre row (31 points) + centre column without its middle (30)
 
 // SDNet weights resident on the device (plus host copies of the small vectors that
 // the tensor-core kernel takes as launch parameters).
@@ -75,8 +78,10 @@ cudaError_t launch_zero_interior(float* u, int nx, int ny, cudaStream_t st);
 
 namespace mf {
 
-// Row r of a colour's batch is interior point p = r mod 961 of subdomain s = r / 961
-// (colour-local index, row-major over the colour's subdomains).
+// Row r of a colour's batch is point p = r mod R of subdomain s = r / R (colour-local
+// index, row-major over the colour's subdomains), R = 961 interior points, or R = 61
+// centre-cross points (p < 31: centre row px = p; else the centre column, py = 0..30
+// without 15) when only the interfaces are predicted.
 struct RowSite {
   int s;      // colour-local subdomain index
   size_t idx; // grid offset of the point
@@ -86,10 +91,17 @@ struct RowSite {
 
 __device__ __forceinline__ RowSite row_site(const ColourGeom& g, int row) {
   RowSite r;
-  r.s = row / kNint;
-  const int p = row - r.s * kNint;
-  r.py = p / kNi;
-  r.px = p - r.py * kNi;
+  r.s = row / g.rows_per_sub;
+  const int p = row - r.s * g.rows_per_sub;
+  if (g.centre) {
+    const int mid = kNi / 2;  // 15
+    const int q = p - kNi;
+    r.px = p < kNi ? p : mid;
+    r.py = p < kNi ? mid : (q < mid ? q : q + 1);
+  } else {
+    r.py = p / kNi;
+    r.px = p - r.py * kNi;
+  }
   const int a = g.ca + 2 * (r.s % g.n_a);
   const int b = g.cb + 2 * (r.s / g.n_a);
   r.ix = kHalf * a + 1 + r.px;

@@ -586,7 +586,7 @@ cudaError_t launch_mlp_bf16(const float* B, const ColourGeom& g, const DevNet& n
   p.wimg = static_cast<const uint8_t*>(net.wimg_bf16);
   p.status = dev_status;
   p.g = g;
-  p.n_rows = g.n_c * kNint;
+  p.n_rows = g.n_c * g.rows_per_sub;
   p.n_tiles = (p.n_rows + kTileRows - 1) / kTileRows;
   p.additive = additive;
   p.bout = net.bout;

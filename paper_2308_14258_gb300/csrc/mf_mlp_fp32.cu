@@ -155,7 +155,7 @@ mlp_fp32_kernel(const float* __restrict__ B, ColourGeom g, int n_rows, const flo
 template <int H>
 cudaError_t launch_h(const float* B, const ColourGeom& g, const DevNet& net, float* u, int additive,
                      cudaStream_t st) {
-  const int n_rows = g.n_c * kNint;
+  const int n_rows = g.n_c * g.rows_per_sub;
   const int tiles = (n_rows + kTR - 1) / kTR;
   const size_t smem = Fp32Cfg<H>::kSmem;
   static bool attr_set = false;

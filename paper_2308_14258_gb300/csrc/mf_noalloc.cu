@@ -73,6 +73,8 @@ mf::ColourGeom geom(int lx, int ly, int c) {
   g.nsy = 2 * ly - 1;
   g.n_a = (g.nsx - g.ca + 1) / 2;
   g.n_c = g.n_a * ((g.nsy - g.cb + 1) / 2);
+  g.centre = 0;
+  g.rows_per_sub = mf::kNint;
   return g;
 }
 

@@ -25,6 +25,7 @@ MF_ERR_UNSUPPORTED = -6
 
 PREC = {"fp32": 0, "bf16": 1, "mixed": 2}
 SCHEDULE = {"M": 0, "multiplicative": 0, "A": 1, "additive": 1}
+QUERY = {"full": 0, "centre": 1, "center": 1}
 
 # Every exported symbol the header declares (checked by the CPU test suite).
 EXPORTS = ["mf_last_error", "mf_version", "mf_load_sdnet", "mf_free_sdnet", "mf_create_grid",
@@ -49,7 +50,7 @@ class GridDesc(C.Structure):
 class SweepOpts(C.Structure):
     _fields_ = [("n_sweeps", C.c_int), ("schedule", C.c_int), ("precision", C.c_int),
                 ("colours", C.c_int), ("eps", C.c_double), ("check_every", C.c_int),
-                ("profile", C.c_int), ("eps_coarse", C.c_double)]
+                ("profile", C.c_int), ("eps_coarse", C.c_double), ("query", C.c_int)]
 
 
 class SweepResult(C.Structure):
@@ -187,13 +188,19 @@ class Grid:
 
     def sweep(self, net: SDNet, n_sweeps: int = 1, schedule: str = "M", precision: str = "fp32",
               colours: int = 0, eps: float = 0.0, check_every: int = 1, stream=None,
-              profile: bool = False, eps_coarse: float = 0.0) -> SweepOutcome:
+              profile: bool = False, eps_coarse: float = 0.0, query: str = "full") -> SweepOutcome:
         opts = SweepOpts(n_sweeps, SCHEDULE[schedule], PREC[precision], colours, eps, check_every,
-                         1 if profile else 0, eps_coarse)
+                         1 if profile else 0, eps_coarse, QUERY[query])
         res = SweepResult()
         _check(load().mf_sweep(self._h, net._h, C.byref(opts), C.byref(res), _stream_ptr(stream)))
         return SweepOutcome(res.sweeps_done, res.delta, res.kernel_launches, res.mlp_launches,
                             res.ms_gather, res.ms_mlp, res.ms_reduce, res.sweeps_bf16)
+
+    def assemble(self, net: SDNet, precision: str = "fp32", stream=None) -> SweepOutcome:
+        """Algorithm 2's final step after centre-line sweeps: every subdomain predicts all
+        its interior points from the current boundaries and each point takes the average
+        over the subdomains that hold it (one additive full sweep)."""
+        return self.sweep(net, 1, "A", precision, stream=stream)
 
     def residual(self, stream=None):
         mx, rms = C.c_double(), C.c_double()

@@ -239,3 +239,41 @@ def test_mixed_precision_refinement_reaches_converged_field(m):
     g2 = m.Grid(L, L, bc)
     g2.sweep(net, 60, "M", "bf16")
     assert rel_err(g2.download(), ref) <= 3e-2
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_centre_line_sweeps_and_assembly(m, prec):
+    """Interface-only sweeps (61 centre-cross points per subdomain, Algorithm 2's
+    iterations) then the averaged full assembly, against the oracle; points off the
+    lattice lines are untouched by the centre-line sweeps."""
+    lx, ly = 3, 2
+    w = I.xavier_sdnet(I.SDNetShape(128, 6), 21, bias_scale=0.1)
+    bc = problem(lx, ly, 22)
+    u0 = random_state(lx, ly, bc, 23)
+    net = m.SDNet(w, 128, 6)
+    g = m.Grid(lx, ly, bc)
+    g.upload(u0)
+    solver = orc.Solver(orc.unpack_sdnet(w, 128, 6))
+    lat = orc.lattice_mask(lx, ly)
+    for _ in range(3):
+        g.sweep(net, 1, "M", prec, query="centre")
+        assert np.array_equal(g.download()[~lat], u0[~lat])
+    # one more sweep against the oracle from the same state (per-sweep error)
+    prev = g.download()
+    g.sweep(net, 1, "M", prec, query="centre")
+    one = orc.sweep_multiplicative(prev.astype(np.float64), lx, ly, solver, query="center")
+    assert rel_err(g.download(), one) <= TOL[prec]
+    # final assembly: one additive full sweep from the same state
+    state = g.download()
+    g.assemble(net, prec)
+    asm = orc.sweep_additive(state.astype(np.float64), lx, ly, solver)
+    assert rel_err(g.download(), asm) <= TOL[prec]
+
+
+def test_centre_line_option_validation(m):
+    w = I.tiny()
+    net = m.SDNet(w.weights(), 64, 4)
+    g = m.Grid(2, 2, w.problems[0].bc)
+    with pytest.raises(m.MFError) as e:
+        g.sweep(net, 1, "A", "fp32", query="centre")
+    assert e.value.status == m.MF_ERR_INVALID_ARG

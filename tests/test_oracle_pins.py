@@ -267,3 +267,47 @@ def test_mutation_dropped_bias_is_caught():
     P["hidden"][0] = (P["hidden"][0][0], np.zeros_like(P["hidden"][0][1]))
     out = mf.sdnet(P, toy_boundary(), mf.interior_coords()[232:233])
     assert abs(out[0] - 6.25) > 1e-3
+
+
+# ------------------------------------------------------- centre-line sweeps
+
+def test_centre_cross_points():
+    pts = mf.centre_cross()
+    assert len(pts) == 61 and len(set(pts.tolist())) == 61
+    X = mf.interior_coords()[pts]
+    assert np.all((X[:, 0] == 0.5) | (X[:, 1] == 0.5))
+    # exactly the interior points that lie on lattice lines of spacing 1/2
+    ny, nx = mf.grid_shape(1, 1)
+    lat = mf.lattice_mask(1, 1)[1:-1, 1:-1].ravel()
+    assert sorted(np.nonzero(lat)[0].tolist()) == sorted(pts.tolist())
+
+
+@pytest.mark.parametrize("solver_kind", ["exact", "sdnet"])
+def test_centre_lines_reproduce_full_sweep_on_lattice(exact, solver_kind):
+    """Gathers read only lattice lines, so predicting just the centre crosses gives the
+    same lattice-line values as predicting whole interiors (Algorithm 2's interface-only
+    iterations), sweep after sweep."""
+    lx, ly = 3, 2
+    if solver_kind == "exact":
+        sol = exact
+    else:
+        sol = mf.Solver(mf.unpack_sdnet(I.xavier_sdnet(I.SDNetShape(64, 3), 3, 0.1), 64, 3))
+    u0 = mf.make_grid(lx, ly, I.bc_values(lx, ly, I.mode_field(I.mode_coeffs(4), lx, ly)))
+    uf, uc = u0.copy(), u0.copy()
+    lat = mf.lattice_mask(lx, ly)
+    for _ in range(4):
+        uf = mf.sweep_multiplicative(uf, lx, ly, sol, query="full")
+        uc = mf.sweep_multiplicative(uc, lx, ly, sol, query="center")
+        assert np.abs(uf[lat] - uc[lat]).max() <= 1e-13 * max(1.0, np.abs(uf).max())
+    # off the lattice the centre-line sweep leaves the initial values untouched
+    assert np.array_equal(uc[~lat], u0[~lat])
+
+
+def test_centre_lines_then_assembly_solve_laplace(exact):
+    """Exact-solver centre-line iterations followed by the averaged full assembly (one
+    additive sweep) reproduce the global FD solution."""
+    lx, ly = 2, 3
+    u0 = mf.make_grid(lx, ly, I.bc_values(lx, ly, I.mode_field(I.mode_coeffs(5), lx, ly)))
+    u, _ = mf.run(u0, lx, ly, exact, 200, eps=1e-15, query="center")
+    u = mf.sweep_additive(u, lx, ly, exact)
+    assert np.abs(u - mf.global_fd_solve(u0)).max() <= 1e-11
