@@ -57,6 +57,7 @@ typedef int mf_status;
 
 typedef struct mf_sdnet mf_sdnet; /* device-resident SDNet weights (both precisions) */
 typedef struct mf_grid mf_grid;   /* device grid of one problem plus its sweep scratch */
+typedef struct mf_batch mf_batch; /* device grids of many independent problems */
 
 typedef struct {
   int width; /* hidden width H: 64 or 128 */
@@ -78,6 +79,7 @@ typedef struct {
   int profile;     /* nonzero: time each phase with CUDA events recorded on `stream` */
   double eps_coarse; /* MF_PREC_MIXED: switch from BF16 to FP32 once delta < eps_coarse (> 0) */
   int query;         /* MF_QUERY_FULL, or MF_QUERY_CENTRE (multiplicative schedule only) */
+  int graph;         /* mf_batch_sweep: replay unchecked sweeps from a captured CUDA graph */
 } mf_sweep_opts;
 
 typedef struct {
@@ -89,6 +91,7 @@ typedef struct {
   double ms_mlp;       /* profile only: summed event time of the SDNet + scatter kernels */
   double ms_reduce;    /* profile only: summed event time of snapshot copies and reductions */
   int sweeps_bf16;     /* of sweeps_done, sweeps run on the BF16 path */
+  int graph_sweeps;    /* mf_batch_sweep: sweeps replayed from the captured graph */
 } mf_sweep_result;
 
 /* Message describing the calling thread's most recent failed call ("" if none). */
@@ -165,6 +168,34 @@ mf_status mf_synchronize(void* stream);
  * result does not depend on timing). Writes max |r| and the root mean square of r
  * to the host doubles; synchronises `stream`. Either output pointer may be NULL. */
 mf_status mf_residual(const mf_grid* grid, double* max_abs, double* rms, void* stream);
+
+/* mf_create_batch -- n independent Laplace problems (Eq. 2) of sizes descs[q] in one
+ * device buffer, each set up like mf_create_grid. `bc_all` holds the problems' CCW
+ * Dirichlet lists (as in mf_create_grid) one after another. Sweeps over a batch treat
+ * the atomic subdomains of one colour of all problems as one batch (Section 4.1
+ * applied across problems). Synchronous. Errors as mf_create_grid. */
+mf_status mf_create_batch(int n, const mf_grid_desc* descs, const double* bc_all, mf_batch** out);
+mf_status mf_destroy_batch(mf_batch* batch);
+
+/* Grid dimensions of one problem and its offset (in floats) inside the batch buffer. */
+mf_status mf_batch_info(const mf_batch* batch, int problem, int* nx, int* ny, long long* offset);
+
+/* Copy one problem's grid in or out (host or device pointer), asynchronously on stream. */
+mf_status mf_batch_upload(mf_batch* batch, int problem, const float* src, int src_on_device, void* stream);
+mf_status mf_batch_download(const mf_batch* batch, int problem, float* dst, int dst_on_device, void* stream);
+
+/* mf_batch_sweep -- multiplicative sweeps (all four colours) of every problem of the
+ * batch at once: per colour one gather launch and one SDNet launch cover all problems.
+ * Options as mf_sweep (precision MF_PREC_FP32 or MF_PREC_BF16; MF_QUERY_FULL or
+ * MF_QUERY_CENTRE; colours must be 0). delta is taken over all problems' grid points
+ * together. With opts->graph set, sweeps after the first are replayed from a CUDA graph
+ * of one sweep (re-captured when the SDNet, precision or query changes). Synchronises
+ * `stream` before returning. Errors as mf_sweep. */
+mf_status mf_batch_sweep(mf_batch* batch, const mf_sdnet* net, const mf_sweep_opts* opts,
+                         mf_sweep_result* result, void* stream);
+
+/* 5-point residual of one problem of the batch, as mf_residual. */
+mf_status mf_batch_residual(const mf_batch* batch, int problem, double* max_abs, double* rms, void* stream);
 
 /* mf_sweep_noalloc -- the multiplicative sweep of mf_sweep (n_sweeps sweeps, all four
  * colours, no early stop) for callers that must not allocate device memory during the

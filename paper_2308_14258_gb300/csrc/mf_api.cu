@@ -87,6 +87,7 @@ mf::ColourGeom colour_geom(const mf_grid* g, int c) {
   cg.n_c = n_a * n_b;
   cg.centre = 0;
   cg.rows_per_sub = mf::kNint;
+  cg.table = nullptr;
   return cg;
 }
 

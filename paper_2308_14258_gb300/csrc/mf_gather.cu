@@ -28,10 +28,8 @@ gather_boundary_kernel(const float* __restrict__ u, ColourGeom g, const float* _
   for (int i = warp; i < kSubPerBlock; i += kGatherThreads / 32) {
     const int s = s0 + i;
     if (s < g.n_c) {
-      const int a = g.ca + 2 * (s % g.n_a);
-      const int b = g.cb + 2 * (s / g.n_a);
-      const size_t nx = (size_t)g.nx;
-      const float* o = u + (size_t)(kHalf * b) * nx + (size_t)(kHalf * a);
+      const size_t nx = sub_stride(g, s);
+      const float* o = u + sub_point(g, s, 0, 0);
       gs[i][lane] = __ldg(o + lane);                                   // (lane, 0)
       gs[i][32 + lane] = __ldg(o + (size_t)lane * nx + kPts);          // (32, lane)
       gs[i][64 + lane] = __ldg(o + (size_t)kPts * nx + (kPts - lane)); // (32 - lane, 32)

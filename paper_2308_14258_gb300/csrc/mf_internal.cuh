@@ -18,7 +18,16 @@ constexpr int kTileRows = 128;  // rows (subdomain, point) per MLP tile
 constexpr int kDevErrNone = 0;
 constexpr int kDevErrTimeout = 1;
 
-// One colour of one problem, as seen by the kernels.
+// A subdomain of a batch of problems: where its corner (local (0,0)) sits in the
+// batch's grid buffer and the row stride of its problem's grid.
+struct SubRef {
+  unsigned long long origin;
+  int nx;
+  int pad;
+};
+
+// One colour of one problem (or of a batch of problems, through `table`), as seen by
+// the kernels.
 struct ColourGeom {
   int nx;           // grid row length (points)
   int ca, cb;       // colour parity in x and y
@@ -27,7 +36,22 @@ struct ColourGeom {
   int nsx, nsy;     // subdomains along x and y (all colours)
   int centre;       // 1: predict only each subdomain's centre cross (61 points)
   int rows_per_sub; // kNint (961) or kNcross (61)
+  const SubRef* table; // batch: the colour's subdomains (then ca, cb, n_a, nsx, nsy unused)
 };
+
+// Grid offset of local point (i, j) of colour-local subdomain s.
+__device__ __forceinline__ size_t sub_point(const ColourGeom& g, int s, int i, int j) {
+  if (g.table) {
+    const SubRef r = g.table[s];
+    return (size_t)r.origin + (size_t)j * (size_t)r.nx + (size_t)i;
+  }
+  const int a = g.ca + 2 * (s % g.n_a);
+  const int b = g.cb + 2 * (s / g.n_a);
+  return (size_t)(kHalf * b + j) * (size_t)g.nx + (size_t)(kHalf * a + i);
+}
+__device__ __forceinline__ size_t sub_stride(const ColourGeom& g, int s) {
+  return g.table ? (size_t)g.table[s].nx : (size_t)g.nx;
+}
 constexpr int kNcross = 61;  // centre row (31 points) + centre column without its middle (30)
 
 // SDNet weights resident on the device (plus host copies of the small vectors that
@@ -68,7 +92,7 @@ bool bf16_supported(const DevNet& net);
 // out 5 doubles: {sum (u-prev)^2, sum prev^2, max |r|, sum r^2, delta}.
 constexpr int kReduceBlocks = 512;
 cudaError_t launch_reduce(const float* u, const float* prev, int nx, int ny, double* partial,
-                          double* out, cudaStream_t st);
+                          double* out, cudaStream_t st, bool residual = true);
 
 // K0 grid set-up: boundary from the FP64 counter-clockwise list `bc` (device), interior 0.
 cudaError_t launch_init_grid(float* u, int nx, int ny, const double* bc, cudaStream_t st);
@@ -101,6 +125,12 @@ __device__ __forceinline__ RowSite row_site(const ColourGeom& g, int row) {
   } else {
     r.py = p / kNi;
     r.px = p - r.py * kNi;
+  }
+  if (g.table) {
+    const SubRef t = g.table[r.s];
+    r.ix = r.iy = 0;  // (only the additive schedule needs them; batches are multiplicative)
+    r.idx = (size_t)t.origin + (size_t)(1 + r.py) * (size_t)t.nx + (size_t)(1 + r.px);
+    return r;
   }
   const int a = g.ca + 2 * (r.s % g.n_a);
   const int b = g.cb + 2 * (r.s / g.n_a);

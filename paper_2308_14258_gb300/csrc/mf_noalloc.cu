@@ -75,6 +75,7 @@ mf::ColourGeom geom(int lx, int ly, int c) {
   g.n_c = g.n_a * ((g.nsy - g.cb + 1) / 2);
   g.centre = 0;
   g.rows_per_sub = mf::kNint;
+  g.table = nullptr;
   return g;
 }
 

@@ -49,13 +49,13 @@ __device__ __forceinline__ float residual5(float e, float w, float n, float s, f
 // thread are folded into FP64 accumulators, so FP64 carries the long sums.
 __global__ void __launch_bounds__(kThreads)
 reduce_grid_kernel(const float* __restrict__ u, const float* __restrict__ prev, int nx, int ny,
-                   double* __restrict__ partial) {
+                   double* __restrict__ partial, int residual) {
   double sd = 0.0, sp = 0.0, rmax = 0.0, rsq = 0.0;
   float fd = 0.f, fp = 0.f, fr = 0.f, fmx = 0.f;
   int n = 0;
   for (int iy = blockIdx.x; iy < ny; iy += gridDim.x) {
     const float* row = u + (size_t)iy * nx;
-    const bool inner_row = iy > 0 && iy < ny - 1;
+    const bool inner_row = residual && iy > 0 && iy < ny - 1;
     for (int ix = threadIdx.x; ix < nx; ix += kThreads) {
       const float c = row[ix];
       if (prev) {
@@ -122,8 +122,8 @@ finalize_kernel(const double* __restrict__ partial, double* __restrict__ out) {
 }  // namespace
 
 cudaError_t launch_reduce(const float* u, const float* prev, int nx, int ny, double* partial, double* out,
-                          cudaStream_t st) {
-  reduce_grid_kernel<<<kReduceBlocks, kThreads, 0, st>>>(u, prev, nx, ny, partial);
+                          cudaStream_t st, bool residual) {
+  reduce_grid_kernel<<<kReduceBlocks, kThreads, 0, st>>>(u, prev, nx, ny, partial, residual ? 1 : 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   finalize_kernel<<<1, kReduceBlocks, 0, st>>>(partial, out);

@@ -30,7 +30,8 @@ QUERY = {"full": 0, "centre": 1, "center": 1}
 # Every exported symbol the header declares (checked by the CPU test suite).
 EXPORTS = ["mf_last_error", "mf_version", "mf_load_sdnet", "mf_free_sdnet", "mf_create_grid",
            "mf_destroy_grid", "mf_grid_dims", "mf_grid_upload", "mf_grid_download", "mf_sweep",
-           "mf_residual", "mf_synchronize", "mf_sweep_noalloc"]
+           "mf_residual", "mf_synchronize", "mf_sweep_noalloc", "mf_create_batch", "mf_destroy_batch",
+           "mf_batch_info", "mf_batch_upload", "mf_batch_download", "mf_batch_sweep", "mf_batch_residual"]
 
 
 class MFError(RuntimeError):
@@ -50,13 +51,13 @@ class GridDesc(C.Structure):
 class SweepOpts(C.Structure):
     _fields_ = [("n_sweeps", C.c_int), ("schedule", C.c_int), ("precision", C.c_int),
                 ("colours", C.c_int), ("eps", C.c_double), ("check_every", C.c_int),
-                ("profile", C.c_int), ("eps_coarse", C.c_double), ("query", C.c_int)]
+                ("profile", C.c_int), ("eps_coarse", C.c_double), ("query", C.c_int), ("graph", C.c_int)]
 
 
 class SweepResult(C.Structure):
     _fields_ = [("sweeps_done", C.c_int), ("delta", C.c_double), ("kernel_launches", C.c_int),
                 ("mlp_launches", C.c_int), ("ms_gather", C.c_double), ("ms_mlp", C.c_double),
-                ("ms_reduce", C.c_double), ("sweeps_bf16", C.c_int)]
+                ("ms_reduce", C.c_double), ("sweeps_bf16", C.c_int), ("graph_sweeps", C.c_int)]
 
 
 _lib = None
@@ -89,6 +90,13 @@ def load(path: str | None = None) -> C.CDLL:
     lib.mf_residual.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
     lib.mf_synchronize.argtypes = [vp]
     lib.mf_sweep_noalloc.argtypes = [vp, i, i, vp, i, i, C.POINTER(C.c_double), vp]
+    lib.mf_create_batch.argtypes = [i, vp, vp, C.POINTER(vp)]
+    lib.mf_destroy_batch.argtypes = [vp]
+    lib.mf_batch_info.argtypes = [vp, i, C.POINTER(i), C.POINTER(i), C.POINTER(C.c_longlong)]
+    lib.mf_batch_upload.argtypes = [vp, i, vp, i, vp]
+    lib.mf_batch_download.argtypes = [vp, i, vp, i, vp]
+    lib.mf_batch_sweep.argtypes = [vp, vp, C.POINTER(SweepOpts), C.POINTER(SweepResult), vp]
+    lib.mf_batch_residual.argtypes = [vp, i, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
     for name in EXPORTS:
         if name not in ("mf_last_error", "mf_version"):
             getattr(lib, name).restype = i
@@ -146,6 +154,7 @@ class SweepOutcome:
     ms_mlp: float = 0.0
     ms_reduce: float = 0.0
     sweeps_bf16: int = 0
+    graph_sweeps: int = 0
 
 
 class Grid:
@@ -194,7 +203,7 @@ class Grid:
         res = SweepResult()
         _check(load().mf_sweep(self._h, net._h, C.byref(opts), C.byref(res), _stream_ptr(stream)))
         return SweepOutcome(res.sweeps_done, res.delta, res.kernel_launches, res.mlp_launches,
-                            res.ms_gather, res.ms_mlp, res.ms_reduce, res.sweeps_bf16)
+                            res.ms_gather, res.ms_mlp, res.ms_reduce, res.sweeps_bf16, res.graph_sweeps)
 
     def assemble(self, net: SDNet, precision: str = "fp32", stream=None) -> SweepOutcome:
         """Algorithm 2's final step after centre-line sweeps: every subdomain predicts all
@@ -205,6 +214,58 @@ class Grid:
     def residual(self, stream=None):
         mx, rms = C.c_double(), C.c_double()
         _check(load().mf_residual(self._h, C.byref(mx), C.byref(rms), _stream_ptr(stream)))
+        return mx.value, rms.value
+
+
+class Batch:
+    """mf_create_batch / mf_batch_*: many independent problems swept together."""
+
+    def __init__(self, sizes, bcs):
+        self.n = len(sizes)
+        descs = (GridDesc * self.n)(*[GridDesc(int(lx), int(ly)) for lx, ly in sizes])
+        bc = np.ascontiguousarray(np.concatenate([np.asarray(b, dtype=np.float64) for b in bcs]))
+        self.sizes = [(int(lx), int(ly)) for lx, ly in sizes]
+        self._h = C.c_void_p()
+        _check(load().mf_create_batch(self.n, descs, bc.ctypes.data, C.byref(self._h)))
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.mf_destroy_batch(self._h)
+            self._h = None
+
+    def shape(self, q):
+        lx, ly = self.sizes[q]
+        return (32 * ly + 1, 32 * lx + 1)
+
+    def upload(self, q, src, stream=None):
+        ptr, dev, nbytes = _buffer(src)
+        if nbytes != int(np.prod(self.shape(q))) * 4:
+            raise ValueError("grid size mismatch")
+        _check(load().mf_batch_upload(self._h, q, ptr, dev, _stream_ptr(stream)))
+
+    def download(self, q, dst=None, stream=None, sync=True):
+        if dst is None:
+            dst = np.empty(self.shape(q), dtype=np.float32)
+        ptr, dev, nbytes = _buffer(dst)
+        if nbytes != int(np.prod(self.shape(q))) * 4:
+            raise ValueError("grid size mismatch")
+        _check(load().mf_batch_download(self._h, q, ptr, dev, _stream_ptr(stream)))
+        if sync:
+            synchronize(stream)
+        return dst
+
+    def sweep(self, net: SDNet, n_sweeps: int = 1, precision: str = "fp32", eps: float = 0.0,
+              check_every: int = 1, query: str = "full", graph: bool = False, stream=None) -> SweepOutcome:
+        opts = SweepOpts(n_sweeps, 0, PREC[precision], 0, eps, check_every, 0, 0.0, QUERY[query],
+                         1 if graph else 0)
+        res = SweepResult()
+        _check(load().mf_batch_sweep(self._h, net._h, C.byref(opts), C.byref(res), _stream_ptr(stream)))
+        return SweepOutcome(res.sweeps_done, res.delta, res.kernel_launches, res.mlp_launches,
+                            res.ms_gather, res.ms_mlp, res.ms_reduce, res.sweeps_bf16, res.graph_sweeps)
+
+    def residual(self, q, stream=None):
+        mx, rms = C.c_double(), C.c_double()
+        _check(load().mf_batch_residual(self._h, q, C.byref(mx), C.byref(rms), _stream_ptr(stream)))
         return mx.value, rms.value
 
 
