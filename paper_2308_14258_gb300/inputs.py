@@ -246,4 +246,33 @@ def batched(n_problems: int = 256) -> Workload:
     return Workload("batched_256", probs, SDNetShape(128, 6), 4, 200, 1e-6, "bf16")
 
 
+@dataclass
+class TrainBatch:
+    G: np.ndarray    # (F, 128) boundary values of each function (CCW on the unit square)
+    Xc: np.ndarray   # (F, Nc, 2) collocation points, uniform in the open unit square
+    Xb: np.ndarray   # (F, Nb, 2) data points: the 128 boundary points
+    Yb: np.ndarray   # (F, Nb) data targets: the boundary values
+
+
+def unit_square_boundary_points() -> np.ndarray:
+    """(128, 2) boundary points of the unit square at spacing 1/32, CCW from (0, 0)."""
+    h = 1.0 / POINTS_PER_UNIT
+    n = POINTS_PER_UNIT
+    pts = [(i * h, 0.0) for i in range(n)] + [(1.0, j * h) for j in range(n)]
+    pts += [(1.0 - i * h, 1.0) for i in range(n)] + [(0.0, 1.0 - j * h) for j in range(n)]
+    return np.array(pts)
+
+
+def training_batch(n_functions: int = 1024, n_colloc: int = 1024, seed: int = 3) -> TrainBatch:
+    """Physics-informed SDNet training batch: n_functions random 8-mode harmonic functions
+    on the unit square (a_k ~ N(0,1)), n_colloc uniform collocation points each for the
+    PDE loss, the 128 boundary points with their values for the data loss."""
+    coef = Stream(seed, TAG_BC).normal(8 * n_functions).reshape(n_functions, 8)
+    xb = unit_square_boundary_points()
+    G = np.stack([mode_field(coef[f], 1.0, 1.0)(xb[:, 0], xb[:, 1]) for f in range(n_functions)])
+    Xc = Stream(seed, TAG_COLLOCATION).uniform(n_functions * n_colloc * 2).reshape(n_functions, n_colloc, 2)
+    Xb = np.broadcast_to(xb, (n_functions, 128, 2)).copy()
+    return TrainBatch(G=G, Xc=Xc, Xb=Xb, Yb=G.copy())
+
+
 WORKLOADS = {"tiny": tiny, "mid": mid, "large": large, "batched": batched}

@@ -82,3 +82,12 @@ def test_presets():
     assert t.shape.width == 64 and t.shape.depth == 4
     b = I.batched(16)
     assert all(p.lx in (2, 4, 8, 16, 32) for p in b.problems)
+
+
+def test_training_batch_shapes_and_harmonic_data():
+    tb = I.training_batch(4, 16)
+    assert tb.G.shape == (4, 128) and tb.Xc.shape == (4, 16, 2) and tb.Xb.shape == (4, 128, 2)
+    assert np.all((tb.Xc > 0) & (tb.Xc < 1))
+    assert np.array_equal(tb.Yb, tb.G)
+    # the 8-mode field vanishes on the bottom, left and right edges of the unit square
+    assert np.abs(tb.G[:, :32]).max() < 1e-12 and np.abs(tb.G[:, 96:]).max() < 1e-12
