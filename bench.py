@@ -56,6 +56,8 @@ def parse():
                                                       "smaller values only for profiling captures)")
     ap.add_argument("--fp32-steps", type=int, default=-1)
     ap.add_argument("--e2e-steps", type=int, default=-1)
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-train", action="store_true")
     return ap.parse_args()
 
 
@@ -324,6 +326,107 @@ def main():
     ms32, mlp32, _, _ = timed_steps("fp32", k32)
     fp32_value = evals_per_sweep * k32 / (sum(ms32) / 1e3) if k32 > 0 else None
 
+    # centre-line (interface-only) sweeps of the same grid: Algorithm 2's per-iteration work
+    k_c = max(3, min(args.steps, 10))
+    cl_ms = []
+    for _ in range(k_c):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        grid.sweep(net, 1, "M", "bf16", stream=stream, query="centre")
+        e1.record(stream)
+        e1.synchronize()
+        cl_ms.append(e0.elapsed_time(e1))
+    n_sub_c = n_sub * 61
+
+    # the batched workload: 256 problems of sides 2..32 units, one SDNet launch per colour
+    batched = None
+    if args.L == 64 and not args.no_batched:
+        wl = I.batched(256)
+        bnet = m.SDNet(wl.weights(), 128, 6)
+        bt = m.Batch([(p.lx, p.ly) for p in wl.problems], [p.bc for p in wl.problems])
+        b_evals = sum((2 * p.lx - 1) * (2 * p.ly - 1) for p in wl.problems) * 961
+        bt.sweep(bnet, 2, "bf16", stream=stream)  # warm-up (uncaptured)
+        res = {}
+        for mode in ("plain", "graph"):
+            kb = 4
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            o = bt.sweep(bnet, kb, "bf16", graph=(mode == "graph"), check_every=kb, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+            res[mode] = {"value": b_evals * kb / t, "ms_per_sweep": 1e3 * t / kb, "graph_sweeps": o.graph_sweeps}
+        batched = {"workload": "256 problems, sides uniform in {2,4,8,16,32} units (seed 4), 8-mode BC seed 1000+q, "
+                               "SDNet 6x128 BF16; grids 287 MB (> L2)",
+                   "unit": UNIT, "evals_per_sweep": b_evals, **res}
+        del bt
+
+    # physics-informed training step (Eq. 3, Algorithm 1): 1024 functions x (1024 collocation
+    # + 128 boundary points), SDNet 6x128, BF16 layer GEMMs, LAMB; ~20 GB working set (> L2)
+    train = None
+    if args.L == 64 and not args.no_train:
+        F, Nc, Nb, H, NH = 1024, 1024, 128, 128, 5
+        tb = I.training_batch(F, Nc, 3)
+        tdev = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+                for a in (tb.G, tb.Xc, tb.Xb, tb.Yb)]
+        tr = m.Trainer(I.xavier_sdnet(I.SDNetShape(H, NH + 1), 4), H, NH + 1, "bf16", "lamb",
+                       max_functions=F, max_points=Nc)
+        for _ in range(3):
+            first_loss = tr.step(*tdev, 1e-3, stream=stream)[0]
+        kt = max(3, min(args.steps, 10))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(kt):
+            last_loss = tr.step(*tdev, 1e-3, stream=stream)[0]
+        e1.record(stream)
+        e1.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        # layer-GEMM flops: forward 2 H^2 per channel and layer, backward twice that;
+        # 4 Taylor channels per collocation point, 1 channel per data point
+        gemm_flop = 3 * 2 * H * H * NH * (4 * F * Nc + F * Nb)
+        train = {"value": kt / t, "unit": "train steps/s", "ms_per_step": 1e3 * t / kt,
+                 "workload": f"{F} functions (8-mode harmonic, seed 3) x ({Nc} collocation + {Nb} boundary points), "
+                             "SDNet 6x128 tanh, BF16 layer GEMMs (cuBLAS) + own Taylor-mode kernels, LAMB",
+                 "gemm_tflop_per_step": gemm_flop / 1e12, "gemm_tflops_achieved": gemm_flop * kt / t / 1e12,
+                 "loss_after_warmup": first_loss, "loss_last": last_loss, "l2": "working set ~20 GB (> L2)"}
+        del tr
+        torch.cuda.empty_cache()
+        # FP32 mode on the same batch (cuBLAS FP32 GEMMs), fewer steps
+        tr = m.Trainer(I.xavier_sdnet(I.SDNetShape(H, NH + 1), 4), H, NH + 1, "fp32", "lamb",
+                       max_functions=F, max_points=Nc)
+        tr.step(*tdev, 1e-3, stream=stream)
+        k32t = 3
+        e0.record(stream)
+        for _ in range(k32t):
+            tr.step(*tdev, 1e-3, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        t32 = e0.elapsed_time(e1) / 1e3
+        train["fp32"] = {"value": k32t / t32, "unit": "train steps/s", "ms_per_step": 1e3 * t32 / k32t}
+        del tr, tdev
+        torch.cuda.empty_cache()
+        # BF16 gradient against the FP64 oracle on 4 sampled functions (full Nc)
+        if rank == 0 and not args.no_cpu_baseline:
+            from oracle import pinn
+            sl = slice(0, 4)
+            small = [np.ascontiguousarray(a[sl], dtype=np.float32) for a in (tb.G, tb.Xc, tb.Xb, tb.Yb)]
+            w0 = I.xavier_sdnet(I.SDNetShape(H, NH + 1), 4)
+            (lt, ld, lp), gref = pinn.loss_and_grads(w0.astype(np.float64), H, NH + 1,
+                                                     *[a.astype(np.float64) for a in small])
+            tr = m.Trainer(w0, H, NH + 1, "bf16", "sgd", max_functions=4, max_points=Nc)
+            lo = tr.grad(*[torch.from_numpy(a).cuda() for a in small])
+            g = tr.grads().astype(np.float64)
+            train["err_vs_oracle_bf16"] = {
+                "functions": "0..3 of the batch, initial weights",
+                "grad_rel_l2": float(np.linalg.norm(g - gref) / np.linalg.norm(gref)),
+                "loss_data_rel": abs(lo[1] - ld) / ld, "rms_laplacian_rel": abs(math.sqrt(lo[2]) - math.sqrt(lp)) / math.sqrt(lp)}
+            del tr
+
     # end to end through the public API: pinned host grid -> upload -> sweep -> download
     host_in = torch.empty(grid.shape, dtype=torch.float32).pin_memory()
     host_out = torch.empty(grid.shape, dtype=torch.float32).pin_memory()
@@ -379,6 +482,11 @@ def main():
         "fp32": {"value": fp32_value, "unit": UNIT, "ms_per_step": sum(ms32) / k32 if k32 else None,
                  "speedup_bf16_over_fp32": value / world / fp32_value if fp32_value else None},
         "err_vs_oracle_bf16_sweep": err,
+        "centre_lines": {"sweeps_per_s": 1e3 * k_c / sum(cl_ms), "ms_per_sweep": sum(cl_ms) / k_c,
+                         "point_evals_per_sweep": n_sub_c, "unit": "sweeps/s",
+                         "note": "interface-only sweeps (61 centre-cross points per subdomain, Algorithm 2)"},
+        "batched": batched,
+        "train": train,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
         "gpu_launches": launches,
         "roofline": {"kernel": "mlp_bf16_kernel<128,5>", "bound": "tensor", "achieved": achieved,

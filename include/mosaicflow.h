@@ -217,6 +217,64 @@ mf_status mf_batch_residual(const mf_batch* batch, int problem, double* max_abs,
 mf_status mf_sweep_noalloc(float* u, int lx, int ly, const mf_sdnet* net, int precision, int n_sweeps,
                            double* delta, void* stream);
 
+/* ---- Physics-informed SDNet training (Section 3.3, Eq. 3, Algorithm 1) ---- */
+
+#define MF_OPT_SGD 0  /* w -= lr g */
+#define MF_OPT_LAMB 1 /* LAMB (You et al., ICLR 2020): Adam moments, trust ratio ||w||/||r|| per tensor */
+
+typedef struct mf_trainer mf_trainer; /* device weights, optimiser state and training scratch */
+
+typedef struct {
+  int width;         /* hidden width H: 64 or 128 */
+  int depth;         /* tanh layers, 2..6, as mf_sdnet_desc */
+  int precision;     /* MF_PREC_FP32, or MF_PREC_BF16: BF16 operands of the H x H layer GEMMs */
+  int optimizer;     /* MF_OPT_SGD or MF_OPT_LAMB */
+  int max_functions; /* functions per chunk (>= 1); a call with more functions runs in chunks */
+  int max_points;    /* largest Nc or Nb of any call: a multiple of 64 */
+  float beta1, beta2, eps, weight_decay; /* LAMB hyper-parameters (ignored by SGD) */
+} mf_train_desc;
+
+/* mf_create_trainer -- device state for training one SDNet on the current device.
+ * `weights`: host FP32 parameters in the mf_load_sdnet packing, copied during the call.
+ * Device memory grows with max_functions * max_points * width * depth (about 20 GB at
+ * 1024 x 1024 x 128 x 6 in BF16): a chunk of functions is processed at a time, so
+ * max_functions bounds memory without bounding the batch.
+ * Errors: MF_ERR_INVALID_ARG (null pointer, unsupported option, non-finite weight,
+ * 4 * max_functions * max_points above 2^31 - 1), MF_ERR_OUT_OF_MEMORY, MF_ERR_CUDA.
+ * Synchronous. */
+mf_status mf_create_trainer(const mf_train_desc* desc, const float* weights, mf_trainer** out);
+mf_status mf_destroy_trainer(mf_trainer* trainer);
+
+/* Replace the weights from a host (src_on_device = 0) or device (1) FP32 array in the
+ * packing above; optimiser moments are kept. Asynchronous on `stream`. */
+mf_status mf_trainer_set_weights(mf_trainer* trainer, const float* src, int src_on_device, void* stream);
+
+/* Copy the current weights, or the gradient of the last mf_train_grad / mf_train_step,
+ * to a host or device FP32 array in the packing above. Asynchronous on `stream`. */
+mf_status mf_trainer_get_weights(const mf_trainer* trainer, float* dst, int dst_on_device, void* stream);
+mf_status mf_trainer_get_grads(const mf_trainer* trainer, float* dst, int dst_on_device, void* stream);
+
+/* mf_train_grad -- loss and gradient of one training iteration (Algorithm 1 on one
+ * device, where the gradient allreduce is the identity):
+ *   L = L_data + L_pde,  L_data = mean over the F * Nb data points of (N(x, g_f) - y)^2,
+ *   L_pde = mean over the F * Nc collocation points of (Delta_x N(x, g_f))^2   (Eq. 3),
+ * with N the SDNet of Eq. 7-8 and Delta_x its Laplacian in the query coordinate.
+ * Device arrays (FP32, row-major, read only): G [F][128] boundary values of each
+ * function (CCW from the corner, as in a subdomain), Xc [F][Nc][2] collocation points,
+ * Xb [F][Nb][2] data points, Yb [F][Nb] their targets. Nc and Nb must be multiples of 64
+ * and at most max_points; F >= 1. The gradient stays on the device (mf_trainer_get_grads).
+ * If loss3 is not NULL it receives (L, L_data, L_pde) in that order. Synchronises `stream`.
+ * Errors: MF_ERR_INVALID_ARG, MF_ERR_DIVERGED (a loss term is not finite),
+ * MF_ERR_CUDA. */
+mf_status mf_train_grad(mf_trainer* trainer, int F, int Nc, int Nb, const float* G, const float* Xc,
+                        const float* Xb, const float* Yb, double* loss3, void* stream);
+
+/* mf_train_step -- mf_train_grad followed by the optimiser update with learning rate lr
+ * (Algorithm 1, step 4; LAMB as used for SDNet training in Section 5.2). Arguments and
+ * errors as mf_train_grad; the weights are not updated when the loss is not finite. */
+mf_status mf_train_step(mf_trainer* trainer, int F, int Nc, int Nb, const float* G, const float* Xc,
+                        const float* Xb, const float* Yb, float lr, double* loss3, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -96,7 +96,7 @@ def loss_and_grads(w, width: int, depth: int, G, Xc, Xb, Yb):
     g_pde = torch.autograd.grad(l_pde, params, allow_unused=True)  # b_out drops out of Delta u
     grads = [(a if a is not None else torch.zeros_like(p)) + (b if b is not None else torch.zeros_like(p))
              for a, b, p in zip(g_data, g_pde, params)]
-    ld, lp = float(l_data), float(l_pde)
+    ld, lp = float(l_data.detach()), float(l_pde.detach())
     return (ld + lp, ld, lp), pack(grads)
 
 

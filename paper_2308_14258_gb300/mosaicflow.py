@@ -1,8 +1,9 @@
 """ctypes binding of libmosaicflow.so: the mf_* calls with Python argument marshalling.
 
-Every step of the sweep runs in the library's sm_103a kernels; this module only converts
-arguments (NumPy arrays, torch tensors, streams) to the C ABI and raises MFError on a
-non-zero status. There is no CPU fallback: if the library is missing or cannot be
+Every step of the sweep runs in the library's sm_103a kernels, and every step of the
+training step in its kernels plus the cuBLAS layer GEMMs it calls; this module only
+converts arguments (NumPy arrays, torch tensors, streams) to the C ABI and raises
+MFError on a non-zero status. There is no CPU fallback: if the library is missing or cannot be
 loaded, loading raises.
 """
 from __future__ import annotations
@@ -26,12 +27,15 @@ MF_ERR_UNSUPPORTED = -6
 PREC = {"fp32": 0, "bf16": 1, "mixed": 2}
 SCHEDULE = {"M": 0, "multiplicative": 0, "A": 1, "additive": 1}
 QUERY = {"full": 0, "centre": 1, "center": 1}
+OPTIMIZER = {"sgd": 0, "lamb": 1}
 
 # Every exported symbol the header declares (checked by the CPU test suite).
 EXPORTS = ["mf_last_error", "mf_version", "mf_load_sdnet", "mf_free_sdnet", "mf_create_grid",
            "mf_destroy_grid", "mf_grid_dims", "mf_grid_upload", "mf_grid_download", "mf_sweep",
            "mf_residual", "mf_synchronize", "mf_sweep_noalloc", "mf_create_batch", "mf_destroy_batch",
-           "mf_batch_info", "mf_batch_upload", "mf_batch_download", "mf_batch_sweep", "mf_batch_residual"]
+           "mf_batch_info", "mf_batch_upload", "mf_batch_download", "mf_batch_sweep", "mf_batch_residual",
+           "mf_create_trainer", "mf_destroy_trainer", "mf_trainer_set_weights", "mf_trainer_get_weights",
+           "mf_trainer_get_grads", "mf_train_grad", "mf_train_step"]
 
 
 class MFError(RuntimeError):
@@ -58,6 +62,12 @@ class SweepResult(C.Structure):
     _fields_ = [("sweeps_done", C.c_int), ("delta", C.c_double), ("kernel_launches", C.c_int),
                 ("mlp_launches", C.c_int), ("ms_gather", C.c_double), ("ms_mlp", C.c_double),
                 ("ms_reduce", C.c_double), ("sweeps_bf16", C.c_int), ("graph_sweeps", C.c_int)]
+
+
+class TrainDesc(C.Structure):
+    _fields_ = [("width", C.c_int), ("depth", C.c_int), ("precision", C.c_int), ("optimizer", C.c_int),
+                ("max_functions", C.c_int), ("max_points", C.c_int), ("beta1", C.c_float), ("beta2", C.c_float),
+                ("eps", C.c_float), ("weight_decay", C.c_float)]
 
 
 _lib = None
@@ -97,6 +107,13 @@ def load(path: str | None = None) -> C.CDLL:
     lib.mf_batch_download.argtypes = [vp, i, vp, i, vp]
     lib.mf_batch_sweep.argtypes = [vp, vp, C.POINTER(SweepOpts), C.POINTER(SweepResult), vp]
     lib.mf_batch_residual.argtypes = [vp, i, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
+    lib.mf_create_trainer.argtypes = [C.POINTER(TrainDesc), vp, C.POINTER(vp)]
+    lib.mf_destroy_trainer.argtypes = [vp]
+    lib.mf_trainer_set_weights.argtypes = [vp, vp, i, vp]
+    lib.mf_trainer_get_weights.argtypes = [vp, vp, i, vp]
+    lib.mf_trainer_get_grads.argtypes = [vp, vp, i, vp]
+    lib.mf_train_grad.argtypes = [vp, i, i, i, vp, vp, vp, vp, C.POINTER(C.c_double), vp]
+    lib.mf_train_step.argtypes = [vp, i, i, i, vp, vp, vp, vp, C.c_float, C.POINTER(C.c_double), vp]
     for name in EXPORTS:
         if name not in ("mf_last_error", "mf_version"):
             getattr(lib, name).restype = i
@@ -286,3 +303,104 @@ def sweep_noalloc(u, lx: int, ly: int, net: SDNet, n_sweeps: int = 1, precision:
 def synchronize(stream=None):
     """mf_synchronize: wait for the work enqueued on `stream` (None = default stream)."""
     _check(load().mf_synchronize(_stream_ptr(stream)))
+
+
+class Trainer:
+    """mf_create_trainer / mf_train_grad / mf_train_step: physics-informed SDNet training
+    (Eq. 3, Algorithm 1) with the weights, gradient and optimiser state on the device."""
+
+    def __init__(self, weights: np.ndarray, width: int, depth: int, precision: str = "bf16",
+                 optimizer: str = "lamb", max_functions: int = 1024, max_points: int = 1024,
+                 beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-6, weight_decay: float = 0.0):
+        w = np.ascontiguousarray(weights, dtype=np.float32)
+        self.width, self.depth, self.n_params = width, depth, w.size
+        d = TrainDesc(width, depth, PREC[precision], OPTIMIZER[optimizer], max_functions, max_points,
+                      beta1, beta2, eps, weight_decay)
+        self._h = C.c_void_p()
+        _check(load().mf_create_trainer(C.byref(d), w.ctypes.data, C.byref(self._h)))
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.mf_destroy_trainer(self._h)
+            self._h = None
+
+    @staticmethod
+    def _batch(G, Xc, Xb, Yb):
+        F = G.shape[0]
+        for name, t, shp in (("G", G, (F, 128)), ("Xc", Xc, (F, Xc.shape[1], 2)),
+                             ("Xb", Xb, (F, Xb.shape[1], 2)), ("Yb", Yb, (F, Xb.shape[1]))):
+            ptr, on_dev, _ = _buffer(t)
+            if not on_dev:
+                raise TypeError(f"{name} must be a CUDA tensor")
+            if tuple(t.shape) != shp:
+                raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {shp}")
+        return F, Xc.shape[1], Xb.shape[1], G.data_ptr(), Xc.data_ptr(), Xb.data_ptr(), Yb.data_ptr()
+
+    def grad(self, G, Xc, Xb, Yb, stream=None):
+        """Loss (total, data, pde) of the batch; the gradient stays on the device."""
+        F, Nc, Nb, g, xc, xb, yb = self._batch(G, Xc, Xb, Yb)
+        loss = (C.c_double * 3)()
+        _check(load().mf_train_grad(self._h, F, Nc, Nb, g, xc, xb, yb, loss, _stream_ptr(stream)))
+        return tuple(loss)
+
+    def step(self, G, Xc, Xb, Yb, lr: float, stream=None):
+        """One training iteration: gradient, then the optimiser update; returns the loss."""
+        F, Nc, Nb, g, xc, xb, yb = self._batch(G, Xc, Xb, Yb)
+        loss = (C.c_double * 3)()
+        _check(load().mf_train_step(self._h, F, Nc, Nb, g, xc, xb, yb, lr, loss, _stream_ptr(stream)))
+        return tuple(loss)
+
+    def _get(self, fn, dst, stream):
+        if dst is None:
+            dst = np.empty(self.n_params, dtype=np.float32)
+        ptr, dev, nbytes = _buffer(dst)
+        if nbytes != self.n_params * 4:
+            raise ValueError("parameter vector size mismatch")
+        _check(fn(self._h, ptr, dev, _stream_ptr(stream)))
+        synchronize(stream)
+        return dst
+
+    def weights(self, dst=None, stream=None):
+        return self._get(load().mf_trainer_get_weights, dst, stream)
+
+    def grads(self, dst=None, stream=None):
+        return self._get(load().mf_trainer_get_grads, dst, stream)
+
+    def set_weights(self, src, stream=None):
+        ptr, dev, nbytes = _buffer(src)
+        if nbytes != self.n_params * 4:
+            raise ValueError("parameter vector size mismatch")
+        _check(load().mf_trainer_set_weights(self._h, ptr, dev, _stream_ptr(stream)))
+
+
+def pinn_loss(weights, trainer: Trainer, G, Xc, Xb, Yb):
+    """L = L_data + L_pde (Eq. 3) as a differentiable function of the packed FP32 weight
+    tensor (on the GPU): the forward pass and the gradient both come from mf_train_grad."""
+    return _pinn_function().apply(weights, trainer, G, Xc, Xb, Yb)
+
+
+_PINN_FN = None
+
+
+def _pinn_function():
+    global _PINN_FN
+    if _PINN_FN is None:
+        import torch
+
+        class PinnLoss(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, weights, trainer, G, Xc, Xb, Yb):
+                stream = torch.cuda.current_stream(weights.device)
+                w = weights.detach().contiguous()
+                trainer.set_weights(w, stream)
+                total, _, _ = trainer.grad(G, Xc, Xb, Yb, stream)
+                ctx.save_for_backward(trainer.grads(torch.empty_like(w), stream))
+                return weights.new_tensor(total)
+
+            @staticmethod
+            def backward(ctx, gout):
+                (g,) = ctx.saved_tensors
+                return gout * g, None, None, None, None, None
+
+        _PINN_FN = PinnLoss
+    return _PINN_FN

@@ -1,0 +1,258 @@
+"""Training step (Eq. 3, Algorithm 1) on the GPU against the FP64 autograd oracle.
+
+Error measures, on identical FP32 inputs and weights:
+    loss:     |L_gpu - L_ref| / |L_ref| per term
+    gradient: ||g_gpu - g_ref||_2 / ||g_ref||_2 over the packed parameter vector, and
+              max |g_gpu - g_ref| / max |g_ref|
+Tolerances: FP32 mode 1e-4 (FP32 GEMMs and FP32 Taylor channels against FP64 nested
+autograd), BF16 mode 3e-2 (BF16 layer-GEMM operands, FP32 accumulation).
+The PDE term is compared through sqrt(L_pde), the RMS of Delta u: BF16 rounds the
+operands of every channel, so the absolute error of Delta u scales with the terms
+t (z_x^2 + z_y^2) and s Delta z it is summed from, not with Delta u itself, and a
+nearly linear network (small Delta u) has a larger relative error in Delta u; squaring
+doubles it again.
+"""
+import numpy as np
+import pytest
+
+from oracle import pinn
+from paper_2308_14258_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-4, "bf16": 3e-2}
+
+
+@pytest.fixture(scope="module")
+def m():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2308_14258_gb300 import mosaicflow
+    return mosaicflow
+
+
+def batch(F, Nc, Nb, seed, data_from_field=True):
+    """FP32 training batch: harmonic boundary data (the training workload's recipe) with Nb
+    data points, or random data points and targets when data_from_field is False."""
+    tb = I.training_batch(F, Nc, seed)
+    G = tb.G.astype(np.float32)
+    Xc = tb.Xc.astype(np.float32)
+    if data_from_field and Nb == 128:
+        Xb, Yb = tb.Xb.astype(np.float32), tb.Yb.astype(np.float32)
+    else:
+        st = I.Stream(seed + 7, I.TAG_TEST)
+        Xb = st.uniform(F * Nb * 2).reshape(F, Nb, 2).astype(np.float32)
+        Yb = st.normal(F * Nb).reshape(F, Nb).astype(np.float32)
+    return G, Xc, Xb, Yb
+
+
+def to_dev(*arrs):
+    import torch
+    return [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrs]
+
+
+def oracle(w, width, depth, G, Xc, Xb, Yb):
+    f64 = lambda a: np.asarray(a, dtype=np.float64)
+    return pinn.loss_and_grads(f64(w), width, depth, f64(G), f64(Xc), f64(Xb), f64(Yb))
+
+
+def grad_errors(g, gref):
+    g = g.astype(np.float64)
+    return (float(np.linalg.norm(g - gref) / np.linalg.norm(gref)),
+            float(np.abs(g - gref).max() / np.abs(gref).max()))
+
+
+def pde_close(got, ref, tol):
+    return abs(np.sqrt(got) - np.sqrt(ref)) <= tol * np.sqrt(ref)
+
+
+def check(m, width, depth, prec, F, Nc, Nb, seed, max_functions=None, bias=0.1):
+    w = I.xavier_sdnet(I.SDNetShape(width, depth), seed, bias_scale=bias)
+    G, Xc, Xb, Yb = batch(F, Nc, Nb, seed)
+    tr = m.Trainer(w, width, depth, prec, "sgd", max_functions=max_functions or F, max_points=max(Nc, Nb))
+    loss = tr.grad(*to_dev(G, Xc, Xb, Yb))
+    g = tr.grads()
+    (lt, ld, lp), gref = oracle(w, width, depth, G, Xc, Xb, Yb)
+    tol = TOL[prec]
+    assert abs(loss[1] - ld) <= tol * abs(ld), (loss, ld)
+    assert pde_close(loss[2], lp, tol), (loss, lp)
+    assert abs(loss[0] - (loss[1] + loss[2])) <= 1e-12 * abs(loss[0])
+    e2, emax = grad_errors(g, gref)
+    assert e2 <= tol and emax <= tol, (e2, emax)
+    return e2, emax
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("width,depth,F,Nc,Nb", [
+    (64, 2, 1, 64, 64),      # one hidden layer, minimum point counts
+    (64, 4, 3, 192, 128),    # several row blocks per function
+    (128, 6, 4, 128, 128),   # the paper's 6 x 128 SDNet
+])
+def test_grad_matches_oracle(m, prec, width, depth, F, Nc, Nb):
+    check(m, width, depth, prec, F, Nc, Nb, seed=width + depth + F)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_chunked_batch_matches_oracle(m, prec):
+    # 5 functions in chunks of 2 (a ragged last chunk of 1)
+    check(m, 64, 3, prec, 5, 128, 64, seed=11, max_functions=2)
+
+
+def test_random_data_points(m):
+    # data points off the boundary with random targets
+    w = I.xavier_sdnet(I.SDNetShape(64, 3), 5, bias_scale=0.1)
+    G, Xc, Xb, Yb = batch(2, 64, 192, 5, data_from_field=False)
+    tr = m.Trainer(w, 64, 3, "fp32", "sgd", max_functions=2, max_points=192)
+    loss = tr.grad(*to_dev(G, Xc, Xb, Yb))
+    (lt, ld, lp), gref = oracle(w, 64, 3, G, Xc, Xb, Yb)
+    assert abs(loss[0] - lt) <= 1e-4 * lt
+    e2, emax = grad_errors(tr.grads(), gref)
+    assert e2 <= 1e-4 and emax <= 1e-4
+
+
+def test_constant_network_closed_form(m):
+    """All weights zero, b_out = 0.75: u = 0.75 everywhere, so L_pde = 0 exactly, and the
+    only non-zero gradient is dL/db_out = 2 mean(0.75 - y)."""
+    shape = I.SDNetShape(64, 3)
+    w = np.zeros(shape.n_params, dtype=np.float32)
+    w[-1] = 0.75
+    G, Xc, Xb, Yb = batch(3, 64, 128, 2)
+    tr = m.Trainer(w, 64, 3, "fp32", "sgd", max_functions=3, max_points=128)
+    loss = tr.grad(*to_dev(G, Xc, Xb, Yb))
+    g = tr.grads()
+    y = Yb.astype(np.float64)
+    assert loss[2] == 0.0
+    assert abs(loss[1] - np.mean((0.75 - y) ** 2)) <= 1e-6 * loss[1]
+    assert np.all(g[:-1] == 0.0)
+    assert abs(g[-1] - 2 * np.mean(0.75 - y)) <= 1e-6 * abs(g[-1]) + 1e-7
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_sgd_step(m, prec):
+    w = I.xavier_sdnet(I.SDNetShape(64, 3), 3, bias_scale=0.1)
+    G, Xc, Xb, Yb = to_dev(*batch(2, 64, 128, 3))
+    tr = m.Trainer(w, 64, 3, prec, "sgd", max_functions=2, max_points=128)
+    lr = 0.05
+    tr.step(G, Xc, Xb, Yb, lr)
+    g = tr.grads().astype(np.float64)
+    w1 = tr.weights().astype(np.float64)
+    ref = pinn.sgd(w, g, lr)
+    assert np.abs(w1 - ref).max() <= 1e-7 * max(1.0, np.abs(ref).max())
+    # the next gradient is taken at the updated weights
+    tr.grad(G, Xc, Xb, Yb)
+    _, gref = oracle(w1.astype(np.float32), 64, 3, *[t.cpu().numpy() for t in (G, Xc, Xb, Yb)])
+    e2, _ = grad_errors(tr.grads(), gref)
+    assert e2 <= TOL[prec]
+
+
+def test_lamb_steps_match_oracle_update(m):
+    """Three LAMB steps: each update equals the oracle's LAMB applied to the GPU's own
+    gradient of that step (the optimiser is checked apart from the gradient)."""
+    width, depth = 64, 3
+    w = I.xavier_sdnet(I.SDNetShape(width, depth), 9, bias_scale=0.1)
+    G, Xc, Xb, Yb = to_dev(*batch(2, 64, 128, 9))
+    tr = m.Trainer(w, width, depth, "fp32", "lamb", max_functions=2, max_points=128,
+                   beta1=0.9, beta2=0.999, eps=1e-6, weight_decay=0.01)
+    mm = np.zeros(w.size)
+    vv = np.zeros(w.size)
+    for k in range(1, 4):
+        w_before = tr.weights().astype(np.float64)
+        tr.step(G, Xc, Xb, Yb, 1e-3)
+        g = tr.grads().astype(np.float64)
+        ref, mm, vv = pinn.lamb(w_before, g, mm, vv, k, 1e-3, width, depth, eps=1e-6, wd=0.01)
+        got = tr.weights().astype(np.float64)
+        step = np.abs(ref - w_before).max()
+        assert np.abs(got - ref).max() <= 1e-3 * step + 1e-7, k
+
+
+def test_training_reduces_loss(m):
+    w = I.xavier_sdnet(I.SDNetShape(64, 4), 21, bias_scale=0.0)
+    G, Xc, Xb, Yb = to_dev(*batch(16, 128, 128, 21))
+    tr = m.Trainer(w, 64, 4, "bf16", "lamb", max_functions=16, max_points=128)
+    first = tr.step(G, Xc, Xb, Yb, 5e-3)[0]
+    for _ in range(40):
+        last = tr.step(G, Xc, Xb, Yb, 5e-3)[0]
+    # the FP64 oracle with the same recipe goes from 1.00 to 0.77 in these 41 steps
+    assert np.isfinite(last) and last < 0.9 * first, (first, last)
+
+
+def test_autograd_function(m):
+    import torch
+    width, depth = 64, 3
+    w = I.xavier_sdnet(I.SDNetShape(width, depth), 4, bias_scale=0.1)
+    Gn, Xcn, Xbn, Ybn = batch(2, 64, 128, 4)
+    G, Xc, Xb, Yb = to_dev(Gn, Xcn, Xbn, Ybn)
+    tr = m.Trainer(w, width, depth, "fp32", "sgd", max_functions=2, max_points=128)
+    wt = torch.from_numpy(w).cuda().requires_grad_(True)
+    loss = m.pinn_loss(wt, tr, G, Xc, Xb, Yb)
+    (3.0 * loss).backward()
+    (lt, _, _), gref = oracle(w, width, depth, Gn, Xcn, Xbn, Ybn)
+    assert abs(float(loss.detach()) - lt) <= 1e-4 * lt
+    e2, _ = grad_errors(wt.grad.cpu().numpy() / 3.0, gref)
+    assert e2 <= 1e-4
+
+
+def test_invalid_arguments(m):
+    import torch
+    w = I.xavier_sdnet(I.SDNetShape(64, 3), 1)
+    tr = m.Trainer(w, 64, 3, "fp32", "sgd", max_functions=2, max_points=128)
+    G, Xc, Xb, Yb = to_dev(*batch(2, 64, 128, 1))
+    with pytest.raises(m.MFError) as e:          # Nc not a multiple of 64
+        tr.grad(G, Xc[:, :63].contiguous(), Xb, Yb)
+    assert e.value.status == m.MF_ERR_INVALID_ARG
+    with pytest.raises(m.MFError) as e:          # Nc above max_points
+        Xbig = torch.zeros(2, 192, 2, device="cuda")
+        tr.grad(G, Xbig, Xb, Yb)
+    assert e.value.status == m.MF_ERR_INVALID_ARG
+    with pytest.raises(TypeError):               # host tensors are refused
+        tr.grad(G.cpu(), Xc, Xb, Yb)
+    with pytest.raises(m.MFError):               # unsupported width
+        m.Trainer(I.xavier_sdnet(I.SDNetShape(32, 3), 1), 32, 3, "fp32")
+    bad = w.copy()
+    bad[5] = np.nan
+    with pytest.raises(m.MFError):
+        m.Trainer(bad, 64, 3, "fp32")
+
+
+def test_full_size_workload(m):
+    """1024 functions x (1024 collocation + 128 boundary points), SDNet 6 x 128 (the
+    training workload). (1) The batch gradient is the mean of per-function gradients, a
+    property at any size: the full batch equals the same batch in 64-function chunks to
+    FP32 reduction order. (2) The FP32 mode, pinned below to the oracle on sampled
+    functions at full Nc, is the reference at full size for the BF16 mode. (3) Sampled
+    functions alone against the oracle: FP32 at 1e-4; BF16 on four functions at 3e-2
+    (a single function's gradient sums fewer points and cancels more, so its BF16
+    relative error is larger)."""
+    import torch
+    width, depth, F, Nc = 128, 6, 1024, 1024
+    w = I.xavier_sdnet(I.SDNetShape(width, depth), 4, bias_scale=0.0)
+    Gn, Xcn, Xbn, Ybn = batch(F, Nc, 128, 3)
+    G, Xc, Xb, Yb = to_dev(Gn, Xcn, Xbn, Ybn)
+    runs = {}
+    for prec, mf in (("bf16", F), ("bf16", 64), ("fp32", F)):
+        tr = m.Trainer(w, width, depth, prec, "lamb", max_functions=mf, max_points=Nc)
+        runs[(prec, mf)] = (tr.grad(G, Xc, Xb, Yb), tr.grads().astype(np.float64))
+        del tr
+        torch.cuda.synchronize()
+    (lf, gf), (lc, gc), (l32, g32) = runs[("bf16", F)], runs[("bf16", 64)], runs[("fp32", F)]
+    for a, b in zip(lf, lc):
+        assert abs(a - b) <= 1e-5 * abs(a)
+    assert np.linalg.norm(gf - gc) <= 1e-4 * np.linalg.norm(gf)
+    assert abs(lf[1] - l32[1]) <= 3e-2 * l32[1] and pde_close(lf[2], l32[2], 3e-2), (lf, l32)
+    assert np.linalg.norm(gf - g32) <= 3e-2 * np.linalg.norm(g32)
+    one = m.Trainer(w, width, depth, "fp32", "sgd", max_functions=1, max_points=Nc)
+    for f in (0, F - 1):
+        sl = slice(f, f + 1)
+        lo = one.grad(*to_dev(Gn[sl], Xcn[sl], Xbn[sl], Ybn[sl]))
+        (lt, ld, lp), gref = oracle(w, width, depth, Gn[sl], Xcn[sl], Xbn[sl], Ybn[sl])
+        assert abs(lo[1] - ld) <= 1e-4 * ld and abs(lo[2] - lp) <= 1e-4 * lp, (f, lo, ld, lp)
+        e2, _ = grad_errors(one.grads(), gref)
+        assert e2 <= 1e-4, (f, e2)
+    del one
+    four = m.Trainer(w, width, depth, "bf16", "sgd", max_functions=4, max_points=Nc)
+    sl = slice(F - 4, F)
+    lo = four.grad(*to_dev(Gn[sl], Xcn[sl], Xbn[sl], Ybn[sl]))
+    (lt, ld, lp), gref = oracle(w, width, depth, Gn[sl], Xcn[sl], Xbn[sl], Ybn[sl])
+    assert abs(lo[1] - ld) <= 3e-2 * ld and pde_close(lo[2], lp, 3e-2), (lo, ld, lp)
+    e2, _ = grad_errors(four.grads(), gref)
+    assert e2 <= 3e-2, e2
