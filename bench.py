@@ -41,7 +41,10 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 
 # DRAM traffic of one SDNet (tensor-core) launch from an ncu capture, valid only while
 # the kernel source is unchanged (keyed by the source hash).
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # ncu --set full, colour 0 of the L = 64 grid: dram__bytes_read 2.64 MB + write 0.33 MB
+    "919671705c06ef71": 2965248,
+}
 
 
 def parse():
@@ -187,9 +190,12 @@ def blas_threads():
 
 
 def source_hash():
-    p = os.path.join(ROOT, "paper_2308_14258_gb300", "csrc", "mf_mlp_bf16.cu")
-    with open(p, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    """Hash of the tensor-core SDNet kernel's sources (the kernel and its headers)."""
+    h = hashlib.sha256()
+    for name in ("mf_mlp_bf16.cu", "mf_wait.cuh", "mf_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2308_14258_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 # ------------------------------------------------------------------ CPU oracle sample
@@ -394,6 +400,11 @@ def main():
                              "SDNet 6x128 tanh, BF16 layer GEMMs (cuBLAS) + own Taylor-mode kernels, LAMB",
                  "gemm_tflop_per_step": gemm_flop / 1e12, "gemm_tflops_achieved": gemm_flop * kt / t / 1e12,
                  "loss_after_warmup": first_loss, "loss_last": last_loss, "l2": "working set ~20 GB (> L2)"}
+        tpeak = load_peaks()[0].get("bf16_tflops_sustained")
+        train["roofline"] = {"bound": "tensor", "achieved": train["gemm_tflops_achieved"], "peak": tpeak,
+                             "unit": "TFLOP/s", "frac": train["gemm_tflops_achieved"] / tpeak,
+                             "note": "whole step: layer-GEMM flops / step time; the step streams ~100 GB "
+                                     "through HBM (layer-by-layer kernels), which sets its time"}
         del tr
         torch.cuda.empty_cache()
         # FP32 mode on the same batch (cuBLAS FP32 GEMMs), fewer steps

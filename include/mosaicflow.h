@@ -217,6 +217,19 @@ mf_status mf_batch_residual(const mf_batch* batch, int problem, double* max_abs,
 mf_status mf_sweep_noalloc(float* u, int lx, int ly, const mf_sdnet* net, int precision, int n_sweeps,
                            double* delta, void* stream);
 
+/* mf_check_wait_timeout -- failure-detection self-test of the bounded device waits.
+ * Launches one CTA whose 64 threads wait, through the same bounded-wait routines as the
+ * tensor-core SDNet kernel, on an mbarrier phase that nothing completes, with a limit of
+ * limit_ms milliseconds (0 < limit_ms <= 1000). Every wait must give up, record the
+ * timeout in the device status word and return; the call then reads that word as
+ * mf_sweep does. Returns MF_ERR_TIMEOUT when the status word recorded the timeout (the
+ * designed outcome), MF_OK if it did not (a defect), MF_ERR_INVALID_ARG for a bad limit,
+ * MF_ERR_CUDA on a CUDA error. *waits_gave_up (may be NULL) receives how many of the 64
+ * waits returned without the phase completing (64 by design). Synchronous; the device
+ * context stays usable. The paper has no counterpart: this checks this library's
+ * failure handling. */
+mf_status mf_check_wait_timeout(double limit_ms, int* waits_gave_up);
+
 /* ---- Physics-informed SDNet training (Section 3.3, Eq. 3, Algorithm 1) ---- */
 
 #define MF_OPT_SGD 0  /* w -= lr g */

@@ -26,6 +26,7 @@
 #include <stdint.h>
 
 #include "mf_internal.cuh"
+#include "mf_wait.cuh"
 
 namespace mf {
 
@@ -34,7 +35,6 @@ namespace {
 constexpr int kMaxHidden = 5;
 constexpr int kEpiWarps = 16;                     // 2 tile slots x 2 column halves x 4 row quadrants
 constexpr int kThreadsBf16 = (kEpiWarps + 2) * 32;  // + one MMA-issuing warp per slot
-constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s
 
 struct Bf16Params {
   const float* B;        // [n_c][H] first-layer boundary term
@@ -54,30 +54,11 @@ struct Bf16Params {
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
-__device__ __forceinline__ unsigned long long globaltimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
 }
 __device__ __forceinline__ void fence_barrier_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -163,60 +144,6 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
 // Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major.
 __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
-}
-
-// Bounded wait on an mbarrier phase; false once the CTA is aborting or after the limit.
-__device__ __noinline__ bool wait_bounded(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status,
-                                          bool honour_abort) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = globaltimer();
-  while (true) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (honour_abort && *abort_flag) return false;
-    if (globaltimer() - t0 > kWaitLimitNs) {
-      *abort_flag = 1;
-      atomicExch(status, kDevErrTimeout);
-      return false;
-    }
-  }
-}
-
-__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Spinning bounded wait: polls the phase without suspending (a suspended try_wait wakes
-// a few hundred cycles after the phase completes, which sits on the critical path);
-// the abort flag and the time limit are checked every 64 polls.
-__device__ __noinline__ bool wait_spin(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status) {
-  if (mbar_test(bar, parity)) return true;
-  const unsigned long long t0 = globaltimer();
-  for (uint32_t i = 1;; ++i) {
-    if (mbar_test(bar, parity)) return true;
-    if ((i & 63u) == 0u) {
-      if (*abort_flag) return false;
-      if (globaltimer() - t0 > kWaitLimitNs) {
-        *abort_flag = 1;
-        atomicExch(status, kDevErrTimeout);
-        return false;
-      }
-    }
-  }
-}
-
-// Warp-uniform form: every lane waits, and the warp continues only if all lanes saw
-// the phase complete (the .sync.aligned tcgen05 loads that follow need the whole warp).
-__device__ __forceinline__ bool wait_warp(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status) {
-  const bool ok = wait_spin(bar, parity, abort_flag, status);
-  return __all_sync(0xffffffffu, ok);
 }
 
 // ---------------------------------------------------------------- kernel

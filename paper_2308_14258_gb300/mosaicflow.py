@@ -35,7 +35,7 @@ EXPORTS = ["mf_last_error", "mf_version", "mf_load_sdnet", "mf_free_sdnet", "mf_
            "mf_residual", "mf_synchronize", "mf_sweep_noalloc", "mf_create_batch", "mf_destroy_batch",
            "mf_batch_info", "mf_batch_upload", "mf_batch_download", "mf_batch_sweep", "mf_batch_residual",
            "mf_create_trainer", "mf_destroy_trainer", "mf_trainer_set_weights", "mf_trainer_get_weights",
-           "mf_trainer_get_grads", "mf_train_grad", "mf_train_step"]
+           "mf_trainer_get_grads", "mf_train_grad", "mf_train_step", "mf_check_wait_timeout"]
 
 
 class MFError(RuntimeError):
@@ -107,6 +107,7 @@ def load(path: str | None = None) -> C.CDLL:
     lib.mf_batch_download.argtypes = [vp, i, vp, i, vp]
     lib.mf_batch_sweep.argtypes = [vp, vp, C.POINTER(SweepOpts), C.POINTER(SweepResult), vp]
     lib.mf_batch_residual.argtypes = [vp, i, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
+    lib.mf_check_wait_timeout.argtypes = [C.c_double, C.POINTER(i)]
     lib.mf_create_trainer.argtypes = [C.POINTER(TrainDesc), vp, C.POINTER(vp)]
     lib.mf_destroy_trainer.argtypes = [vp]
     lib.mf_trainer_set_weights.argtypes = [vp, vp, i, vp]
@@ -298,6 +299,14 @@ def sweep_noalloc(u, lx: int, ly: int, net: SDNet, n_sweeps: int = 1, precision:
     d = C.c_double()
     _check(load().mf_sweep_noalloc(ptr, lx, ly, net._h, PREC[precision], n_sweeps, C.byref(d), _stream_ptr(stream)))
     return d.value
+
+
+def check_wait_timeout(limit_ms: float = 20.0):
+    """mf_check_wait_timeout: run the bounded device waits against a phase that never
+    completes; returns (status, waits_gave_up), (MF_ERR_TIMEOUT, 64) by design."""
+    n = C.c_int()
+    st = load().mf_check_wait_timeout(limit_ms, C.byref(n))
+    return st, n.value
 
 
 def synchronize(stream=None):
