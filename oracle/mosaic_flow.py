@@ -11,7 +11,10 @@ path and scipy's sparse direct solver for the global finite-difference check:
 * SDNet (Section 2.2; Section 3.1-3.2): N(x, g; theta), an MLP whose first layer reads
   the discretised boundary g (4N values, N = 32) and the coordinate x. Both the
   input-concat form (Eq. 5-6) and the input-split form (Eq. 7-8) are written out.
-  Hidden activation tanh (the paper uses GELU, Section 3.1; the workloads fix tanh).
+  Hidden activation tanh (the workloads fix it), or the paper's own variant (Section
+  3.1): GELU activations and a boundary embedding by 1-D convolutions over g taken as a
+  closed curve (two circular conv1d layers, the second with stride 2, each followed by
+  GELU), whose output replaces g as the first layer's boundary input.
 * Mosaic Flow predictor (Section 2.4, Figure 3; Section 4.1): overlapping unit
   subdomains on a lattice of spacing 1/2 (Section 4.2), atomic (non-overlapping)
   subdomains of one colour predicted as one batch, colours applied one after another
@@ -36,6 +39,7 @@ Conventions (readings where the paper is silent):
 from __future__ import annotations
 
 import numpy as np
+from scipy.special import erf
 
 PTS = 32           # intervals per unit length
 SUB = PTS + 1      # points per subdomain side
@@ -139,12 +143,46 @@ def write_interior(u: np.ndarray, a: int, b: int, v: np.ndarray):
 # SDNet (Section 3.2).
 # ---------------------------------------------------------------------------
 
-def unpack_sdnet(w, width: int, depth: int) -> dict:
+def gelu(x):
+    """GELU (Hendrycks and Gimpel), the paper's activation (Section 3.1):
+    x Phi(x) = x (1 + erf(x / sqrt 2)) / 2, with scipy's erf."""
+    return 0.5 * x * (1.0 + erf(x / np.sqrt(2.0)))
+
+
+def conv1d_circular(h: np.ndarray, W: np.ndarray, b: np.ndarray, stride: int) -> np.ndarray:
+    """Cross-correlation of the closed sequence h (C_in x n) with W (C_out x C_in x K),
+    K odd, centred, wrapping around: out[c, i] = b[c] + sum_{c', t} W[c, c', t]
+    h[c', (stride i + t - K//2) mod n], for i = 0 .. n/stride - 1."""
+    c_in, n = h.shape
+    c_out, _, k = W.shape
+    m = n // stride
+    out = np.tile(b[:, None], (1, m)).astype(np.float64)
+    base = stride * np.arange(m)
+    for t in range(k):
+        idx = (base + t - k // 2) % n
+        out += W[:, :, t] @ h[:, idx]
+    return out
+
+
+def embed_boundary(P: dict, g: np.ndarray) -> np.ndarray:
+    """Boundary embedding of the variant: the 128 CCW values as a closed curve,
+    GELU(conv1d 1 -> C, stride 1), then GELU(conv1d C -> C, stride 2), flattened
+    channel-major (C x 64 values). Without an embedding, g itself."""
+    if not P.get("embed"):
+        return g
+    h1 = gelu(conv1d_circular(g[None, :], P["cw1"], P["cb1"], 1))
+    h2 = gelu(conv1d_circular(h1, P["cw2"], P["cb2"], 2))
+    return h2.reshape(-1)
+
+
+def unpack_sdnet(w, width: int, depth: int, activation: str = "tanh", embed_channels: int = 0,
+                 embed_kernel: int = 0) -> dict:
     """Packed FP32 vector -> FP64 parameters.
 
-    Layout: W0[H][130] (boundary block W1 = columns 0..127, coordinate block W2 =
-    columns 128..129, as in Eq. 7), b0[H], then depth-1 hidden layers W[H][H], b[H],
-    then w_out[H], b_out.
+    Layout: [conv1 W[C][1][K], b[C], conv2 W[C][C][K], b[C] when embed_channels = C > 0],
+    W0[H][n_in + 2] (boundary block W1 = the first n_in columns, n_in = 128 or C x 64,
+    coordinate block W2 = the last two, as in Eq. 7), b0[H], then depth-1 hidden layers
+    W[H][H], b[H], then w_out[H], b_out.
     """
     w = np.asarray(w, dtype=np.float64)
     h = width
@@ -156,7 +194,16 @@ def unpack_sdnet(w, width: int, depth: int) -> dict:
         o += n
         return out
 
-    W = take(h * (N_BDRY + 2)).reshape(h, N_BDRY + 2)
+    P = {"act": activation, "embed": embed_channels > 0}
+    n_in = N_BDRY
+    if embed_channels:
+        c, k = embed_channels, embed_kernel
+        P["cw1"] = take(c * k).reshape(c, 1, k)
+        P["cb1"] = take(c)
+        P["cw2"] = take(c * c * k).reshape(c, c, k)
+        P["cb2"] = take(c)
+        n_in = c * (N_BDRY // 2)
+    W = take(h * (n_in + 2)).reshape(h, n_in + 2)
     b0 = take(h)
     hidden = []
     for _ in range(depth - 1):
@@ -166,27 +213,34 @@ def unpack_sdnet(w, width: int, depth: int) -> dict:
     wout = take(h)
     bout = take(1)[0]
     assert o == w.size, (o, w.size)
-    return {"W": W, "W1": W[:, :N_BDRY], "W2": W[:, N_BDRY:], "b0": b0,
-            "hidden": hidden, "wout": wout, "bout": bout}
+    P.update({"W": W, "W1": W[:, :n_in], "W2": W[:, n_in:], "b0": b0,
+              "hidden": hidden, "wout": wout, "bout": bout})
+    return P
+
+
+def activation(P: dict, x: np.ndarray) -> np.ndarray:
+    return gelu(x) if P.get("act") == "gelu" else np.tanh(x)
 
 
 def first_layer_concat(P: dict, g: np.ndarray, X: np.ndarray) -> np.ndarray:
-    """Eq. 5-6: I = [G X] with g replicated per point; pre-activation I W^T + b0."""
+    """Eq. 5-6: I = [G X] with g (or its embedding) replicated per point; pre-activation
+    I W^T + b0."""
     q = X.shape[0]
-    I = np.concatenate([np.tile(g[None, :], (q, 1)), X], axis=1)
+    z = embed_boundary(P, g)
+    I = np.concatenate([np.tile(z[None, :], (q, 1)), X], axis=1)
     return I @ P["W"].T + P["b0"]
 
 
 def first_layer_split(P: dict, g: np.ndarray, X: np.ndarray) -> np.ndarray:
-    """Eq. 7-8: g W1^T broadcast-summed with X W2^T (plus b0)."""
-    return (g @ P["W1"].T + P["b0"])[None, :] + X @ P["W2"].T
+    """Eq. 7-8: g W1^T (g or its embedding) broadcast-summed with X W2^T (plus b0)."""
+    return (embed_boundary(P, g) @ P["W1"].T + P["b0"])[None, :] + X @ P["W2"].T
 
 
 def mlp_tail(P: dict, pre1: np.ndarray) -> np.ndarray:
-    """tanh of the first layer, the hidden tanh layers, then the linear output."""
-    h = np.tanh(pre1)
+    """Activation of the first layer, the hidden layers, then the linear output."""
+    h = activation(P, pre1)
     for Wl, bl in P["hidden"]:
-        h = np.tanh(h @ Wl.T + bl)
+        h = activation(P, h @ Wl.T + bl)
     return h @ P["wout"] + P["bout"]
 
 
@@ -201,7 +255,8 @@ def sdnet_batched(P: dict, G: np.ndarray, X: np.ndarray) -> np.ndarray:
 
     G: (n, 128) boundaries, X: (q, 2) points. Returns (n, q)."""
     n, q = G.shape[0], X.shape[0]
-    B = G @ P["W1"].T + P["b0"]            # per-subdomain boundary term (n, H)
+    Z = np.stack([embed_boundary(P, g) for g in G]) if P.get("embed") else G
+    B = Z @ P["W1"].T + P["b0"]            # per-subdomain boundary term (n, H)
     C = X @ P["W2"].T                      # per-point coordinate term  (q, H)
     pre = (B[:, None, :] + C[None, :, :]).reshape(n * q, -1)
     return mlp_tail(P, pre).reshape(n, q)

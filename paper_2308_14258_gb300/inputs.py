@@ -97,12 +97,21 @@ N_COORD = 2
 @dataclass
 class SDNetShape:
     width: int = 128  # H
-    depth: int = 6    # number of tanh layers (first layer + depth-1 hidden layers)
+    depth: int = 6    # number of activation layers (first layer + depth-1 hidden layers)
+    activation: str = "tanh"  # "tanh" or "gelu"
+    embed_channels: int = 0   # C > 0: two circular conv1d layers embed the boundary first
+    embed_kernel: int = 0     # odd kernel size K of both conv1d layers
+
+    @property
+    def n_in(self) -> int:
+        """Width of the boundary input of the first layer: 128 raw values or C x 64."""
+        return self.embed_channels * (N_BDRY // 2) if self.embed_channels else N_BDRY
 
     @property
     def n_params(self) -> int:
-        h = self.width
-        return h * (N_BDRY + N_COORD) + h + (self.depth - 1) * (h * h + h) + h + 1
+        h, c, k = self.width, self.embed_channels, self.embed_kernel
+        conv = (c * k + c) + (c * c * k + c) if c else 0
+        return conv + h * (self.n_in + N_COORD) + h + (self.depth - 1) * (h * h + h) + h + 1
 
 
 def xavier_sdnet(shape: SDNetShape, seed: int, bias_scale: float = 0.0) -> np.ndarray:
@@ -119,12 +128,23 @@ def xavier_sdnet(shape: SDNetShape, seed: int, bias_scale: float = 0.0) -> np.nd
         bound = math.sqrt(6.0 / (rows + cols))
         return (2.0 * st.uniform(rows * cols) - 1.0) * bound
 
+    def conv(c_out, c_in, k):
+        bound = math.sqrt(6.0 / (c_in * k + c_out * k))
+        return (2.0 * st.uniform(c_out * c_in * k) - 1.0) * bound
+
     def bias(n):
         if bias_scale > 0:
             return (2.0 * st.uniform(n) - 1.0) * bias_scale
         return np.zeros(n)
 
-    parts.append(mat(h, N_BDRY + N_COORD))
+    c, k = shape.embed_channels, shape.embed_kernel
+    if c:
+        # conv1d weights [C_out][C_in][K]: fan_in C_in K, fan_out C_out K
+        parts.append(conv(c, 1, k))
+        parts.append(bias(c))
+        parts.append(conv(c, c, k))
+        parts.append(bias(c))
+    parts.append(mat(h, shape.n_in + N_COORD))
     parts.append(bias(h))
     for _ in range(d - 1):
         parts.append(mat(h, h))
