@@ -43,7 +43,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # the kernel source is unchanged (keyed by the source hash).
 NCU_TRAFFIC = {
     # ncu --set full, colour 0 of the L = 64 grid: dram__bytes_read 2.64 MB + write 0.33 MB
-    "919671705c06ef71": 2965248,
+    "4ea9d8d75b0f990f": 2965504,
 }
 
 
@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=-1)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-train", action="store_true")
+    ap.add_argument("--no-variant", action="store_true")
     return ap.parse_args()
 
 
@@ -371,6 +372,32 @@ def main():
                    "unit": UNIT, "evals_per_sweep": b_evals, **res}
         del bt
 
+    # the paper's SDNet variant (Section 3.1): conv1d boundary embedding (8 channels,
+    # kernel 5) + GELU, 6 x 128, on the same grid
+    variant = None
+    if args.L == 64 and not args.no_variant:
+        vshape = I.SDNetShape(128, 6, "gelu", 8, 5)
+        vnet = m.SDNet(I.xavier_sdnet(vshape, 2), 128, 6, "gelu", 8, 5)
+        variant = {"workload": "large_L64 grid, SDNet 6x128 GELU with a circular conv1d boundary embedding "
+                               "(8 channels, kernel 5; Xavier seed 2)", "unit": UNIT}
+        for prec, kv in (("bf16", max(3, min(args.steps, 10))), ("fp32", 2)):
+            vgrid = m.Grid(p.lx, p.ly, p.bc)
+            vgrid.sweep(vnet, 2, "M", prec, stream=stream)
+            vms = []
+            for _ in range(kv):
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                vgrid.sweep(vnet, 1, "M", prec, stream=stream)
+                e1.record(stream)
+                e1.synchronize()
+                vms.append(e0.elapsed_time(e1))
+            variant[prec] = {"value": evals_per_sweep * kv / (sum(vms) / 1e3), "ms_per_sweep": sum(vms) / kv}
+            del vgrid
+        del vnet
+
     # physics-informed training step (Eq. 3, Algorithm 1): 1024 functions x (1024 collocation
     # + 128 boundary points), SDNet 6x128, BF16 layer GEMMs, LAMB; ~20 GB working set (> L2)
     train = None
@@ -498,9 +525,10 @@ def main():
                          "note": "interface-only sweeps (61 centre-cross points per subdomain, Algorithm 2)"},
         "batched": batched,
         "train": train,
+        "variant_conv1d_gelu": variant,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
         "gpu_launches": launches,
-        "roofline": {"kernel": "mlp_bf16_kernel<128,5>", "bound": "tensor", "achieved": achieved,
+        "roofline": {"kernel": "mlp_bf16_kernel<128,5,tanh>", "bound": "tensor", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "peak_source": f"{peak_src} bf16_tflops_sustained",
                      "traffic": NCU_TRAFFIC.get(h), "per_launch_ms": per_launch_ms,

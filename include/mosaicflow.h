@@ -94,6 +94,18 @@ typedef struct {
   int graph_sweeps;    /* mf_batch_sweep: sweeps replayed from the captured graph */
 } mf_sweep_result;
 
+#define MF_ACT_TANH 0 /* tanh activations (the default network) */
+#define MF_ACT_GELU 1 /* GELU activations, x Phi(x) (Section 3.1) */
+
+typedef struct {
+  int width;          /* hidden width H: 64 or 128 */
+  int depth;          /* activation layers (first + depth-1 hidden H x H layers), 2..6 */
+  int activation;     /* MF_ACT_TANH or MF_ACT_GELU, for the first and hidden layers */
+  int embed_channels; /* 0: the first layer reads the 128 boundary values; C in 1..16: it
+                         reads their conv1d embedding of C x 64 values (see mf_load_sdnet_ex) */
+  int embed_kernel;   /* with embed_channels > 0: odd kernel size K of both conv layers, 1..9 */
+} mf_sdnet_desc_ex;
+
 /* Message describing the calling thread's most recent failed call ("" if none). */
 const char* mf_last_error(void);
 
@@ -110,6 +122,21 @@ int mf_version(void);
  * Errors: MF_ERR_INVALID_ARG for a null pointer or unsupported width/depth,
  * MF_ERR_OUT_OF_MEMORY / MF_ERR_CUDA from the device. Synchronous. */
 mf_status mf_load_sdnet(const mf_sdnet_desc* desc, const float* weights, mf_sdnet** out);
+
+/* mf_load_sdnet_ex -- mf_load_sdnet for the SDNet variants of Section 3.1: GELU
+ * activations and/or a boundary embedding by 1-D convolutions, the boundary taken as a
+ * closed curve (the paper gives no sizes; channels and kernel size are parameters).
+ * With embed_channels = C > 0 the 128 CCW boundary values g pass through
+ *   h1[c][i] = act(cb1[c] + sum_t cw1[c][t] g[(i + t - K/2) mod 128]),      i < 128
+ *   h2[c][i] = act(cb2[c] + sum_{c',t} cw2[c][c'][t] h1[c'][(2i + t - K/2) mod 128]), i < 64
+ * (act = the network's activation) and z[c * 64 + i] = h2[c][i] replaces g as the first
+ * layer's boundary input; the first layer stays input-split (Eq. 8), evaluated once per
+ * subdomain. `weights` then begins with cw1[C][1][K], cb1[C], cw2[C][C][K], cb2[C], and
+ * W0 is [H][C*64 + 2]; the rest of the packing is that of mf_load_sdnet.
+ * MF_ACT_GELU is x Phi(x): exact (erf) on the FP32 path; on the BF16 path its tanh form
+ * 0.5 x (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3))) (Hendrycks and Gimpel), whose error is
+ * far below the BF16 rounding. Errors and synchronisation as mf_load_sdnet. */
+mf_status mf_load_sdnet_ex(const mf_sdnet_desc_ex* desc, const float* weights, mf_sdnet** out);
 mf_status mf_free_sdnet(mf_sdnet* net);
 
 /* mf_create_grid -- allocate the global grid of one Laplace problem (Eq. 2) on the

@@ -166,12 +166,13 @@ def conv1d_circular(h: np.ndarray, W: np.ndarray, b: np.ndarray, stride: int) ->
 
 def embed_boundary(P: dict, g: np.ndarray) -> np.ndarray:
     """Boundary embedding of the variant: the 128 CCW values as a closed curve,
-    GELU(conv1d 1 -> C, stride 1), then GELU(conv1d C -> C, stride 2), flattened
-    channel-major (C x 64 values). Without an embedding, g itself."""
+    act(conv1d 1 -> C, stride 1), then act(conv1d C -> C, stride 2), flattened
+    channel-major (C x 64 values), act the network's activation (GELU in the paper).
+    Without an embedding, g itself."""
     if not P.get("embed"):
         return g
-    h1 = gelu(conv1d_circular(g[None, :], P["cw1"], P["cb1"], 1))
-    h2 = gelu(conv1d_circular(h1, P["cw2"], P["cb2"], 2))
+    h1 = activation(P, conv1d_circular(g[None, :], P["cw1"], P["cb1"], 1))
+    h2 = activation(P, conv1d_circular(h1, P["cw2"], P["cb2"], 2))
     return h2.reshape(-1)
 
 
@@ -326,10 +327,13 @@ def sweep_multiplicative(u: np.ndarray, lx: int, ly: int, solver: Solver,
                          colours=(0, 1, 2, 3), query: str = "full") -> np.ndarray:
     """One sweep, colours in order; each colour gathers from the grid as left by the
     previous colour, predicts its atomic subdomains as one batch and writes them.
-    query="center" predicts only each subdomain's centre cross (the interface points,
-    Algorithm 2's per-iteration work); query="full" predicts all interior points."""
+    query="centre" (or "center") predicts only each subdomain's centre cross (the
+    interface points, Algorithm 2's per-iteration work); query="full" predicts all
+    interior points."""
+    if query not in ("full", "centre", "center"):
+        raise ValueError(f"unknown query {query!r}")
     u = u.copy()
-    pts = centre_cross() if query == "center" else None
+    pts = centre_cross() if query in ("centre", "center") else None
     for c in colours:
         subs = subdomains_of_colour(lx, ly, c)
         if not subs:

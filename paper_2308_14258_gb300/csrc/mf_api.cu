@@ -144,24 +144,43 @@ const char* mf_last_error(void) { return g_err.c_str(); }
 int mf_version(void) { return 100; }
 
 mf_status mf_load_sdnet(const mf_sdnet_desc* desc, const float* w, mf_sdnet** out) {
+  if (!desc) return fail(MF_ERR_INVALID_ARG, "mf_load_sdnet: null argument");
+  const mf_sdnet_desc_ex ex{desc->width, desc->depth, MF_ACT_TANH, 0, 0};
+  return mf_load_sdnet_ex(&ex, w, out);
+}
+
+mf_status mf_load_sdnet_ex(const mf_sdnet_desc_ex* desc, const float* w, mf_sdnet** out) {
   if (!desc || !w || !out) return fail(MF_ERR_INVALID_ARG, "mf_load_sdnet: null argument");
   *out = nullptr;
   const int H = desc->width, D = desc->depth;
   if (H != 64 && H != 128) return fail(MF_ERR_INVALID_ARG, "mf_load_sdnet: width must be 64 or 128");
   if (D < 2 || D > 6) return fail(MF_ERR_INVALID_ARG, "mf_load_sdnet: depth must be in 2..6");
+  if (desc->activation != MF_ACT_TANH && desc->activation != MF_ACT_GELU)
+    return fail(MF_ERR_INVALID_ARG, "mf_load_sdnet: activation must be MF_ACT_TANH or MF_ACT_GELU");
+  const int C = desc->embed_channels, K = desc->embed_kernel;
+  if (C < 0 || C > mf::kMaxEmbedC) return fail(MF_ERR_INVALID_ARG, "mf_load_sdnet: embed_channels must be in 0..16");
+  if (C > 0 && (K < 1 || K > mf::kMaxEmbedK || K % 2 == 0))
+    return fail(MF_ERR_INVALID_ARG, "mf_load_sdnet: embed_kernel must be odd, 1..9");
   const int NH = D - 1;
-  for (size_t i = 0, n = (size_t)H * 131 + (size_t)NH * (H * H + H) + H + 1; i < n; ++i)
+  const int n_in = C > 0 ? C * 64 : 128;
+  const size_t n_conv = C > 0 ? (size_t)C * K + C + (size_t)C * C * K + C : 0;
+  const size_t n_all = n_conv + (size_t)H * (n_in + 2) + H + (size_t)NH * (H * H + H) + H + 1;
+  for (size_t i = 0; i < n_all; ++i)
     if (!std::isfinite(w[i])) return fail(MF_ERR_INVALID_ARG, "mf_load_sdnet: non-finite weight");
 
-  // unpack the FP32 layout W0[H][130], b0, {W[H][H], b}, w_out, b_out
+  // unpack [conv1 W, b, conv2 W, b], W0[H][n_in+2], b0, {W[H][H], b}, w_out, b_out
   const float* p = w;
-  const float* W0 = p;  p += (size_t)H * 130;
+  const float* cw1 = p;  p += (size_t)C * K;
+  const float* cb1 = p;  p += C;
+  const float* cw2 = p;  p += (size_t)C * C * K;
+  const float* cb2 = p;  p += C;
+  const float* W0 = p;  p += (size_t)H * (n_in + 2);
   const float* b0 = p;  p += H;
-  std::vector<float> W1t((size_t)128 * H), W2((size_t)H * 2), WhT((size_t)NH * H * H), bh((size_t)NH * H);
+  std::vector<float> W1t((size_t)n_in * H), W2((size_t)H * 2), WhT((size_t)NH * H * H), bh((size_t)NH * H);
   for (int j = 0; j < H; ++j) {
-    for (int k = 0; k < 128; ++k) W1t[(size_t)k * H + j] = W0[(size_t)j * 130 + k];
-    W2[2 * j] = W0[(size_t)j * 130 + 128];
-    W2[2 * j + 1] = W0[(size_t)j * 130 + 129];
+    for (int k = 0; k < n_in; ++k) W1t[(size_t)k * H + j] = W0[(size_t)j * (n_in + 2) + k];
+    W2[2 * j] = W0[(size_t)j * (n_in + 2) + n_in];
+    W2[2 * j + 1] = W0[(size_t)j * (n_in + 2) + n_in + 1];
   }
   std::vector<uint16_t> img((size_t)NH * H * H);
   for (int l = 0; l < NH; ++l) {
@@ -177,12 +196,12 @@ mf_status mf_load_sdnet(const mf_sdnet_desc* desc, const float* w, mf_sdnet** ou
 
   mf_sdnet* net = new mf_sdnet();
   cudaGetDevice(&net->device);
-  // one allocation: W1t | W2 | b0 | WhT | bh | wout | BF16 images (each 256-byte aligned)
+  // one allocation: W1t | W2 | b0 | WhT | bh | wout | BF16 images | conv (each 256-byte aligned)
   auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t sz_W1t = up(W1t.size() * 4), sz_W2 = up(W2.size() * 4), sz_b0 = up((size_t)H * 4),
                sz_WhT = up(WhT.size() * 4), sz_bh = up(bh.size() * 4), sz_wout = up((size_t)H * 4),
-               sz_img = up(img.size() * 2);
-  const size_t total = sz_W1t + sz_W2 + sz_b0 + sz_WhT + sz_bh + sz_wout + sz_img;
+               sz_img = up(img.size() * 2), sz_conv = up(n_conv * 4 + 4);
+  const size_t total = sz_W1t + sz_W2 + sz_b0 + sz_WhT + sz_bh + sz_wout + sz_img + sz_conv;
   cudaError_t e = cudaMalloc(&net->dmem, total);
   if (e != cudaSuccess) {
     delete net;
@@ -193,7 +212,7 @@ mf_status mf_load_sdnet(const mf_sdnet_desc* desc, const float* w, mf_sdnet** ou
   auto place = [&](const void* src, size_t bytes, size_t slot) -> void* {
     void* dst = base + o;
     o += slot;
-    if (cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return nullptr;
+    if (bytes && cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return nullptr;
     return dst;
   };
   net->d.W1t = (const float*)place(W1t.data(), W1t.size() * 4, sz_W1t);
@@ -203,7 +222,9 @@ mf_status mf_load_sdnet(const mf_sdnet_desc* desc, const float* w, mf_sdnet** ou
   net->d.bh = (const float*)place(bh.data(), bh.size() * 4, sz_bh);
   net->d.wout = (const float*)place(wout, (size_t)H * 4, sz_wout);
   net->d.wimg_bf16 = place(img.data(), img.size() * 2, sz_img);
-  if (!net->d.W1t || !net->d.W2 || !net->d.b0 || !net->d.WhT || !net->d.bh || !net->d.wout || !net->d.wimg_bf16) {
+  const float* conv = (const float*)place(w, n_conv * 4, sz_conv);  // cw1 | cb1 | cw2 | cb2, as packed
+  if (!net->d.W1t || !net->d.W2 || !net->d.b0 || !net->d.WhT || !net->d.bh || !net->d.wout || !net->d.wimg_bf16 ||
+      !conv) {
     cudaError_t err = cudaGetLastError();
     cudaFree(net->dmem);
     delete net;
@@ -212,6 +233,14 @@ mf_status mf_load_sdnet(const mf_sdnet_desc* desc, const float* w, mf_sdnet** ou
   net->d.width = H;
   net->d.depth = D;
   net->d.n_hidden = NH;
+  net->d.act = desc->activation == MF_ACT_GELU ? mf::kActGelu : mf::kActTanh;
+  net->d.embed_c = C;
+  net->d.embed_k = C > 0 ? K : 0;
+  net->d.n_in = n_in;
+  net->d.cw1 = C > 0 ? conv + (cw1 - w) : nullptr;
+  net->d.cb1 = C > 0 ? conv + (cb1 - w) : nullptr;
+  net->d.cw2 = C > 0 ? conv + (cw2 - w) : nullptr;
+  net->d.cb2 = C > 0 ? conv + (cb2 - w) : nullptr;
   net->d.bout = bout;
   net->d.wimg_bytes = img.size() * 2;
   net->h_bh = bh;

@@ -1,4 +1,5 @@
-// K0 grid set-up and K1 boundary gather + per-subdomain first-layer term.
+// K0 grid set-up and K1 boundary gather + per-subdomain first-layer term (with the
+// conv1d boundary embedding of the SDNet variant when the network has one).
 //
 // K1 reads, for every subdomain of one colour, its 128 boundary values from the global
 // grid (the in-device form of Algorithm 2's boundary exchange) and forms the left
@@ -62,6 +63,94 @@ gather_boundary_kernel(const float* __restrict__ u, ColourGeom g, const float* _
   }
 }
 
+// K1 for the SDNet variant with a boundary embedding (Section 3.1): the 128 boundary
+// values of a subdomain, taken as a closed curve, pass through two circular conv1d
+// layers (1 -> C channels at stride 1, then C -> C at stride 2, kernel K, each followed
+// by the network's activation); the C x 64 outputs z, channel-major, give
+// B[s][j] = sum_e W1[j][e] z[e] + b0[j]. Four subdomains per block; everything in FP32.
+constexpr int kEmbedThreads = 256;
+constexpr int kEmbedSubs = 4;
+
+__host__ __device__ constexpr int embed_floats_per_sub(int C) { return kNbdry + C * kNbdry + C * (kNbdry / 2); }
+
+template <int H, int ACT>
+__global__ void __launch_bounds__(kEmbedThreads)
+embed_boundary_kernel(const float* __restrict__ u, ColourGeom g, const float* __restrict__ cw1,
+                      const float* __restrict__ cb1, const float* __restrict__ cw2, const float* __restrict__ cb2,
+                      int C, int K, const float* __restrict__ W1t, const float* __restrict__ b0,
+                      float* __restrict__ B) {
+  extern __shared__ float sm[];  // per subdomain: g[128] | h1[C][128] | z = h2[C][64]
+  const int per = embed_floats_per_sub(C);
+  const int s0 = blockIdx.x * kEmbedSubs;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp < kEmbedSubs) {
+    float* gs = sm + warp * per;
+    const int s = s0 + warp;
+    if (s < g.n_c) {
+      const size_t nx = sub_stride(g, s);
+      const float* o = u + sub_point(g, s, 0, 0);
+      gs[lane] = __ldg(o + lane);
+      gs[32 + lane] = __ldg(o + (size_t)lane * nx + kPts);
+      gs[64 + lane] = __ldg(o + (size_t)kPts * nx + (kPts - lane));
+      gs[96 + lane] = __ldg(o + (size_t)(kPts - lane) * nx);
+    } else {
+      gs[lane] = gs[32 + lane] = gs[64 + lane] = gs[96 + lane] = 0.f;
+    }
+  }
+  __syncthreads();
+  const int half = K / 2;
+  // conv 1: h1[c][i] = act(cb1[c] + sum_t cw1[c][t] g[(i + t - K/2) mod 128])
+  for (int idx = threadIdx.x; idx < kEmbedSubs * C * kNbdry; idx += kEmbedThreads) {
+    const int i = idx & (kNbdry - 1), row = idx >> 7, c = row % C, sub = row / C;
+    const float* gs = sm + sub * per;
+    float acc = __ldg(cb1 + c);
+    for (int t = 0; t < K; ++t) acc = fmaf(__ldg(cw1 + c * K + t), gs[(i + t - half + kNbdry) & (kNbdry - 1)], acc);
+    sm[sub * per + kNbdry + c * kNbdry + i] = act_exact<ACT>(acc);
+  }
+  __syncthreads();
+  // conv 2, stride 2: z[c][i] = act(cb2[c] + sum_{c',t} cw2[c][c'][t] h1[c'][(2i + t - K/2) mod 128])
+  for (int idx = threadIdx.x; idx < kEmbedSubs * C * (kNbdry / 2); idx += kEmbedThreads) {
+    const int i = idx & (kNbdry / 2 - 1), row = idx >> 6, c = row % C, sub = row / C;
+    const float* h1 = sm + sub * per + kNbdry;
+    float acc = __ldg(cb2 + c);
+    for (int cp = 0; cp < C; ++cp) {
+      const float* wr = cw2 + (size_t)(c * C + cp) * K;
+      const float* hr = h1 + cp * kNbdry;
+      for (int t = 0; t < K; ++t) acc = fmaf(__ldg(wr + t), hr[(2 * i + t - half + kNbdry) & (kNbdry - 1)], acc);
+    }
+    sm[sub * per + kNbdry + C * kNbdry + c * (kNbdry / 2) + i] = act_exact<ACT>(acc);
+  }
+  __syncthreads();
+  // B[s][j] = sum_e W1t[e][j] z[e] + b0[j]
+  constexpr int kGroups = kEmbedThreads / H;
+  const int j = threadIdx.x % H, grp = threadIdx.x / H;
+  const int n_in = C * (kNbdry / 2);
+  for (int sub = grp; sub < kEmbedSubs; sub += kGroups) {
+    const float* z = sm + sub * per + kNbdry + C * kNbdry;
+    float acc = 0.f;
+    for (int e = 0; e < n_in; ++e) acc = fmaf(__ldg(W1t + (size_t)e * H + j), z[e], acc);
+    const int s = s0 + sub;
+    if (s < g.n_c) B[(size_t)s * H + j] = acc + __ldg(b0 + j);
+  }
+}
+
+template <int H, int ACT>
+cudaError_t launch_embed(const float* u, const ColourGeom& g, const DevNet& net, float* B, cudaStream_t st) {
+  const size_t smem = (size_t)kEmbedSubs * embed_floats_per_sub(net.embed_c) * sizeof(float);
+  static bool attr_set = false;
+  if (!attr_set) {
+    const int max_smem = kEmbedSubs * embed_floats_per_sub(kMaxEmbedC) * (int)sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(embed_boundary_kernel<H, ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         max_smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int blocks = (g.n_c + kEmbedSubs - 1) / kEmbedSubs;
+  embed_boundary_kernel<H, ACT><<<blocks, kEmbedThreads, smem, st>>>(u, g, net.cw1, net.cb1, net.cw2, net.cb2,
+                                                                      net.embed_c, net.embed_k, net.W1t, net.b0, B);
+  return cudaGetLastError();
+}
+
 // K0: boundary from the CCW Dirichlet list (rounded to FP32), interior zero.
 __global__ void init_grid_kernel(float* __restrict__ u, int nx, int ny, const double* __restrict__ bc) {
   const size_t n = (size_t)nx * ny;
@@ -95,6 +184,11 @@ __global__ void zero_interior_kernel(float* __restrict__ u, int nx, int ny) {
 cudaError_t launch_gather_boundary(const float* u, const ColourGeom& g, const DevNet& net, float* B,
                                    cudaStream_t st) {
   if (g.n_c <= 0) return cudaSuccess;
+  if (net.embed_c > 0) {
+    if (net.width == 128)
+      return net.act == kActGelu ? launch_embed<128, kActGelu>(u, g, net, B, st) : launch_embed<128, kActTanh>(u, g, net, B, st);
+    return net.act == kActGelu ? launch_embed<64, kActGelu>(u, g, net, B, st) : launch_embed<64, kActTanh>(u, g, net, B, st);
+  }
   const int blocks = (g.n_c + kSubPerBlock - 1) / kSubPerBlock;
   if (net.width == 128)
     gather_boundary_kernel<128><<<blocks, kGatherThreads, 0, st>>>(u, g, net.W1t, net.b0, B);

@@ -14,6 +14,20 @@ constexpr int kNint = 961;      // interior points per subdomain
 constexpr int kNbdry = 128;     // boundary values per subdomain
 constexpr int kTileRows = 128;  // rows (subdomain, point) per MLP tile
 
+// Activations of the SDNet layers.
+constexpr int kActTanh = 0;
+constexpr int kActGelu = 1;
+constexpr int kMaxEmbedC = 16;  // boundary-embedding channels
+constexpr int kMaxEmbedK = 9;   // boundary-embedding kernel size (odd)
+
+// Activation in FP32 with CUDA's accurate functions: tanh, or GELU x Phi(x) =
+// x (1 + erf(x / sqrt 2)) / 2 (the FP32 kernels, and the boundary embedding).
+template <int ACT>
+__device__ __forceinline__ float act_exact(float x) {
+  if constexpr (ACT == kActTanh) return tanhf(x);
+  else return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f));
+}
+
 // Device error codes written to the status word by kernels whose bounded waits give up.
 constexpr int kDevErrNone = 0;
 constexpr int kDevErrTimeout = 1;
@@ -57,9 +71,16 @@ constexpr int kNcross = 61;  // centre row (31 points) + centre column without i
 // SDNet weights resident on the device (plus host copies of the small vectors that
 // the tensor-core kernel takes as launch parameters).
 struct DevNet {
-  int width, depth;      // H and number of tanh layers
+  int width, depth;      // H and number of activation layers
   int n_hidden;          // depth - 1 hidden H x H layers
-  const float* W1t;      // [128][H] boundary block of W0, transposed (k-major)
+  int act;               // kActTanh or kActGelu (first and hidden layers)
+  int embed_c, embed_k;  // boundary embedding: channels C (0 = none) and kernel size K
+  int n_in;              // boundary input width of the first layer: 128, or C x 64
+  const float* cw1;      // [C][K] first conv1d layer (1 -> C), stride 1
+  const float* cb1;      // [C]
+  const float* cw2;      // [C][C][K] second conv1d layer (C -> C), stride 2
+  const float* cb2;      // [C]
+  const float* W1t;      // [n_in][H] boundary block of W0, transposed (k-major)
   const float* W2;       // [H][2] coordinate block of W0
   const float* b0;       // [H]
   const float* WhT;      // [n_hidden][H(k)][H(n)] hidden weights, transposed (k-major)
@@ -74,7 +95,8 @@ struct DevNet {
 };
 
 // K1: gather the boundary of every subdomain of the colour from `u` and form the
-// per-subdomain first-layer term B[s][:] = W1 g_s + b0 (Eq. 8, left operand).
+// per-subdomain first-layer term B[s][:] = W1 z_s + b0 (Eq. 8, left operand), with z_s
+// the boundary g_s itself or, for the embedding variant, its conv1d embedding.
 cudaError_t launch_gather_boundary(const float* u, const ColourGeom& g, const DevNet& net,
                                    float* B, cudaStream_t st);
 

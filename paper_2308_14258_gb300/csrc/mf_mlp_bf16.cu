@@ -125,6 +125,29 @@ __device__ __forceinline__ uint32_t tanh_bf16x2(uint32_t x) {
 }
 __device__ __forceinline__ float bf16_lo(uint32_t v) { return __uint_as_float(v << 16); }
 __device__ __forceinline__ float bf16_hi(uint32_t v) { return __uint_as_float(v & 0xffff0000u); }
+__device__ __forceinline__ float tanh_approx(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Activation of two FP32 pre-activations, packed as BF16x2. tanh: the hardware tanh on
+// the BF16 pair. GELU: its tanh form 0.5 x (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3)))
+// (Hendrycks and Gimpel) with the FP32 hardware tanh, so that 1 + tanh keeps its
+// accuracy for negative x; both forms cost one tanh per element on the MUFU unit.
+template <int ACT>
+__device__ __forceinline__ uint32_t act_bf16x2(float a0, float a1) {
+  if constexpr (ACT == kActTanh) {
+    return tanh_bf16x2(pack_bf16x2(a0, a1));
+  } else {
+    constexpr float k0 = 0.7978845608028654f;  // sqrt(2 / pi)
+    constexpr float k1 = k0 * 0.044715f;
+    const float t0 = tanh_approx(a0 * fmaf(k1 * a0, a0, k0));
+    const float t1 = tanh_approx(a1 * fmaf(k1 * a1, a1, k0));
+    const float h0 = 0.5f * a0, h1 = 0.5f * a1;
+    return pack_bf16x2(fmaf(h0, t0, h0), fmaf(h1, t1, h1));
+  }
+}
 
 __device__ __forceinline__ void named_barrier_sync(int id, int threads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
@@ -250,7 +273,7 @@ __device__ __forceinline__ void mma_issuer(const Bf16Params& P, int s, uint32_t 
 
 // Epilogue of one warp: slot s, row quadrant q (TMEM lanes / tile rows 32q..32q+31),
 // member JJ of the column pair (in K half h it owns columns h*H/2 + JJ*H/4 .. + H/4 - 1).
-template <int H, int NH, int JJ>
+template <int H, int NH, int JJ, int ACT>
 __device__ __forceinline__ void epilogue(const Bf16Params& P, int s, int q, int lane, uint32_t tmem, uint32_t sA,
                                          uint32_t bar_act0, uint32_t bar_act1, uint32_t bar_acc, uint32_t tok_wait,
                                          uint32_t tok_give, float* half_sum, volatile int* pair_ok,
@@ -322,7 +345,7 @@ __device__ __forceinline__ void epilogue(const Bf16Params& P, int s, int q, int 
             const int col = c0 + 2 * i;
             const float a0 = fmaf(P.w2[col][1], y, fmaf(P.w2[col][0], x, bb[i].x));
             const float a1 = fmaf(P.w2[col + 1][1], y, fmaf(P.w2[col + 1][0], x, bb[i].y));
-            pk[i] = tanh_bf16x2(pack_bf16x2(a0, a1));
+            pk[i] = act_bf16x2<ACT>(a0, a1);
           }
           put(c0, pk);
           signal(h == 0 ? bar_act0 : bar_act1);
@@ -354,7 +377,7 @@ __device__ __forceinline__ void epilogue(const Bf16Params& P, int s, int q, int 
         for (int i = 0; i < CW / 2; ++i) {
           const float a0 = __uint_as_float(v[2 * i]) + P.bias[m - 1][c0 + 2 * i];
           const float a1 = __uint_as_float(v[2 * i + 1]) + P.bias[m - 1][c0 + 2 * i + 1];
-          pk[i] = tanh_bf16x2(pack_bf16x2(a0, a1));
+          pk[i] = act_bf16x2<ACT>(a0, a1);
         }
         if (h == 1) tc_fence_before();
         if (m < NH) {
@@ -388,7 +411,7 @@ __device__ __forceinline__ void epilogue(const Bf16Params& P, int s, int q, int 
   }
 }
 
-template <int H, int NH>
+template <int H, int NH, int ACT>
 __global__ void __launch_bounds__(kThreadsBf16, 1) mlp_bf16_kernel(const __grid_constant__ Bf16Params P) {
   using C = Bf16Cfg<H, NH>;
   extern __shared__ uint8_t smem_raw[];
@@ -445,10 +468,10 @@ __global__ void __launch_bounds__(kThreadsBf16, 1) mlp_bf16_kernel(const __grid_
   } else {
     const int s = warp >> 3, jj = (warp >> 2) & 1, q = warp & 3;
     if (jj == 0)
-      epilogue<H, NH, 0>(P, s, q, lane, tmem, sA, bar(1 + 2 * s), bar(2 + 2 * s), bar(5 + s), bar(9 + s),
+      epilogue<H, NH, 0, ACT>(P, s, q, lane, tmem, sA, bar(1 + 2 * s), bar(2 + 2 * s), bar(5 + s), bar(9 + s),
                          bar(10 - s), half_sum, pair_ok, abort_flag);
     else
-      epilogue<H, NH, 1>(P, s, q, lane, tmem, sA, bar(1 + 2 * s), bar(2 + 2 * s), bar(5 + s), bar(9 + s),
+      epilogue<H, NH, 1, ACT>(P, s, q, lane, tmem, sA, bar(1 + 2 * s), bar(2 + 2 * s), bar(5 + s), bar(9 + s),
                          bar(10 - s), half_sum, pair_ok, abort_flag);
   }
 
@@ -460,19 +483,19 @@ __global__ void __launch_bounds__(kThreadsBf16, 1) mlp_bf16_kernel(const __grid_
   }
 }
 
-template <int H, int NH>
+template <int H, int NH, int ACT>
 cudaError_t launch_t(const Bf16Params& p, cudaStream_t st) {
   using C = Bf16Cfg<H, NH>;
   static int grid_cap = 0;
   static size_t smem_bytes = 0;
   if (grid_cap == 0) {
-    cudaError_t e = cudaFuncSetAttribute(mlp_bf16_kernel<H, NH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(mlp_bf16_kernel<H, NH, ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)C::kSmem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_bf16_kernel<H, NH>, kThreadsBf16, C::kSmem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_bf16_kernel<H, NH, ACT>, kThreadsBf16, C::kSmem);
     if (e != cudaSuccess) return e;
     // every resident CTA must be able to hold its tensor memory at once (512 columns):
     // if shared memory alone would admit more CTAs per SM, request more of it
@@ -482,9 +505,9 @@ cudaError_t launch_t(const Bf16Params& p, cudaStream_t st) {
       int smem_sm = 0;
       cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
       smem_bytes = (size_t)smem_sm / (size_t)(tmem_cap + 1) + 1024;
-      e = cudaFuncSetAttribute(mlp_bf16_kernel<H, NH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+      e = cudaFuncSetAttribute(mlp_bf16_kernel<H, NH, ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
       if (e != cudaSuccess) return e;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_bf16_kernel<H, NH>, kThreadsBf16, smem_bytes);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_bf16_kernel<H, NH, ACT>, kThreadsBf16, smem_bytes);
       if (e != cudaSuccess) return e;
     }
     if (per_sm > tmem_cap || per_sm < 1) return cudaErrorInvalidConfiguration;
@@ -493,8 +516,28 @@ cudaError_t launch_t(const Bf16Params& p, cudaStream_t st) {
   int grid = (p.n_tiles + kSlots - 1) / kSlots;
   if (grid > grid_cap) grid = grid_cap;
   if (grid < 1) return cudaSuccess;
-  mlp_bf16_kernel<H, NH><<<grid, kThreadsBf16, smem_bytes, st>>>(p);
+  mlp_bf16_kernel<H, NH, ACT><<<grid, kThreadsBf16, smem_bytes, st>>>(p);
   return cudaGetLastError();
+}
+
+template <int ACT>
+cudaError_t dispatch(const DevNet& net, const Bf16Params& p, cudaStream_t st) {
+  if (net.width == 128) {
+    switch (net.n_hidden) {
+      case 1: return launch_t<128, 1, ACT>(p, st);
+      case 2: return launch_t<128, 2, ACT>(p, st);
+      case 3: return launch_t<128, 3, ACT>(p, st);
+      case 4: return launch_t<128, 4, ACT>(p, st);
+      default: return launch_t<128, 5, ACT>(p, st);
+    }
+  }
+  switch (net.n_hidden) {
+    case 1: return launch_t<64, 1, ACT>(p, st);
+    case 2: return launch_t<64, 2, ACT>(p, st);
+    case 3: return launch_t<64, 3, ACT>(p, st);
+    case 4: return launch_t<64, 4, ACT>(p, st);
+    default: return launch_t<64, 5, ACT>(p, st);
+  }
 }
 
 }  // namespace
@@ -524,22 +567,8 @@ cudaError_t launch_mlp_bf16(const float* B, const ColourGeom& g, const DevNet& n
     p.w2[j][0] = j < net.width ? net.h_W2[2 * j] : 0.f;
     p.w2[j][1] = j < net.width ? net.h_W2[2 * j + 1] : 0.f;
   }
-  if (net.width == 128) {
-    switch (net.n_hidden) {
-      case 1: return launch_t<128, 1>(p, st);
-      case 2: return launch_t<128, 2>(p, st);
-      case 3: return launch_t<128, 3>(p, st);
-      case 4: return launch_t<128, 4>(p, st);
-      default: return launch_t<128, 5>(p, st);
-    }
-  }
-  switch (net.n_hidden) {
-    case 1: return launch_t<64, 1>(p, st);
-    case 2: return launch_t<64, 2>(p, st);
-    case 3: return launch_t<64, 3>(p, st);
-    case 4: return launch_t<64, 4>(p, st);
-    default: return launch_t<64, 5>(p, st);
-  }
+  if (net.act == kActGelu) return dispatch<kActGelu>(net, p, st);
+  return dispatch<kActTanh>(net, p, st);
 }
 
 }  // namespace mf

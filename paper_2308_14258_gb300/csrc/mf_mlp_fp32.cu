@@ -2,13 +2,13 @@
 //
 // Rows r = (subdomain s, interior point p) of the colour are processed in tiles of 128.
 // Per row the first layer is the input-split form of Eq. 8: tanh(B[s] + W2 x_p), with
-// B[s] = W1 g_s + b0 from K1; then depth-1 hidden layers tanh(W h + b) and the linear
-// output w_out . h + b_out (Section 3.1-3.2, activation tanh). Activations stay in
+// B[s] = W1 g_s + b0 from K1; then depth-1 hidden layers act(W h + b) and the linear
+// output w_out . h + b_out (Section 3.1-3.2; act = tanh, or GELU for the variant). Activations stay in
 // shared memory k-major (act[k][row]); each hidden layer is a 128 x H x H SIMT GEMM
 // with an 8 x (H/16) register tile per thread, its weights streamed from L2 with
 // cp.async into a double buffer while the previous layer computes. tanh is CUDA's
-// accurate tanhf (no approximate hardware tanh), which keeps this path within 1e-5 of
-// the FP64 oracle. The prediction of each row is written to its grid point (store for
+// accurate tanhf and GELU uses erff (no approximate hardware tanh), which keeps this
+// path within 1e-5 of the FP64 oracle. The prediction of each row is written to its grid point (store for
 // the multiplicative schedule, weighted add for the additive one).
 #include "mf_internal.cuh"
 
@@ -47,7 +47,7 @@ __device__ __forceinline__ void load_layer(float* dst, const float* __restrict__
   }
 }
 
-template <int H>
+template <int H, int ACT>
 __global__ void __launch_bounds__(kThreads)
 mlp_fp32_kernel(const float* __restrict__ B, ColourGeom g, int n_rows, const float* __restrict__ W2,
                 const float* __restrict__ WhT, const float* __restrict__ bh, const float* __restrict__ wout,
@@ -74,7 +74,7 @@ mlp_fp32_kernel(const float* __restrict__ B, ColourGeom g, int n_rows, const flo
     const float* Bs = B + (size_t)site.s * H;
     for (int k = half; k < H; k += 2) {
       const float2 w = __ldg(reinterpret_cast<const float2*>(W2) + k);
-      act[k * kLda + r] = tanhf(fmaf(w.y, y, fmaf(w.x, x, __ldg(Bs + k))));
+      act[k * kLda + r] = act_exact<ACT>(fmaf(w.y, y, fmaf(w.x, x, __ldg(Bs + k))));
     }
   }
 
@@ -120,10 +120,10 @@ mlp_fp32_kernel(const float* __restrict__ B, ColourGeom g, int n_rows, const flo
 #pragma unroll
         for (int rg = 0; rg < 2; ++rg) {
           float4 v;
-          v.x = tanhf(acc[4 * rg + 0][4 * cg + j] + bn);
-          v.y = tanhf(acc[4 * rg + 1][4 * cg + j] + bn);
-          v.z = tanhf(acc[4 * rg + 2][4 * cg + j] + bn);
-          v.w = tanhf(acc[4 * rg + 3][4 * cg + j] + bn);
+          v.x = act_exact<ACT>(acc[4 * rg + 0][4 * cg + j] + bn);
+          v.y = act_exact<ACT>(acc[4 * rg + 1][4 * cg + j] + bn);
+          v.z = act_exact<ACT>(acc[4 * rg + 2][4 * cg + j] + bn);
+          v.w = act_exact<ACT>(acc[4 * rg + 3][4 * cg + j] + bn);
           *reinterpret_cast<float4*>(act + n * kLda + 64 * rg + 4 * tr) = v;
         }
       }
@@ -152,7 +152,7 @@ mlp_fp32_kernel(const float* __restrict__ B, ColourGeom g, int n_rows, const flo
   }
 }
 
-template <int H>
+template <int H, int ACT>
 cudaError_t launch_h(const float* B, const ColourGeom& g, const DevNet& net, float* u, int additive,
                      cudaStream_t st) {
   const int n_rows = g.n_c * g.rows_per_sub;
@@ -160,11 +160,12 @@ cudaError_t launch_h(const float* B, const ColourGeom& g, const DevNet& net, flo
   const size_t smem = Fp32Cfg<H>::kSmem;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(mlp_fp32_kernel<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(mlp_fp32_kernel<H, ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  mlp_fp32_kernel<H><<<tiles, kThreads, smem, st>>>(B, g, n_rows, net.W2, net.WhT, net.bh, net.wout, net.bout,
+  mlp_fp32_kernel<H, ACT><<<tiles, kThreads, smem, st>>>(B, g, n_rows, net.W2, net.WhT, net.bh, net.wout, net.bout,
                                                      net.n_hidden, u, additive);
   return cudaGetLastError();
 }
@@ -174,7 +175,11 @@ cudaError_t launch_h(const float* B, const ColourGeom& g, const DevNet& net, flo
 cudaError_t launch_mlp_fp32(const float* B, const ColourGeom& g, const DevNet& net, float* u, int additive,
                             cudaStream_t st) {
   if (g.n_c <= 0) return cudaSuccess;
-  return net.width == 128 ? launch_h<128>(B, g, net, u, additive, st) : launch_h<64>(B, g, net, u, additive, st);
+  if (net.act == kActGelu)
+    return net.width == 128 ? launch_h<128, kActGelu>(B, g, net, u, additive, st)
+                            : launch_h<64, kActGelu>(B, g, net, u, additive, st);
+  return net.width == 128 ? launch_h<128, kActTanh>(B, g, net, u, additive, st)
+                          : launch_h<64, kActTanh>(B, g, net, u, additive, st);
 }
 
 }  // namespace mf

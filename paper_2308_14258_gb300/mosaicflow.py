@@ -28,9 +28,10 @@ PREC = {"fp32": 0, "bf16": 1, "mixed": 2}
 SCHEDULE = {"M": 0, "multiplicative": 0, "A": 1, "additive": 1}
 QUERY = {"full": 0, "centre": 1, "center": 1}
 OPTIMIZER = {"sgd": 0, "lamb": 1}
+ACTIVATION = {"tanh": 0, "gelu": 1}
 
 # Every exported symbol the header declares (checked by the CPU test suite).
-EXPORTS = ["mf_last_error", "mf_version", "mf_load_sdnet", "mf_free_sdnet", "mf_create_grid",
+EXPORTS = ["mf_last_error", "mf_version", "mf_load_sdnet", "mf_load_sdnet_ex", "mf_free_sdnet", "mf_create_grid",
            "mf_destroy_grid", "mf_grid_dims", "mf_grid_upload", "mf_grid_download", "mf_sweep",
            "mf_residual", "mf_synchronize", "mf_sweep_noalloc", "mf_create_batch", "mf_destroy_batch",
            "mf_batch_info", "mf_batch_upload", "mf_batch_download", "mf_batch_sweep", "mf_batch_residual",
@@ -46,6 +47,11 @@ class MFError(RuntimeError):
 
 class SDNetDesc(C.Structure):
     _fields_ = [("width", C.c_int), ("depth", C.c_int)]
+
+
+class SDNetDescEx(C.Structure):
+    _fields_ = [("width", C.c_int), ("depth", C.c_int), ("activation", C.c_int),
+                ("embed_channels", C.c_int), ("embed_kernel", C.c_int)]
 
 
 class GridDesc(C.Structure):
@@ -90,6 +96,7 @@ def load(path: str | None = None) -> C.CDLL:
     lib.mf_last_error.restype = C.c_char_p
     lib.mf_version.restype = i
     lib.mf_load_sdnet.argtypes = [C.POINTER(SDNetDesc), vp, C.POINTER(vp)]
+    lib.mf_load_sdnet_ex.argtypes = [C.POINTER(SDNetDescEx), vp, C.POINTER(vp)]
     lib.mf_free_sdnet.argtypes = [vp]
     lib.mf_create_grid.argtypes = [C.POINTER(GridDesc), vp, C.POINTER(vp)]
     lib.mf_destroy_grid.argtypes = [vp]
@@ -148,13 +155,19 @@ def _buffer(arr):
 
 
 class SDNet:
-    """mf_load_sdnet / mf_free_sdnet."""
+    """mf_load_sdnet / mf_load_sdnet_ex / mf_free_sdnet. activation "tanh" or "gelu";
+    embed_channels > 0 adds the conv1d boundary embedding (kernel size embed_kernel)."""
 
-    def __init__(self, weights: np.ndarray, width: int, depth: int):
+    def __init__(self, weights: np.ndarray, width: int, depth: int, activation: str = "tanh",
+                 embed_channels: int = 0, embed_kernel: int = 0):
         w = np.ascontiguousarray(weights, dtype=np.float32)
         self.width, self.depth = width, depth
         self._h = C.c_void_p()
-        _check(load().mf_load_sdnet(C.byref(SDNetDesc(width, depth)), w.ctypes.data, C.byref(self._h)))
+        if activation == "tanh" and embed_channels == 0:
+            _check(load().mf_load_sdnet(C.byref(SDNetDesc(width, depth)), w.ctypes.data, C.byref(self._h)))
+        else:
+            d = SDNetDescEx(width, depth, ACTIVATION[activation], embed_channels, embed_kernel)
+            _check(load().mf_load_sdnet_ex(C.byref(d), w.ctypes.data, C.byref(self._h)))
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:

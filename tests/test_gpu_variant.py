@@ -1,0 +1,157 @@
+"""The SDNet variant of Section 3.1 (GELU activations, circular conv1d boundary
+embedding) on the GPU against the FP64 oracle, through the C ABI.
+
+Error measure and tolerances as for the tanh network: one sweep from an identical FP32
+state, e = max |u_gpu - u_oracle| / max |u_oracle|; FP32 path 1e-5 (exact GELU with
+erff), BF16 path 3e-2 (BF16 operands, GELU in its tanh form)."""
+import numpy as np
+import pytest
+
+from oracle import mosaic_flow as orc
+from paper_2308_14258_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-5, "bf16": 3e-2}
+VARIANTS = [
+    # (width, depth, activation, embed channels, kernel)
+    (128, 6, "gelu", 8, 5),   # the paper's form: embedding + GELU
+    (64, 4, "gelu", 0, 0),    # GELU on the raw boundary
+    (64, 3, "tanh", 4, 3),    # embedding with tanh
+    (128, 2, "gelu", 16, 9),  # largest embedding, one hidden layer
+]
+
+
+@pytest.fixture(scope="module")
+def m():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2308_14258_gb300 import mosaicflow
+    return mosaicflow
+
+
+def setup(m, lx, ly, v, seed):
+    width, depth, act, c, k = v
+    shape = I.SDNetShape(width, depth, act, c, k)
+    w = I.xavier_sdnet(shape, seed, bias_scale=0.1)
+    bc = I.bc_values(lx, ly, I.mode_field(I.mode_coeffs(seed + 100), lx, ly))
+    u0 = orc.make_grid(lx, ly, bc)
+    ny, nx = u0.shape
+    u0[1:-1, 1:-1] = I.Stream(seed + 200, I.TAG_TEST).normal((ny - 2) * (nx - 2)).reshape(ny - 2, nx - 2) * 0.3
+    u0 = u0.astype(np.float32)
+    net = m.SDNet(w, width, depth, act, c, k)
+    solver = orc.Solver(orc.unpack_sdnet(w, width, depth, act, c, k))
+    return net, solver, bc, u0
+
+
+def rel_err(got, ref):
+    return float(np.abs(got.astype(np.float64) - ref).max() / np.abs(ref).max())
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("v", VARIANTS)
+def test_one_sweep_multiplicative(m, prec, v):
+    lx, ly = 3, 2
+    net, solver, bc, u0 = setup(m, lx, ly, v, 1)
+    g = m.Grid(lx, ly, bc)
+    g.upload(u0)
+    g.sweep(net, 1, "M", prec)
+    ref = orc.sweep_multiplicative(u0.astype(np.float64), lx, ly, solver)
+    assert rel_err(g.download(), ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_one_sweep_additive(m, prec):
+    lx, ly = 2, 3
+    net, solver, bc, u0 = setup(m, lx, ly, VARIANTS[0], 2)
+    g = m.Grid(lx, ly, bc)
+    g.upload(u0)
+    g.sweep(net, 1, "A", prec)
+    ref = orc.sweep_additive(u0.astype(np.float64), lx, ly, solver)
+    assert rel_err(g.download(), ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_centre_line_sweep(m, prec):
+    lx, ly = 3, 3
+    net, solver, bc, u0 = setup(m, lx, ly, VARIANTS[0], 3)
+    g = m.Grid(lx, ly, bc)
+    g.upload(u0)
+    g.sweep(net, 1, "M", prec, query="centre")
+    ref = orc.sweep_multiplicative(u0.astype(np.float64), lx, ly, solver, query="centre")
+    assert rel_err(g.download(), ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_batch_of_uneven_problems(m, prec):
+    v = VARIANTS[0]
+    width, depth, act, c, k = v
+    w = I.xavier_sdnet(I.SDNetShape(width, depth, act, c, k), 4, bias_scale=0.1)
+    net = m.SDNet(w, width, depth, act, c, k)
+    solver = orc.Solver(orc.unpack_sdnet(w, width, depth, act, c, k))
+    sizes = [(1, 1), (2, 3), (3, 2)]
+    bcs = [I.bc_values(a, b, I.mode_field(I.mode_coeffs(300 + q), a, b)) for q, (a, b) in enumerate(sizes)]
+    bt = m.Batch(sizes, bcs)
+    states = []
+    for q, ((a, b), bc) in enumerate(zip(sizes, bcs)):
+        u0 = orc.make_grid(a, b, bc)
+        ny, nx = u0.shape
+        u0[1:-1, 1:-1] = I.Stream(400 + q, I.TAG_TEST).normal((ny - 2) * (nx - 2)).reshape(ny - 2, nx - 2) * 0.3
+        u0 = u0.astype(np.float32)
+        bt.upload(q, u0)
+        states.append(u0)
+    bt.sweep(net, 1, prec)
+    for q, (a, b) in enumerate(sizes):
+        ref = orc.sweep_multiplicative(states[q].astype(np.float64), a, b, solver)
+        assert rel_err(bt.download(q), ref) <= TOL[prec], q
+
+
+def test_large_sampled_colour(m):
+    """The benchmark grid (2049 x 2049, 16129 subdomains) with the 6 x 128 variant in the
+    benchmark's launch configuration: one colour alone, sampled subdomains against the
+    oracle from the same state, all points outside the colour's interiors unchanged."""
+    width, depth, act, c, k = VARIANTS[0]
+    w = I.xavier_sdnet(I.SDNetShape(width, depth, act, c, k), 2)
+    p = I.large().problems[0]
+    net = m.SDNet(w, width, depth, act, c, k)
+    solver = orc.Solver(orc.unpack_sdnet(w, width, depth, act, c, k))
+    rng = np.random.default_rng(1)
+    for prec in ("bf16", "fp32"):
+        g = m.Grid(p.lx, p.ly, p.bc)
+        g.sweep(net, 1, "M", prec)
+        pre = g.download()
+        g.sweep(net, 1, "M", prec, colours=1 << 3)
+        post = g.download()
+        subs = orc.subdomains_of_colour(p.lx, p.ly, 3)
+        pick = [subs[i] for i in rng.choice(len(subs), 16, replace=False)] + [subs[0], subs[-1]]
+        V = solver.solve_batch(np.stack([orc.gather(pre.astype(np.float64), a, b) for (a, b) in pick]))
+        scale = np.abs(pre).max()
+        for (a, b), vv in zip(pick, V):
+            blk = post[16 * b + 1:16 * b + 32, 16 * a + 1:16 * a + 32].astype(np.float64).ravel()
+            assert np.abs(blk - vv).max() / scale <= TOL[prec], (prec, a, b)
+        mask = np.ones(pre.shape, dtype=bool)
+        for (a, b) in subs:
+            mask[16 * b + 1:16 * b + 32, 16 * a + 1:16 * a + 32] = False
+        assert np.array_equal(pre[mask], post[mask])
+
+
+def test_noalloc_sweep_with_variant(m):
+    import torch
+    lx, ly = 2, 2
+    net, solver, bc, u0 = setup(m, lx, ly, VARIANTS[0], 5)
+    u = torch.from_numpy(u0.copy()).cuda()
+    m.sweep_noalloc(u, lx, ly, net, 1, "fp32")
+    ref = orc.sweep_multiplicative(u0.astype(np.float64), lx, ly, solver)
+    assert rel_err(u.cpu().numpy(), ref) <= TOL["fp32"]
+
+
+def test_invalid_variant_options(m):
+    w = I.xavier_sdnet(I.SDNetShape(64, 3, "gelu", 4, 3), 0)
+    for act, c, k in (("gelu", 17, 3), ("gelu", 4, 4), ("gelu", 4, 11), ("gelu", -1, 3)):
+        with pytest.raises(m.MFError) as e:
+            m.SDNet(w, 64, 3, act, c, k)
+        assert e.value.status == m.MF_ERR_INVALID_ARG
+    d = m.SDNetDescEx(64, 3, 2, 0, 0)     # unknown activation code
+    import ctypes as C
+    h = C.c_void_p()
+    assert m.load().mf_load_sdnet_ex(C.byref(d), w.ctypes.data, C.byref(h)) == m.MF_ERR_INVALID_ARG
