@@ -262,6 +262,9 @@ mf_status mf_check_wait_timeout(double limit_ms, int* waits_gave_up);
 #define MF_OPT_SGD 0  /* w -= lr g */
 #define MF_OPT_LAMB 1 /* LAMB (You et al., ICLR 2020): Adam moments, trust ratio ||w||/||r|| per tensor */
 
+#define MF_TRAIN_ENGINE_AUTO 0 /* fused tensor-core layer kernels for BF16 at width 128, else GEMM */
+#define MF_TRAIN_ENGINE_GEMM 1 /* layer GEMMs through cuBLAS, elementwise steps in own kernels */
+
 typedef struct mf_trainer mf_trainer; /* device weights, optimiser state and training scratch */
 
 typedef struct {
@@ -272,13 +275,17 @@ typedef struct {
   int max_functions; /* functions per chunk (>= 1); a call with more functions runs in chunks */
   int max_points;    /* largest Nc or Nb of any call: a multiple of 64 */
   float beta1, beta2, eps, weight_decay; /* LAMB hyper-parameters (ignored by SGD) */
+  int engine;        /* MF_TRAIN_ENGINE_AUTO or MF_TRAIN_ENGINE_GEMM (same results to rounding) */
 } mf_train_desc;
 
 /* mf_create_trainer -- device state for training one SDNet on the current device.
  * `weights`: host FP32 parameters in the mf_load_sdnet packing, copied during the call.
  * Device memory grows with max_functions * max_points * width * depth (about 20 GB at
- * 1024 x 1024 x 128 x 6 in BF16): a chunk of functions is processed at a time, so
- * max_functions bounds memory without bounding the batch.
+ * 1024 x 1024 x 128 x 6 in BF16 with the GEMM engine, 8 GB with the fused engine): a
+ * chunk of functions is processed at a time, so max_functions bounds memory without
+ * bounding the batch. The fused engine (BF16, width 128) runs each layer as one
+ * tensor-core kernel that recomputes pre-activations in the backward pass instead of
+ * storing them; the GEMM engine stores them and calls cuBLAS for the layer GEMMs.
  * Errors: MF_ERR_INVALID_ARG (null pointer, unsupported option, non-finite weight,
  * 4 * max_functions * max_points above 2^31 - 1), MF_ERR_OUT_OF_MEMORY, MF_ERR_CUDA.
  * Synchronous. */
@@ -305,7 +312,7 @@ mf_status mf_trainer_get_grads(const mf_trainer* trainer, float* dst, int dst_on
  * and at most max_points; F >= 1. The gradient stays on the device (mf_trainer_get_grads).
  * If loss3 is not NULL it receives (L, L_data, L_pde) in that order. Synchronises `stream`.
  * Errors: MF_ERR_INVALID_ARG, MF_ERR_DIVERGED (a loss term is not finite),
- * MF_ERR_CUDA. */
+ * MF_ERR_TIMEOUT (a bounded wait in a fused kernel gave up), MF_ERR_CUDA. */
 mf_status mf_train_grad(mf_trainer* trainer, int F, int Nc, int Nb, const float* G, const float* Xc,
                         const float* Xb, const float* Yb, double* loss3, void* stream);
 

@@ -23,10 +23,13 @@
 // gradient is input-split as well: sum g_z over each function's points, then one
 // (H x F)(F x 128) product.
 //
-// Layer GEMMs (stacked channels x H times H x H, and the H x H weight gradients) are
-// plain GEMMs and go to cuBLAS with BF16 (or FP32) operands and FP32 accumulation;
-// every other step runs in the kernels below. Reductions use fixed-order block
-// partials, so results do not depend on timing.
+// Two engines run these formulas. The fused engine (BF16, width 128; mf_train_tc.cu)
+// keeps each layer's GEMM and its Taylor-mode epilogue in one tensor-core kernel and
+// moves only BF16 activation and gradient tiles through HBM. The GEMM engine (FP32 or
+// BF16, any width) runs the layer GEMMs (stacked channels x H times H x H, and the
+// H x H weight gradients) as plain cuBLAS GEMMs with FP32 accumulation and every other
+// step in the kernels below. Reductions use fixed-order block partials in both, so
+// results do not depend on timing.
 #include <cublas_v2.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -38,6 +41,7 @@
 
 #include "../../include/mosaicflow.h"
 #include "mf_internal.cuh"
+#include "mf_train_tc.cuh"
 
 namespace mf {
 void set_last_error(const std::string& msg);
@@ -382,6 +386,14 @@ struct mf_trainer {
   unsigned long long* ranges = nullptr;  // LAMB tensor ranges
   int n_groups = 0;
   cublasHandle_t cublas = nullptr;
+  // fused engine
+  bool fused = false;
+  void* timg = nullptr;            // [NH] x (W image, W^T image), BF16 swizzled
+  float* tc_gw = nullptr;          // [CTAs][H][H] per-CTA g_W
+  float* tc_small = nullptr;       // per-CTA g_b [CTAs][2][H], g_wout [CTAs][2][H], g_bout [CTAs][2]
+  double* tc_loss = nullptr;       // [CTAs][2]
+  int* status = nullptr;           // device status word of the fused kernels
+  int* h_status = nullptr;         // pinned mirror
 };
 
 namespace {
@@ -513,6 +525,76 @@ mf_status run_pass(mf_trainer* t, int C, int F, int n, const float* G, const flo
   return MF_OK;
 }
 
+// One pass on the fused engine: the first layer into A_0 tiles, the forward kernels of
+// hidden layers 1..NH-1, then the backward kernels from the top (which also forms the
+// output layer and the loss) down, and the first-layer backward from the gA_0 tiles.
+mf_status run_pass_fused(mf_trainer* t, int C, int F, int n, const float* G, const float* X, const float* Y,
+                         float gscale, double lscale, double* loss_slot, cudaStream_t st) {
+  const int H = t->H, NH = t->NH;
+  const int R = F * n;
+  const int n_tiles = R * C / 64;
+  const size_t img = mf::tc_image_bytes();
+  auto wimg = [&](int l) { return static_cast<const char*>(t->timg) + (size_t)(l - 1) * 2 * img; };
+  const int ctas = mf::tc_partial_ctas(), pg = mf::tc_partial_groups();
+  float* gbp = t->tc_small;
+  float* gwop = gbp + (size_t)ctas * pg * H;
+  float* gbop = gwop + (size_t)ctas * pg * H;
+  TR_BLAS(gemm_boundary(t, G, F), "train: boundary GEMM");
+  TR_CUDA(mf::tc_first_fwd(t->Bf, t->w, t->w + t->off_b0, X, n, R, C, t->A[0], st), "train: first layer");
+  for (int l = 1; l < NH; ++l) {
+    mf::TcFwdParams fp{static_cast<const uint8_t*>(t->A[l - 1]), static_cast<uint8_t*>(t->A[l]), wimg(l),
+                       t->w + t->offb[l], n_tiles, C, t->status};
+    TR_CUDA(mf::tc_layer_fwd(fp, st), "train: fused forward");
+  }
+  uint8_t* gbuf[2] = {static_cast<uint8_t*>(t->gZ), reinterpret_cast<uint8_t*>(t->gA)};
+  int cur = 0;
+  for (int l = NH; l >= 1; --l) {
+    mf::TcBwdParams bp{};
+    bp.A_in = static_cast<const uint8_t*>(t->A[l - 1]);
+    bp.gA_in = l == NH ? nullptr : gbuf[cur];
+    bp.gA_out = gbuf[cur ^ 1];
+    bp.wimg = wimg(l);
+    bp.wimgT = wimg(l) + img;
+    bp.bias = t->w + t->offb[l];
+    bp.gW_part = t->tc_gw;
+    bp.gb_part = gbp;
+    bp.wout = t->w + t->off_wout;
+    bp.bout = t->w + t->off_bout;
+    bp.Y = Y;
+    bp.gscale = gscale;
+    bp.loss_part = t->tc_loss;
+    bp.gwout_part = gwop;
+    bp.gbout_part = gbop;
+    bp.n_tiles = n_tiles;
+    bp.C = C;
+    bp.top = l == NH ? 1 : 0;
+    bp.status = t->status;
+    int grid = 0;
+    TR_CUDA(mf::tc_layer_bwd(bp, &grid, st), "train: fused backward");
+    if (grid > 0) {
+      TR_CUDA(mf::tc_colsum(t->tc_gw, grid, H * H, H * H, t->g + t->offW[l], 1, st), "train: g_W");
+      TR_CUDA(mf::tc_colsum(gbp, pg * grid, H, H, t->g + t->offb[l], 1, st), "train: g_b");
+      if (l == NH) {
+        TR_CUDA(mf::tc_colsum(gwop, pg * grid, H, H, t->g + t->off_wout, 1, st), "train: g_wout");
+        if (C == 1) TR_CUDA(mf::tc_sum_float(gbop, pg * grid, t->g + t->off_bout, st), "train: g_bout");
+        TR_CUDA(mf::tc_sum_double(t->tc_loss, pg * grid, lscale, loss_slot, st), "train: loss");
+      }
+    }
+    cur ^= 1;
+  }
+  // first layer: W2 columns and b0 from all rows, W1 through per-function sums
+  const int nblk = R / kRB;
+  const int ncol = (H + 31) / 32;
+  TR_CUDA(mf::tc_first_bwd(t->Bf, t->w, t->w + t->off_b0, X, n, R, C, gbuf[cur], t->part, st),
+          "train: first layer backward");
+  for (int q = 0; q < 3; ++q) colsum_kernel<<<ncol, 1024, 0, st>>>(t->part + q * H, nblk, 3 * H, H, t->sums + q * H, 0);
+  add_w2_b0_kernel<<<1, H, 0, st>>>(t->sums, H, t->g, t->g + t->off_b0);
+  per_function_sum_kernel<<<F, H, 0, st>>>(t->part, n / kRB, H, t->S);
+  TR_CUDA(cudaGetLastError(), "train: first layer gradients");
+  TR_BLAS(gemm_boundary_grad(t, G, F), "train: boundary gradient GEMM");
+  return MF_OK;
+}
+
 // All functions of one loss term, in chunks of at most max_functions functions.
 mf_status run_term(mf_trainer* t, int C, int F, int n, const float* G, const float* X, const float* Y,
                    double* loss_slot, cudaStream_t st) {
@@ -522,7 +604,9 @@ mf_status run_term(mf_trainer* t, int C, int F, int n, const float* G, const flo
     const float* Gc = G + (size_t)f0 * kNB;
     const float* Xc = X + (size_t)f0 * n * 2;
     const float* Yc = Y ? Y + (size_t)f0 * n : nullptr;
-    mf_status s = t->precision == MF_PREC_BF16
+    mf_status s = t->fused
+                      ? run_pass_fused(t, C, fc, n, Gc, Xc, Yc, (float)(2.0 / npts), 1.0 / npts, loss_slot, st)
+                  : t->precision == MF_PREC_BF16
                       ? run_pass<__nv_bfloat16>(t, C, fc, n, Gc, Xc, Yc, (float)(2.0 / npts), 1.0 / npts, loss_slot, st)
                       : run_pass<float>(t, C, fc, n, Gc, Xc, Yc, (float)(2.0 / npts), 1.0 / npts, loss_slot, st);
     if (s != MF_OK) return s;
@@ -532,6 +616,14 @@ mf_status run_term(mf_trainer* t, int C, int F, int n, const float* G, const flo
 
 mf_status refresh_gemm_weights(mf_trainer* t, cudaStream_t st) {
   const size_t HH = (size_t)t->H * t->H;
+  if (t->fused) {
+    const size_t img = mf::tc_image_bytes();
+    for (int l = 1; l <= t->NH; ++l) {
+      char* base = static_cast<char*>(t->timg) + (size_t)(l - 1) * 2 * img;
+      TR_CUDA(mf::tc_pack_weights(t->w + t->offW[l], base, base + img, st), "train: weight images");
+    }
+    return MF_OK;
+  }
   for (int l = 1; l <= t->NH; ++l) {
     if (t->precision == MF_PREC_BF16)
       convert_kernel<__nv_bfloat16><<<64, 256, 0, st>>>(t->w + t->offW[l],
@@ -566,7 +658,8 @@ mf_status mf_destroy_trainer(mf_trainer* t) {
   cudaFree(t->w); cudaFree(t->g); cudaFree(t->m); cudaFree(t->v); cudaFree(t->r);
   cudaFree(t->wq); cudaFree(t->gA); cudaFree(t->gZ); cudaFree(t->Bf); cudaFree(t->S); cudaFree(t->part); cudaFree(t->sums);
   cudaFree(t->lpart); cudaFree(t->loss); cudaFree(t->ranges);
-  cudaFreeHost(t->h_loss);
+  cudaFree(t->timg); cudaFree(t->tc_gw); cudaFree(t->tc_small); cudaFree(t->tc_loss); cudaFree(t->status);
+  cudaFreeHost(t->h_loss); cudaFreeHost(t->h_status);
   delete t;
   return MF_OK;
 }
@@ -584,6 +677,8 @@ mf_status mf_create_trainer(const mf_train_desc* d, const float* weights, mf_tra
     return tfail(MF_ERR_INVALID_ARG, "mf_create_trainer: precision must be MF_PREC_FP32 or MF_PREC_BF16");
   if (d->optimizer != MF_OPT_SGD && d->optimizer != MF_OPT_LAMB)
     return tfail(MF_ERR_INVALID_ARG, "mf_create_trainer: unknown optimizer");
+  if (d->engine != MF_TRAIN_ENGINE_AUTO && d->engine != MF_TRAIN_ENGINE_GEMM)
+    return tfail(MF_ERR_INVALID_ARG, "mf_create_trainer: unknown engine");
   mf_trainer* t = new mf_trainer();
   cudaGetDevice(&t->device);
   t->H = d->width;
@@ -597,6 +692,7 @@ mf_status mf_create_trainer(const mf_train_desc* d, const float* weights, mf_tra
   t->wd = d->weight_decay;
   t->Fmax = d->max_functions;
   t->Nmax = d->max_points;
+  t->fused = d->engine == MF_TRAIN_ENGINE_AUTO && t->precision == MF_PREC_BF16 && t->H == 128;
   t->Rmax = (size_t)t->Fmax * t->Nmax;
   const size_t H = t->H, HH = H * H;
   t->off_b0 = H * (kNB + 2);
@@ -628,10 +724,24 @@ mf_status mf_create_trainer(const mf_train_desc* d, const float* weights, mf_tra
   t->Z.assign(t->NH + 1, nullptr);
   t->a.assign(t->NH + 1, nullptr);
   for (int l = 0; l <= t->NH; ++l) {
+    if (t->fused) {
+      // activation tiles A_0..A_{NH-1} only: pre-activations are recomputed, never stored
+      if (l < t->NH) alloc(&t->A[l], C4 * es);
+      continue;
+    }
     alloc(&t->A[l], C4 * es);
     alloc((void**)&t->a[l], t->Rmax * H * 4);
     if (l > 0) alloc((void**)&t->Z[l], C4 * 4);
   }
+  if (t->fused) {
+    const size_t ctas = (size_t)mf::tc_partial_ctas();
+    alloc(&t->timg, (size_t)t->NH * 2 * mf::tc_image_bytes());
+    alloc((void**)&t->tc_gw, ctas * HH * 4);
+    const size_t pg = (size_t)mf::tc_partial_groups();
+    alloc((void**)&t->tc_small, (ctas * pg * H * 2 + ctas * pg) * 4);
+    alloc((void**)&t->tc_loss, ctas * pg * 8);
+  }
+  alloc((void**)&t->status, sizeof(int));
   alloc((void**)&t->gA, C4 * 4);
   alloc(&t->gZ, C4 * es);
   alloc((void**)&t->Bf, (size_t)t->Fmax * H * 4);
@@ -641,6 +751,8 @@ mf_status mf_create_trainer(const mf_train_desc* d, const float* weights, mf_tra
   alloc((void**)&t->lpart, nblk_max * 8);
   alloc((void**)&t->loss, 4 * 8);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&t->h_loss, 4 * 8);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&t->h_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(t->status, 0, sizeof(int));
   // LAMB tensor ranges in packed order: W0, b0, {W_l, b_l}, w_out, b_out
   std::vector<unsigned long long> rg;
   rg.push_back(0); rg.push_back(t->off_b0);
@@ -712,13 +824,16 @@ mf_status mf_train_grad(mf_trainer* t, int F, int Nc, int Nb, const float* G, co
   TR_BLAS(cublasSetStream(t->cublas, st), "mf_train_grad: cublasSetStream");
   TR_CUDA(cudaMemsetAsync(t->g, 0, t->n_params * 4, st), "mf_train_grad: zero grads");
   TR_CUDA(cudaMemsetAsync(t->loss, 0, 3 * sizeof(double), st), "mf_train_grad: zero loss");
+  TR_CUDA(cudaMemsetAsync(t->status, 0, sizeof(int), st), "mf_train_grad: reset status");
   // Algorithm 1, step 1: data points (value channel only); step 2: collocation points
   // (four Taylor channels); the gradients of both terms accumulate in t->g.
   s = run_term(t, 1, F, Nb, G, Xb, Yb, t->loss + 1, st);
   if (s == MF_OK) s = run_term(t, 4, F, Nc, G, Xc, nullptr, t->loss + 2, st);
   if (s != MF_OK) return s;
   TR_CUDA(cudaMemcpyAsync(t->h_loss, t->loss, 3 * sizeof(double), cudaMemcpyDeviceToHost, st), "mf_train_grad: loss");
+  TR_CUDA(cudaMemcpyAsync(t->h_status, t->status, sizeof(int), cudaMemcpyDeviceToHost, st), "mf_train_grad: status");
   TR_CUDA(cudaStreamSynchronize(st), "mf_train_grad: synchronize");
+  if (*t->h_status != mf::kDevErrNone) return tfail(MF_ERR_TIMEOUT, "mf_train_grad: a kernel wait timed out");
   if (loss3) {
     loss3[1] = t->h_loss[1];
     loss3[2] = t->h_loss[2];

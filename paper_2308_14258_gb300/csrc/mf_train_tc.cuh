@@ -1,0 +1,58 @@
+// Internal interface of the fused tensor-core training kernels (mf_train_tc.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mf {
+
+// Forward of one hidden layer over all tiles: A_out = Taylor-mode tanh(W A_in^T + b).
+struct TcFwdParams {
+  const uint8_t* A_in;   // tiles of A_{l-1} (BF16, swizzled operand layout)
+  uint8_t* A_out;        // tiles of A_l
+  const void* wimg;      // W_l image, K-major 128-byte swizzle, rows = output features
+  const float* bias;     // b_l [128]
+  int n_tiles;
+  int C;                 // channels per point: 1 (data points) or 4 (collocation points)
+  int* status;           // device status word (bounded waits)
+};
+
+// Backward of one hidden layer over all tiles (top = 1: the last hidden layer, with the
+// output layer and the loss folded in).
+struct TcBwdParams {
+  const uint8_t* A_in;   // tiles of A_{l-1}
+  const uint8_t* gA_in;  // tiles of gA_l (unused at the top)
+  uint8_t* gA_out;       // tiles of gA_{l-1}
+  const void* wimg;      // W_l image
+  const void* wimgT;     // W_l^T image
+  const float* bias;     // b_l
+  float* gW_part;        // [CTAs][128][128] per-CTA g_W
+  float* gb_part;        // [CTAs][4][128] per-CTA g_b (four point quarters)
+  const float* wout;     // top: w_out [128]
+  const float* bout;     // top: b_out (device scalar)
+  const float* Y;        // top, data points: targets per point
+  float gscale;          // top: 2 / (points in the loss term)
+  double* loss_part;     // top: [CTAs][4] sums of squared residuals
+  float* gwout_part;     // top: [CTAs][4][128]
+  float* gbout_part;     // top: [CTAs][4]
+  int n_tiles;
+  int C;
+  int top;
+  int* status;
+};
+
+size_t tc_tile_bytes();     // bytes of one 64 x 128 BF16 tile
+size_t tc_image_bytes();    // bytes of one 128 x 128 BF16 weight image
+int tc_partial_ctas();      // most CTAs a backward launch uses (partial-buffer rows)
+int tc_partial_groups();    // partial sums per CTA of g_b, g_wout, g_bout and the loss
+cudaError_t tc_pack_weights(const float* W, void* img, void* imgT, cudaStream_t st);
+cudaError_t tc_first_fwd(const float* Bf, const float* W0, const float* b0, const float* X, int n, int R, int C,
+                         void* A0, cudaStream_t st);
+cudaError_t tc_first_bwd(const float* Bf, const float* W0, const float* b0, const float* X, int n, int R, int C,
+                         const void* gA0, float* part, cudaStream_t st);
+cudaError_t tc_layer_fwd(const TcFwdParams& p, cudaStream_t st);
+cudaError_t tc_layer_bwd(const TcBwdParams& p, int* grid_used, cudaStream_t st);
+cudaError_t tc_colsum(const float* part, int nblk, int stride, int n, float* out, int accumulate, cudaStream_t st);
+cudaError_t tc_sum_double(const double* part, int n, double scale, double* out, cudaStream_t st);
+cudaError_t tc_sum_float(const float* part, int n, float* out, cudaStream_t st);
+
+}  // namespace mf

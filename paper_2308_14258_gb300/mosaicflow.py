@@ -28,6 +28,7 @@ PREC = {"fp32": 0, "bf16": 1, "mixed": 2}
 SCHEDULE = {"M": 0, "multiplicative": 0, "A": 1, "additive": 1}
 QUERY = {"full": 0, "centre": 1, "center": 1}
 OPTIMIZER = {"sgd": 0, "lamb": 1}
+ENGINE = {"auto": 0, "gemm": 1}
 ACTIVATION = {"tanh": 0, "gelu": 1}
 
 # Every exported symbol the header declares (checked by the CPU test suite).
@@ -73,7 +74,7 @@ class SweepResult(C.Structure):
 class TrainDesc(C.Structure):
     _fields_ = [("width", C.c_int), ("depth", C.c_int), ("precision", C.c_int), ("optimizer", C.c_int),
                 ("max_functions", C.c_int), ("max_points", C.c_int), ("beta1", C.c_float), ("beta2", C.c_float),
-                ("eps", C.c_float), ("weight_decay", C.c_float)]
+                ("eps", C.c_float), ("weight_decay", C.c_float), ("engine", C.c_int)]
 
 
 _lib = None
@@ -333,11 +334,12 @@ class Trainer:
 
     def __init__(self, weights: np.ndarray, width: int, depth: int, precision: str = "bf16",
                  optimizer: str = "lamb", max_functions: int = 1024, max_points: int = 1024,
-                 beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-6, weight_decay: float = 0.0):
+                 beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-6, weight_decay: float = 0.0,
+                 engine: str = "auto"):
         w = np.ascontiguousarray(weights, dtype=np.float32)
         self.width, self.depth, self.n_params = width, depth, w.size
         d = TrainDesc(width, depth, PREC[precision], OPTIMIZER[optimizer], max_functions, max_points,
-                      beta1, beta2, eps, weight_decay)
+                      beta1, beta2, eps, weight_decay, ENGINE[engine])
         self._h = C.c_void_p()
         _check(load().mf_create_trainer(C.byref(d), w.ctypes.data, C.byref(self._h)))
 

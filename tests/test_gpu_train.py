@@ -256,3 +256,43 @@ def test_full_size_workload(m):
     assert abs(lo[1] - ld) <= 3e-2 * ld and pde_close(lo[2], lp, 3e-2), (lo, ld, lp)
     e2, _ = grad_errors(four.grads(), gref)
     assert e2 <= 3e-2, e2
+
+
+@pytest.mark.parametrize("F,Nc,Nb,mf", [
+    (4, 128, 128, 4),    # the paper's 6 x 128 shape, a few tiles
+    (3, 64, 64, 3),      # ragged tile counts per CTA, both passes
+    (5, 192, 128, 2),    # chunks of 2 functions
+    (1, 64, 64, 1),      # one tile per CTA
+])
+def test_fused_engine_matches_gemm_engine_and_oracle(m, F, Nc, Nb, mf):
+    """The fused tensor-core engine (BF16, width 128) against the GEMM engine on the same
+    batch, and both against the FP64 oracle."""
+    width, depth = 128, 6
+    w = I.xavier_sdnet(I.SDNetShape(width, depth), 8, bias_scale=0.1)
+    Gn, Xcn, Xbn, Ybn = batch(F, Nc, Nb, 8)
+    dev = to_dev(Gn, Xcn, Xbn, Ybn)
+    out = {}
+    for engine in ("auto", "gemm"):
+        tr = m.Trainer(w, width, depth, "bf16", "sgd", max_functions=mf, max_points=max(Nc, Nb), engine=engine)
+        out[engine] = (tr.grad(*dev), tr.grads().astype(np.float64))
+    (lt, ld, lp), gref = oracle(w, width, depth, Gn, Xcn, Xbn, Ybn)
+    for engine, (lo, g) in out.items():
+        assert abs(lo[1] - ld) <= 3e-2 * ld and pde_close(lo[2], lp, 3e-2), (engine, lo, ld, lp)
+        e2, emax = grad_errors(g, gref)
+        assert e2 <= 3e-2, (engine, e2, emax)
+    (la, ga), (lg, gg) = out["auto"], out["gemm"]
+    assert np.linalg.norm(ga - gg) <= 2e-2 * np.linalg.norm(gg)
+    assert abs(la[1] - lg[1]) <= 1e-2 * lg[1]
+
+
+def test_fused_engine_training_steps(m):
+    # LAMB steps on the fused engine reduce the loss like the GEMM engine
+    w = I.xavier_sdnet(I.SDNetShape(128, 4), 21)
+    dev = to_dev(*batch(16, 128, 128, 21))
+    losses = {}
+    for engine in ("auto", "gemm"):
+        tr = m.Trainer(w, 128, 4, "bf16", "lamb", max_functions=16, max_points=128, engine=engine)
+        ls = [tr.step(*dev, 5e-3)[0] for _ in range(20)]
+        losses[engine] = ls
+        assert np.isfinite(ls[-1]) and ls[-1] < 0.95 * ls[0], (engine, ls[0], ls[-1])
+    assert abs(losses["auto"][-1] - losses["gemm"][-1]) <= 2e-2 * losses["gemm"][-1]
