@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--no-variant", action="store_true")
+    ap.add_argument("--train-only", action="store_true",
+                    help="run only the training-step measurement and print its JSON object (profiling aid)")
     return ap.parse_args()
 
 
@@ -269,6 +271,92 @@ def run_reference(args, world, rank):
 
 # ------------------------------------------------------------------ GPU arm
 
+def measure_train(args, m, I, torch, np, stream, rank):
+    """Training-step measurement (Eq. 3, Algorithm 1): BF16 fused engine (the reported
+    value), FP32 and the BF16 GEMM engine for comparison, and the BF16 gradient error
+    against the FP64 oracle on sampled functions."""
+    # physics-informed training step (Eq. 3, Algorithm 1): 1024 functions x (1024 collocation
+    # + 128 boundary points), SDNet 6x128, BF16, LAMB; ~8 GB working set (> L2)
+    F, Nc, Nb, H, NH = 1024, 1024, 128, 128, 5
+    tb = I.training_batch(F, Nc, 3)
+    tdev = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+            for a in (tb.G, tb.Xc, tb.Xb, tb.Yb)]
+    tr = m.Trainer(I.xavier_sdnet(I.SDNetShape(H, NH + 1), 4), H, NH + 1, "bf16", "lamb",
+                   max_functions=F, max_points=Nc)
+    for _ in range(3):
+        first_loss = tr.step(*tdev, 1e-3, stream=stream)[0]
+    kt = max(3, min(args.steps, 10))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(kt):
+        last_loss = tr.step(*tdev, 1e-3, stream=stream)[0]
+    e1.record(stream)
+    e1.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    # layer-GEMM flops: forward 2 H^2 per channel and layer, backward twice that;
+    # 4 Taylor channels per collocation point, 1 channel per data point
+    gemm_flop = 3 * 2 * H * H * NH * (4 * F * Nc + F * Nb)
+    train = {"value": kt / t, "unit": "train steps/s", "ms_per_step": 1e3 * t / kt,
+             "workload": f"{F} functions (8-mode harmonic, seed 3) x ({Nc} collocation + {Nb} boundary points), "
+                         "SDNet 6x128 tanh, BF16, fused tensor-core layer kernels (Taylor-mode forward, "
+                         "recomputing backward), LAMB",
+             "gemm_tflop_per_step": gemm_flop / 1e12, "gemm_tflops_achieved": gemm_flop * kt / t / 1e12,
+             "loss_after_warmup": first_loss, "loss_last": last_loss, "l2": "working set ~8 GB (> L2)"}
+    tpeak = load_peaks()[0].get("bf16_tflops_sustained")
+    train["roofline"] = {"bound": "tensor", "achieved": train["gemm_tflops_achieved"], "peak": tpeak,
+                         "unit": "TFLOP/s", "frac": train["gemm_tflops_achieved"] / tpeak,
+                         "note": "whole step: layer-GEMM flops / step time; the fused layer kernels stream "
+                                 "BF16 activation and gradient tiles (~26 GB per step) through HBM"}
+    del tr
+    torch.cuda.empty_cache()
+    # FP32 mode on the same batch (cuBLAS FP32 GEMMs), fewer steps
+    tr = m.Trainer(I.xavier_sdnet(I.SDNetShape(H, NH + 1), 4), H, NH + 1, "fp32", "lamb",
+                   max_functions=F, max_points=Nc)
+    tr.step(*tdev, 1e-3, stream=stream)
+    k32t = 3
+    e0.record(stream)
+    for _ in range(k32t):
+        tr.step(*tdev, 1e-3, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    t32 = e0.elapsed_time(e1) / 1e3
+    train["fp32"] = {"value": k32t / t32, "unit": "train steps/s", "ms_per_step": 1e3 * t32 / k32t,
+                     "engine": "cuBLAS FP32 layer GEMMs"}
+    del tr
+    torch.cuda.empty_cache()
+    tr = m.Trainer(I.xavier_sdnet(I.SDNetShape(H, NH + 1), 4), H, NH + 1, "bf16", "lamb",
+                   max_functions=F, max_points=Nc, engine="gemm")
+    tr.step(*tdev, 1e-3, stream=stream)
+    e0.record(stream)
+    for _ in range(k32t):
+        tr.step(*tdev, 1e-3, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    tg = e0.elapsed_time(e1) / 1e3
+    train["bf16_gemm_engine"] = {"value": k32t / tg, "unit": "train steps/s", "ms_per_step": 1e3 * tg / k32t,
+                                 "engine": "cuBLAS BF16 layer GEMMs + elementwise kernels"}
+    del tr, tdev
+    torch.cuda.empty_cache()
+    # BF16 gradient against the FP64 oracle on 4 sampled functions (full Nc)
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle import pinn
+        sl = slice(0, 4)
+        small = [np.ascontiguousarray(a[sl], dtype=np.float32) for a in (tb.G, tb.Xc, tb.Xb, tb.Yb)]
+        w0 = I.xavier_sdnet(I.SDNetShape(H, NH + 1), 4)
+        (lt, ld, lp), gref = pinn.loss_and_grads(w0.astype(np.float64), H, NH + 1,
+                                                 *[a.astype(np.float64) for a in small])
+        tr = m.Trainer(w0, H, NH + 1, "bf16", "sgd", max_functions=4, max_points=Nc)
+        lo = tr.grad(*[torch.from_numpy(a).cuda() for a in small])
+        g = tr.grads().astype(np.float64)
+        train["err_vs_oracle_bf16"] = {
+            "functions": "0..3 of the batch, initial weights",
+            "grad_rel_l2": float(np.linalg.norm(g - gref) / np.linalg.norm(gref)),
+            "loss_data_rel": abs(lo[1] - ld) / ld, "rms_laplacian_rel": abs(math.sqrt(lo[2]) - math.sqrt(lp)) / math.sqrt(lp)}
+        del tr
+    return train
+
+
 def main():
     args = parse()
     world, rank, local = dist_init()
@@ -295,6 +383,9 @@ def main():
     evals_per_sweep = n_sub * 961
     stream = torch.cuda.Stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    if args.train_only:
+        print(json.dumps({"train": measure_train(args, m, I, torch, np, stream, rank)}))
+        return
 
     def timed_steps(prec, k, profile=True):
         ms, mlp_ms, mlp_launch, launches = [], 0.0, 0, 0
@@ -398,72 +489,7 @@ def main():
             del vgrid
         del vnet
 
-    # physics-informed training step (Eq. 3, Algorithm 1): 1024 functions x (1024 collocation
-    # + 128 boundary points), SDNet 6x128, BF16 layer GEMMs, LAMB; ~20 GB working set (> L2)
-    train = None
-    if args.L == 64 and not args.no_train:
-        F, Nc, Nb, H, NH = 1024, 1024, 128, 128, 5
-        tb = I.training_batch(F, Nc, 3)
-        tdev = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
-                for a in (tb.G, tb.Xc, tb.Xb, tb.Yb)]
-        tr = m.Trainer(I.xavier_sdnet(I.SDNetShape(H, NH + 1), 4), H, NH + 1, "bf16", "lamb",
-                       max_functions=F, max_points=Nc)
-        for _ in range(3):
-            first_loss = tr.step(*tdev, 1e-3, stream=stream)[0]
-        kt = max(3, min(args.steps, 10))
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(kt):
-            last_loss = tr.step(*tdev, 1e-3, stream=stream)[0]
-        e1.record(stream)
-        e1.synchronize()
-        t = e0.elapsed_time(e1) / 1e3
-        # layer-GEMM flops: forward 2 H^2 per channel and layer, backward twice that;
-        # 4 Taylor channels per collocation point, 1 channel per data point
-        gemm_flop = 3 * 2 * H * H * NH * (4 * F * Nc + F * Nb)
-        train = {"value": kt / t, "unit": "train steps/s", "ms_per_step": 1e3 * t / kt,
-                 "workload": f"{F} functions (8-mode harmonic, seed 3) x ({Nc} collocation + {Nb} boundary points), "
-                             "SDNet 6x128 tanh, BF16 layer GEMMs (cuBLAS) + own Taylor-mode kernels, LAMB",
-                 "gemm_tflop_per_step": gemm_flop / 1e12, "gemm_tflops_achieved": gemm_flop * kt / t / 1e12,
-                 "loss_after_warmup": first_loss, "loss_last": last_loss, "l2": "working set ~20 GB (> L2)"}
-        tpeak = load_peaks()[0].get("bf16_tflops_sustained")
-        train["roofline"] = {"bound": "tensor", "achieved": train["gemm_tflops_achieved"], "peak": tpeak,
-                             "unit": "TFLOP/s", "frac": train["gemm_tflops_achieved"] / tpeak,
-                             "note": "whole step: layer-GEMM flops / step time; the step streams ~100 GB "
-                                     "through HBM (layer-by-layer kernels), which sets its time"}
-        del tr
-        torch.cuda.empty_cache()
-        # FP32 mode on the same batch (cuBLAS FP32 GEMMs), fewer steps
-        tr = m.Trainer(I.xavier_sdnet(I.SDNetShape(H, NH + 1), 4), H, NH + 1, "fp32", "lamb",
-                       max_functions=F, max_points=Nc)
-        tr.step(*tdev, 1e-3, stream=stream)
-        k32t = 3
-        e0.record(stream)
-        for _ in range(k32t):
-            tr.step(*tdev, 1e-3, stream=stream)
-        e1.record(stream)
-        e1.synchronize()
-        t32 = e0.elapsed_time(e1) / 1e3
-        train["fp32"] = {"value": k32t / t32, "unit": "train steps/s", "ms_per_step": 1e3 * t32 / k32t}
-        del tr, tdev
-        torch.cuda.empty_cache()
-        # BF16 gradient against the FP64 oracle on 4 sampled functions (full Nc)
-        if rank == 0 and not args.no_cpu_baseline:
-            from oracle import pinn
-            sl = slice(0, 4)
-            small = [np.ascontiguousarray(a[sl], dtype=np.float32) for a in (tb.G, tb.Xc, tb.Xb, tb.Yb)]
-            w0 = I.xavier_sdnet(I.SDNetShape(H, NH + 1), 4)
-            (lt, ld, lp), gref = pinn.loss_and_grads(w0.astype(np.float64), H, NH + 1,
-                                                     *[a.astype(np.float64) for a in small])
-            tr = m.Trainer(w0, H, NH + 1, "bf16", "sgd", max_functions=4, max_points=Nc)
-            lo = tr.grad(*[torch.from_numpy(a).cuda() for a in small])
-            g = tr.grads().astype(np.float64)
-            train["err_vs_oracle_bf16"] = {
-                "functions": "0..3 of the batch, initial weights",
-                "grad_rel_l2": float(np.linalg.norm(g - gref) / np.linalg.norm(gref)),
-                "loss_data_rel": abs(lo[1] - ld) / ld, "rms_laplacian_rel": abs(math.sqrt(lo[2]) - math.sqrt(lp)) / math.sqrt(lp)}
-            del tr
+    train = measure_train(args, m, I, torch, np, stream, rank) if (args.L == 64 and not args.no_train) else None
 
     # end to end through the public API: pinned host grid -> upload -> sweep -> download
     host_in = torch.empty(grid.shape, dtype=torch.float32).pin_memory()

@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) tc_fwd_kernel(const __grid_cons
       int issued = 0;
       for (int it = 0; it < n_it; ++it) {
         const int s = it % kStagesF;
-        if (it >= kStagesF && !wait_spin(S.bar(5 + s), (uint32_t)(((it / kStagesF) - 1) & 1), abort_flag, P.status))
+        if (it >= kStagesF && !wait_bounded(S.bar(5 + s), (uint32_t)(((it / kStagesF) - 1) & 1), abort_flag, P.status, true))
           break;
         const int t = (int)blockIdx.x + it * (int)gridDim.x;
         mbar_arrive_expect_tx(S.bar(1 + s), kTile);
@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
   uint8_t* genBar = gen + (sBar - base);
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(genBar + 8 * kBwdBars);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(genBar + 8 * kBwdBars + 8);
-  float* red = reinterpret_cast<float*>(genBar + 8 * kBwdBars + 16);  // [4 quarters][4 quadrants][16 points]
+  float* red = reinterpret_cast<float*>(genBar + 8 * kBwdBars + 16);  // [2][4 quarters][4 quadrants][16 points]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool top = P.top != 0;
@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
       for (int it = 0; it < n_it; ++it) {
         const int s = it % kStagesB;
         if (it >= kStagesB &&
-            !wait_spin(S.bar(kBInE + s), (uint32_t)(((it / kStagesB) - 1) & 1), abort_flag, P.status))
+            !wait_bounded(S.bar(kBInE + s), (uint32_t)(((it / kStagesB) - 1) & 1), abort_flag, P.status, true))
           break;
         const int t = (int)blockIdx.x + it * (int)gridDim.x;
         mbar_arrive_expect_tx(S.bar(kBInF + s), bytes);
@@ -531,25 +531,31 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
       // top layer: the output layer and the loss, u = w_out . a + b_out (data) or
       // Delta u = w_out . Delta a (collocation), summed over the 128 features by the
       // shuffles of warp_sum_n and the four quadrant warps of this point quarter
+      // a = tanh z and s = sech^2 z of this thread's points, computed once
+      float ta[NP], ts[NP];
+#pragma unroll
+      for (int i = 0; i < NP; ++i) tanh_sech2(z[i], ta[i], ts[i]);
       float gu[NP];
       if (top) {
         float part[NP];
 #pragma unroll
         for (int i = 0; i < NP; ++i) {
-          float a, sd;
-          tanh_sech2(z[i], a, sd);
-          if constexpr (C == 4) part[i] = wo * fmaf(-2.0f * a * sd, zx[i] * zx[i] + zy[i] * zy[i], sd * zl[i]);
-          else part[i] = wo * a;
+          if constexpr (C == 4) part[i] = wo * fmaf(-2.0f * ta[i] * ts[i], zx[i] * zx[i] + zy[i] * zy[i], ts[i] * zl[i]);
+          else part[i] = wo * ta[i];
         }
         int idx;
         const float tot = warp_sum_n<NP>(part, lane, idx);
         constexpr int kLanesPerValue = 32 / NP;
-        if ((lane & (kLanesPerValue - 1)) == 0) red[(pq * 4 + q) * 16 + idx] = tot;
+        // the scratch alternates between tiles, so one barrier per tile suffices: a
+        // quarter's warps rewrite a half only after all of them passed the barrier of
+        // the tile after the one that read it
+        float* rb = red + (it & 1) * 256;
+        if ((lane & (kLanesPerValue - 1)) == 0) rb[(pq * 4 + q) * 16 + idx] = tot;
         named_barrier_sync(2 + pq, 128);
 #pragma unroll
         for (int i = 0; i < NP; ++i) {
-          const float sum = red[(pq * 4 + 0) * 16 + i] + red[(pq * 4 + 1) * 16 + i] + red[(pq * 4 + 2) * 16 + i] +
-                            red[(pq * 4 + 3) * 16 + i];
+          const float sum = rb[(pq * 4 + 0) * 16 + i] + rb[(pq * 4 + 1) * 16 + i] + rb[(pq * 4 + 2) * 16 + i] +
+                            rb[(pq * 4 + 3) * 16 + i];
           float d = sum;                                                       // Delta u
           if constexpr (C == 1) d = sum + *P.bout - P.Y[(size_t)t * PT + p0 + i];  // u - y
           gu[i] = P.gscale * d;
@@ -558,7 +564,6 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
             if constexpr (C == 1) gbo += gu[i];
           }
         }
-        named_barrier_sync(2 + pq, 128);
       }
       if (ok) {
         float o[C][NP];
@@ -579,8 +584,7 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
           }
 #pragma unroll
           for (int i = 0; i < NP; ++i) {
-            float a, sd;
-            tanh_sech2(z[i], a, sd);
+            const float a = ta[i], sd = ts[i];
             const float td = -2.0f * a * sd;
             const float tp = -2.0f * sd * sd + 4.0f * a * a * sd;
             const float q2 = zx[i] * zx[i] + zy[i] * zy[i];
@@ -607,8 +611,7 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
           }
 #pragma unroll
           for (int i = 0; i < NP; ++i) {
-            float a, sd;
-            tanh_sech2(z[i], a, sd);
+            const float a = ta[i], sd = ts[i];
             if (top) gwo = fmaf(gu[i], a, gwo);
             o[0][i] = ga[i] * sd;
             gb += o[0][i];
@@ -809,13 +812,22 @@ __global__ void tc_pack_kernel(const float* __restrict__ W, uint16_t* __restrict
   img[off / 2] = bf16_bits(v);
 }
 
-// out[j] (+)= sum over b < nblk of part[b * stride + j], fixed order (one thread per j).
+// out[j] (+)= sum over b < nblk of part[b * stride + j] (one thread per j): four
+// interleaved partial sums (b mod 4) for latency, combined in a fixed order.
 __global__ void tc_colsum_kernel(const float* __restrict__ part, int nblk, int stride, int n, float* __restrict__ out,
                                  int accumulate) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
-  float s = 0.f;
-  for (int b = 0; b < nblk; ++b) s += part[(size_t)b * stride + j];
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+  int b = 0;
+  for (; b + 4 <= nblk; b += 4) {
+    s0 += part[(size_t)b * stride + j];
+    s1 += part[(size_t)(b + 1) * stride + j];
+    s2 += part[(size_t)(b + 2) * stride + j];
+    s3 += part[(size_t)(b + 3) * stride + j];
+  }
+  for (; b < nblk; ++b) s0 += part[(size_t)b * stride + j];
+  const float s = (s0 + s1) + (s2 + s3);
   out[j] = accumulate ? out[j] + s : s;
 }
 
@@ -835,7 +847,7 @@ __global__ void tc_sum_float_kernel(const float* __restrict__ part, int n, float
 
 constexpr size_t kFwdSmem = 1024 + kWImg + kStagesF * kTile + 2 * kTile + 8 * kFwdBars + 64;
 constexpr size_t kBwdSmem = 1024 + 2 * kWImg + 2 * kStagesB * kTile + 2 * kTile + kTile + 8 * kBwdBars + 16 +
-                            4 * 4 * 16 * 4 + 64;
+                            2 * 4 * 4 * 16 * 4 + 64;
 static_assert(kBwdSmem <= 232448, "backward kernel shared memory");
 
 int grid_for(int n_tiles) {
@@ -908,7 +920,7 @@ cudaError_t tc_layer_bwd(const TcBwdParams& p, int* grid_used, cudaStream_t st) 
 }
 
 cudaError_t tc_colsum(const float* part, int nblk, int stride, int n, float* out, int accumulate, cudaStream_t st) {
-  tc_colsum_kernel<<<(n + 127) / 128, 128, 0, st>>>(part, nblk, stride, n, out, accumulate);
+  tc_colsum_kernel<<<(n + 63) / 64, 64, 0, st>>>(part, nblk, stride, n, out, accumulate);
   return cudaGetLastError();
 }
 
