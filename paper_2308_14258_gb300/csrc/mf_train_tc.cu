@@ -55,7 +55,7 @@ constexpr uint32_t kTile = kTR * kW * 2;       // 16 KB
 constexpr uint32_t kWImg = kW * kW * 2;        // 32 KB
 constexpr int kEpi = 8;                        // epilogue warps
 constexpr int kThreadsTc = (2 + kEpi) * 32;    // MMA warp, load warp, epilogue
-constexpr int kStagesF = 4;                    // input tiles in flight per CTA (forward)
+constexpr int kStagesF = 8;                    // input tiles in flight per CTA (forward)
 constexpr uint32_t kIdescRows = idesc_bf16_bmn(128, kTR);  // B = tile, N = rows (MN-major)
 constexpr uint32_t kIdescGW = idesc_bf16(128, kW);          // B = tile, N = features (K-major)
 
@@ -113,6 +113,23 @@ __device__ __forceinline__ void tanh_sech2(float z, float& a, float& s) {
   s = 4.0f * e * r * r;
 }
 
+// Columns [16 cq, 16 cq + 16) of this warp's 32 TMEM lanes <- K elements [32 cq, 32 cq + 32)
+// of rows 32 q .. 32 q + 31 of a 128 x 128 BF16 image in the K-major 128-byte-swizzled
+// layout (global memory): the A operand of tcgen05.mma held in tensor memory.
+__device__ __forceinline__ void weights_to_tmem(const uint8_t* __restrict__ img, uint32_t tcol, int q, int lane,
+                                                int cq) {
+  const int row = 32 * q + lane;
+  uint32_t v[16];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int chunk = (cq & 1) * 4 + c;
+    const uint4 w = *reinterpret_cast<const uint4*>(img + (size_t)(cq >> 1) * 16384 + (size_t)row * 128 +
+                                                    ((uint32_t)(chunk ^ (row & 7)) << 4));
+    v[4 * c] = w.x; v[4 * c + 1] = w.y; v[4 * c + 2] = w.z; v[4 * c + 3] = w.w;
+  }
+  tmem_st16(tcol + ((uint32_t)(32 * q) << 16) + (uint32_t)(16 * cq), v);
+}
+
 // Points and GEMM rows of a tile for C channels.
 __device__ __forceinline__ int pts_per_tile(int C) { return kTR / C; }
 
@@ -123,17 +140,16 @@ struct Smem {
 
 // ------------------------------------------------------------------ forward kernel
 
-// barriers: 0 weights; 1+s in_full[s]; 5+s in_empty[s]; 9+b acc_full[b]; 11+b acc_empty[b];
-// 13 drain
-constexpr int kFwdBars = 14;
+// barriers: 1+s in_full[s]; 9+s in_empty[s]; 17+b acc_full[b]; 19+b acc_empty[b]; 21 drain
+constexpr int kFwdBars = 22;
+enum { kFInF = 1, kFInE = 9, kFAccF = 17, kFAccE = 19, kFDrain = 21 };
 
 __global__ void __launch_bounds__(kThreadsTc, 1) tc_fwd_kernel(const __grid_constant__ TcFwdParams P) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_addr(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* gen = smem_raw + (base - raw);
-  const uint32_t sW = base;
-  const uint32_t sIn = sW + kWImg;                       // kStagesF tiles
+  const uint32_t sIn = base;                             // kStagesF tiles
   const uint32_t sOut = sIn + kStagesF * kTile;          // 2 staging tiles
   const uint32_t sBar = sOut + 2 * kTile;
   Smem S{sBar};
@@ -144,47 +160,53 @@ __global__ void __launch_bounds__(kThreadsTc, 1) tc_fwd_kernel(const __grid_cons
   const int C = P.C, PT = pts_per_tile(C);
   const int n_it = P.n_tiles > (int)blockIdx.x ? (P.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   if (threadIdx.x == 0) {
-    mbar_init(S.bar(0), 1);
-    for (int s = 0; s < kStagesF; ++s) { mbar_init(S.bar(1 + s), 1); mbar_init(S.bar(5 + s), 1); }
-    for (int b = 0; b < 2; ++b) { mbar_init(S.bar(9 + b), 1); mbar_init(S.bar(11 + b), kEpi); }
-    mbar_init(S.bar(13), 1);
+    for (int s = 0; s < kStagesF; ++s) { mbar_init(S.bar(kFInF + s), 1); mbar_init(S.bar(kFInE + s), 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(S.bar(kFAccF + b), 1); mbar_init(S.bar(kFAccE + b), kEpi); }
+    mbar_init(S.bar(kFDrain), 1);
     *abort_flag = 0;
     fence_barrier_init();
   }
   if (warp == 0) {
-    tmem_alloc(smem_addr(tmem_holder), 128);
+    tmem_alloc(smem_addr(tmem_holder), 256);
     tmem_relinquish();
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
+  // TMEM columns: accumulators [0, 128) (two buffers of 64), W as the A operand [128, 192)
+  const uint32_t Wt = tmem + 128;
+  if (warp >= 2) {
+    const int e = warp - 2;
+    weights_to_tmem(static_cast<const uint8_t*>(P.wimg), Wt, warp & 3, lane, 2 * (e >> 2));
+    weights_to_tmem(static_cast<const uint8_t*>(P.wimg), Wt, warp & 3, lane, 2 * (e >> 2) + 1);
+    tmem_wait_st();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
 
   if (warp == 0) {
     if (lane == 0) {
-      mbar_arrive_expect_tx(S.bar(0), kWImg);
-      bulk_g2s(sW, P.wimg, kWImg, S.bar(0));
-      bool ok = wait_bounded(S.bar(0), 0, abort_flag, P.status, true);
-      const uint64_t wd = desc_sw128(sW);
+      bool ok = true;
       for (int it = 0; ok && it < n_it; ++it) {
         const int s = it % kStagesF, b = it & 1;
-        ok = wait_spin(S.bar(1 + s), (uint32_t)((it / kStagesF) & 1), abort_flag, P.status);
-        if (ok && it >= 2) ok = wait_spin(S.bar(11 + b), (uint32_t)(((it >> 1) - 1) & 1), abort_flag, P.status);
+        ok = wait_spin(S.bar(kFInF + s), (uint32_t)((it / kStagesF) & 1), abort_flag, P.status);
+        if (ok && it >= 2) ok = wait_spin(S.bar(kFAccE + b), (uint32_t)(((it >> 1) - 1) & 1), abort_flag, P.status);
         if (!ok) break;
         tc_fence_after();
         const uint32_t tin = sIn + (uint32_t)s * kTile;
         const uint32_t acc = tmem + (uint32_t)(b * kTR);
 #pragma unroll
         for (int ks = 0; ks < kW / 16; ++ks) {
-          const uint64_t a_op = desc_add(wd, kstep_off(kW, ks));
-          if (ks == 0) mma_ss<0>(acc, a_op, desc_rows(tin, ks), kIdescRows);
-          else mma_ss<1>(acc, a_op, desc_rows(tin, ks), kIdescRows);
+          if (ks == 0) mma_ts<0>(acc, Wt + (uint32_t)(8 * ks), desc_rows(tin, ks), kIdescRows);
+          else mma_ts<1>(acc, Wt + (uint32_t)(8 * ks), desc_rows(tin, ks), kIdescRows);
         }
-        mma_commit(S.bar(9 + b));
-        mma_commit(S.bar(5 + s));
+        mma_commit(S.bar(kFAccF + b));
+        mma_commit(S.bar(kFInE + s));
       }
-      mma_commit(S.bar(13));
-      wait_bounded(S.bar(13), 0, abort_flag, P.status, false);
+      mma_commit(S.bar(kFDrain));
+      wait_bounded(S.bar(kFDrain), 0, abort_flag, P.status, false);
     }
     __syncwarp();
   } else if (warp == 1) {
@@ -192,16 +214,17 @@ __global__ void __launch_bounds__(kThreadsTc, 1) tc_fwd_kernel(const __grid_cons
       int issued = 0;
       for (int it = 0; it < n_it; ++it) {
         const int s = it % kStagesF;
-        if (it >= kStagesF && !wait_bounded(S.bar(5 + s), (uint32_t)(((it / kStagesF) - 1) & 1), abort_flag, P.status, true))
+        if (it >= kStagesF &&
+            !wait_bounded(S.bar(kFInE + s), (uint32_t)(((it / kStagesF) - 1) & 1), abort_flag, P.status, true))
           break;
         const int t = (int)blockIdx.x + it * (int)gridDim.x;
-        mbar_arrive_expect_tx(S.bar(1 + s), kTile);
-        bulk_g2s(sIn + (uint32_t)s * kTile, P.A_in + (size_t)t * kTile, kTile, S.bar(1 + s));
+        mbar_arrive_expect_tx(S.bar(kFInF + s), kTile);
+        bulk_g2s(sIn + (uint32_t)s * kTile, P.A_in + (size_t)t * kTile, kTile, S.bar(kFInF + s));
         issued = it + 1;
       }
       // every load issued has landed before shared memory can go away
       for (int it = (issued > kStagesF ? issued - kStagesF : 0); it < issued; ++it)
-        wait_bounded(S.bar(1 + it % kStagesF), (uint32_t)((it / kStagesF) & 1), abort_flag, P.status, false);
+        wait_bounded(S.bar(kFInF + it % kStagesF), (uint32_t)((it / kStagesF) & 1), abort_flag, P.status, false);
     }
     __syncwarp();
   } else {
@@ -215,7 +238,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) tc_fwd_kernel(const __grid_cons
     for (int it = 0; it < n_it; ++it) {
       const int b = it & 1;
       const int t = (int)blockIdx.x + it * (int)gridDim.x;
-      if (ok) ok = wait_warp(S.bar(9 + b), (uint32_t)((it >> 1) & 1), abort_flag, P.status);
+      if (ok) ok = wait_warp(S.bar(kFAccF + b), (uint32_t)((it >> 1) & 1), abort_flag, P.status);
       const uint32_t stage = sOut + (uint32_t)b * kTile;
       if (ok) {
         tc_fence_after();
@@ -227,7 +250,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) tc_fwd_kernel(const __grid_cons
           tmem_wait_ld();
           tc_fence_before();
           __syncwarp();
-          if (lane == 0) mbar_arrive(S.bar(11 + b));
+          if (lane == 0) mbar_arrive(S.bar(kFAccE + b));
           float o[4][8];
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
@@ -252,7 +275,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) tc_fwd_kernel(const __grid_cons
           tmem_wait_ld();
           tc_fence_before();
           __syncwarp();
-          if (lane == 0) mbar_arrive(S.bar(11 + b));
+          if (lane == 0) mbar_arrive(S.bar(kFAccE + b));
           float o[32];
 #pragma unroll
           for (int i = 0; i < 32; ++i) {
@@ -267,16 +290,15 @@ __global__ void __launch_bounds__(kThreadsTc, 1) tc_fwd_kernel(const __grid_cons
         }
         fence_proxy_async_smem();
       }
-      // every epilogue warp reaches both barriers each iteration, aborted or not
+      // one barrier per tile, reached by every epilogue warp, aborted or not: before it,
+      // thread 0 waits until the store of tile it-1 has read the staging tile that tile
+      // it+1 rewrites
+      if (e == 0 && lane == 0) bulk_wait_read<0>();
       named_barrier_sync(1, kEpi * 32);
-      if (e == 0 && lane == 0) {
-        if (ok && !*abort_flag) {
-          bulk_s2g(P.A_out + (size_t)t * kTile, stage, kTile);
-          bulk_commit();
-        }
-        bulk_wait_read<1>();  // the store of the other staging tile has read it
+      if (e == 0 && lane == 0 && ok && !*abort_flag) {
+        bulk_s2g(P.A_out + (size_t)t * kTile, stage, kTile);
+        bulk_commit();
       }
-      named_barrier_sync(1, kEpi * 32);
     }
     if (e == 0 && lane == 0) bulk_wait_all<0>();
   }
@@ -285,7 +307,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) tc_fwd_kernel(const __grid_cons
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    tmem_dealloc(tmem, 128);
+    tmem_dealloc(tmem, 256);
   }
   (void)PT;
 }
@@ -295,14 +317,16 @@ __global__ void __launch_bounds__(kThreadsTc, 1) tc_fwd_kernel(const __grid_cons
 // Backward kernel: 16 epilogue warps (feature quadrant q = w mod 4, point quarter
 // pq = (w-2)/4), three input stages, two g_Z^T buffers so that epilogue 1 of tile t+1
 // runs while MMAs 2 and 3 of tile t execute (epilogue order: 1(0), then per t: 1(t+1),
-// 2(t)). Barriers: 0 weights; 1..3 in_full[s]; 4..6 in_empty[s] (16 epilogue + 1 MMA
-// arrivals); 7 d1_full; 8 d1_empty; 9, 10 gz_full[buffer]; 11 d2_full; 12 d2_empty;
-// 13 d3_done; 14 drain. Each barrier is waited on before it can complete again.
+// 2(t)). W and W^T are the A operands of MMAs 1 and 2 from tensor memory, which halves
+// the shared-memory operand traffic and leaves room for five input stages. Barriers:
+// 1..5 in_full[s]; 6..10 in_empty[s] (16 epilogue + 1 MMA arrivals); 11 d1_full;
+// 12 d1_empty; 13, 14 gz_full[buffer]; 15 d2_full; 16 d2_empty; 17 d3_done; 18 drain.
+// Each barrier is waited on before it can complete again.
 constexpr int kEpiB = 16;
 constexpr int kThreadsB = (2 + kEpiB) * 32;
-constexpr int kStagesB = 3;
-constexpr int kBwdBars = 15;
-enum { kBW = 0, kBInF = 1, kBInE = 4, kBD1F = 7, kBD1E = 8, kBGZ = 9, kBD2F = 11, kBD2E = 12, kBD3 = 13, kBDrain = 14 };
+constexpr int kStagesB = 5;
+constexpr int kBwdBars = 19;
+enum { kBInF = 1, kBInE = 6, kBD1F = 11, kBD1E = 12, kBGZ = 13, kBD2F = 15, kBD2E = 16, kBD3 = 17, kBDrain = 18 };
 
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t* v) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
@@ -354,25 +378,24 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
   const uint32_t raw = smem_addr(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* gen = smem_raw + (base - raw);
-  const uint32_t sW = base;                              // W   [j][k]
-  const uint32_t sWT = sW + kWImg;                       // W^T [k][j]
-  const uint32_t sA = sWT + kWImg;                       // kStagesB tiles of A_{l-1}
+  const uint32_t sA = base;                              // kStagesB tiles of A_{l-1}
   const uint32_t sG = sA + kStagesB * kTile;             // kStagesB tiles of gA_l
   const uint32_t sGZT = sG + kStagesB * kTile;           // 2 g_Z^T tiles
-  const uint32_t sOut = sGZT + 2 * kTile;                // staging tile of gA_{l-1}
-  const uint32_t sBar = sOut + kTile;
+  const uint32_t sOut = sGZT + 2 * kTile;                // 2 staging tiles of gA_{l-1}
+  const uint32_t sBar = sOut + 2 * kTile;
   Smem S{sBar};
   uint8_t* genBar = gen + (sBar - base);
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(genBar + 8 * kBwdBars);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(genBar + 8 * kBwdBars + 8);
-  float* red = reinterpret_cast<float*>(genBar + 8 * kBwdBars + 16);  // [2][4 quarters][4 quadrants][16 points]
+  // top layer only (no gA tiles are loaded there): the reduction scratch of the output
+  // layer, [2][4 quarters][4 quadrants][16 points], lives in the first gA stage
+  float* red = reinterpret_cast<float*>(gen + (sG - base));
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool top = P.top != 0;
   const int n_it = P.n_tiles > (int)blockIdx.x ? (P.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   // TMEM columns: D1 = Z^T [0, 64), D2 = gA^T [64, 128), D3 = g_W [128, 256)
   if (threadIdx.x == 0) {
-    mbar_init(S.bar(kBW), 1);
     for (int s = 0; s < kStagesB; ++s) { mbar_init(S.bar(kBInF + s), 1); mbar_init(S.bar(kBInE + s), kEpiB + 1); }
     mbar_init(S.bar(kBD1F), 1);
     mbar_init(S.bar(kBD1E), kEpiB);
@@ -386,22 +409,29 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
     fence_barrier_init();
   }
   if (warp == 0) {
-    tmem_alloc(smem_addr(tmem_holder), 256);
+    tmem_alloc(smem_addr(tmem_holder), 512);
     tmem_relinquish();
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
-  const uint32_t D1 = tmem, D2 = tmem + 64, D3 = tmem + 128;
+  // TMEM columns: D1 = Z^T [0, 64), D2 = gA^T [64, 128), D3 = g_W [128, 256),
+  // W [256, 320) and W^T [320, 384) as A operands
+  const uint32_t D1 = tmem, D2 = tmem + 64, D3 = tmem + 128, Wt = tmem + 256, WTt = tmem + 320;
+  if (warp >= 2) {
+    const int cq = (warp - 2) >> 2;
+    weights_to_tmem(static_cast<const uint8_t*>(P.wimg), Wt, warp & 3, lane, cq);
+    weights_to_tmem(static_cast<const uint8_t*>(P.wimgT), WTt, warp & 3, lane, cq);
+    tmem_wait_st();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
 
   if (warp == 0) {
     if (lane == 0) {
-      mbar_arrive_expect_tx(S.bar(kBW), 2 * kWImg);
-      bulk_g2s(sW, P.wimg, kWImg, S.bar(kBW));
-      bulk_g2s(sWT, P.wimgT, kWImg, S.bar(kBW));
-      bool ok = wait_bounded(S.bar(kBW), 0, abort_flag, P.status, true);
-      const uint64_t wd = desc_sw128(sW), wtd = desc_sw128(sWT);
+      bool ok = true;
       // MMA 1 (Z^T = W A^T) of tile `it`, once its tiles are in and D1 has been read out
       auto mma1 = [&](int it) -> bool {
         const int s = it % kStagesB;
@@ -411,9 +441,8 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
         const uint32_t ta = sA + (uint32_t)s * kTile;
 #pragma unroll
         for (int ks = 0; ks < kW / 16; ++ks) {
-          const uint64_t a_op = desc_add(wd, kstep_off(kW, ks));
-          if (ks == 0) mma_ss<0>(D1, a_op, desc_rows(ta, ks), kIdescRows);
-          else mma_ss<1>(D1, a_op, desc_rows(ta, ks), kIdescRows);
+          if (ks == 0) mma_ts<0>(D1, Wt + (uint32_t)(8 * ks), desc_rows(ta, ks), kIdescRows);
+          else mma_ts<1>(D1, Wt + (uint32_t)(8 * ks), desc_rows(ta, ks), kIdescRows);
         }
         mma_commit(S.bar(kBD1F));
         return true;
@@ -432,9 +461,8 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
         // MMA 2: gA^T = W^T g_Z^T (g_Z^T tile read MN-major: N = rows, K = features)
 #pragma unroll
         for (int ks = 0; ks < kW / 16; ++ks) {
-          const uint64_t a_op = desc_add(wtd, kstep_off(kW, ks));
-          if (ks == 0) mma_ss<0>(D2, a_op, desc_rows(gz, ks), kIdescRows);
-          else mma_ss<1>(D2, a_op, desc_rows(gz, ks), kIdescRows);
+          if (ks == 0) mma_ts<0>(D2, WTt + (uint32_t)(8 * ks), desc_rows(gz, ks), kIdescRows);
+          else mma_ts<1>(D2, WTt + (uint32_t)(8 * ks), desc_rows(gz, ks), kIdescRows);
         }
         // MMA 3: g_W += g_Z^T A (A tile read K-major: N = features, K = rows)
         const uint64_t gzd = desc_sw128(gz), tad = desc_sw128(ta);
@@ -631,11 +659,12 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
       }
     };
 
-    // ---- epilogue 2 of tile it: the gA_{l-1} tile (row = this thread's input feature)
+    // ---- epilogue 2 of tile it: the gA_{l-1} tile (row = this thread's input feature),
+    // written to staging tile it mod 2. One barrier per tile: before it, thread 0 waits
+    // until the store of tile it-1 has read its staging tile, which tile it+1 rewrites.
     auto epi2 = [&](int it) {
       const int t = (int)blockIdx.x + it * (int)gridDim.x;
-      if (e == 0 && lane == 0) bulk_wait_read<0>();  // the previous store has read the staging tile
-      named_barrier_sync(1, kEpiB * 32);
+      const uint32_t sOutB = sOut + (uint32_t)(it & 1) * kTile;
       if (ok) ok = wait_warp(S.bar(kBD2F), (uint32_t)(it & 1), abort_flag, P.status);
       if (ok) {
         tc_fence_after();
@@ -649,7 +678,7 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
           if (lane == 0) mbar_arrive(S.bar(kBD2E));
 #pragma unroll
           for (int ch = 0; ch < 4; ++ch)
-            st_shared_v2(row_addr(sOut, ch), pack2(__uint_as_float(v[ch][0]), __uint_as_float(v[ch][1])),
+            st_shared_v2(row_addr(sOutB, ch), pack2(__uint_as_float(v[ch][0]), __uint_as_float(v[ch][1])),
                          pack2(__uint_as_float(v[ch][2]), __uint_as_float(v[ch][3])));
         } else {
           uint32_t v[16];
@@ -660,7 +689,7 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
           if (lane == 0) mbar_arrive(S.bar(kBD2E));
 #pragma unroll
           for (int c = 0; c < 2; ++c)
-            st_shared_v4(sOut + tile_chunk(j, (p0 >> 3) + c),
+            st_shared_v4(sOutB + tile_chunk(j, (p0 >> 3) + c),
                          pack2(__uint_as_float(v[8 * c]), __uint_as_float(v[8 * c + 1])),
                          pack2(__uint_as_float(v[8 * c + 2]), __uint_as_float(v[8 * c + 3])),
                          pack2(__uint_as_float(v[8 * c + 4]), __uint_as_float(v[8 * c + 5])),
@@ -668,9 +697,10 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
         }
         fence_proxy_async_smem();
       }
+      if (e == 0 && lane == 0) bulk_wait_read<0>();
       named_barrier_sync(1, kEpiB * 32);
       if (e == 0 && lane == 0 && ok && !*abort_flag) {
-        bulk_s2g(P.gA_out + (size_t)t * kTile, sOut, kTile);
+        bulk_s2g(P.gA_out + (size_t)t * kTile, sOutB, kTile);
         bulk_commit();
       }
     };
@@ -713,7 +743,7 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    tmem_dealloc(tmem, 256);
+    tmem_dealloc(tmem, 512);
   }
 }
 
@@ -845,9 +875,8 @@ __global__ void tc_sum_float_kernel(const float* __restrict__ part, int n, float
   *out += s;
 }
 
-constexpr size_t kFwdSmem = 1024 + kWImg + kStagesF * kTile + 2 * kTile + 8 * kFwdBars + 64;
-constexpr size_t kBwdSmem = 1024 + 2 * kWImg + 2 * kStagesB * kTile + 2 * kTile + kTile + 8 * kBwdBars + 16 +
-                            2 * 4 * 4 * 16 * 4 + 64;
+constexpr size_t kFwdSmem = 1024 + kStagesF * kTile + 2 * kTile + 8 * kFwdBars + 64;
+constexpr size_t kBwdSmem = 1024 + 2 * kStagesB * kTile + 2 * kTile + 2 * kTile + 8 * kBwdBars + 16 + 64;
 static_assert(kBwdSmem <= 232448, "backward kernel shared memory");
 
 int grid_for(int n_tiles) {
