@@ -42,8 +42,8 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # DRAM traffic of one SDNet (tensor-core) launch from an ncu capture, valid only while
 # the kernel source is unchanged (keyed by the source hash).
 NCU_TRAFFIC = {
-    # ncu --set full, colour 0 of the L = 64 grid: dram__bytes_read 2.64 MB + write 0.33 MB
-    "a46b955a07527b02": 2960384,
+    # ncu --set full, colour 0 of the L = 64 grid: dram__bytes_read 2.64 MB + write 0.32 MB
+    "e54aa9a8a9a9d1cc": 2962432,
 }
 
 
@@ -195,7 +195,7 @@ def blas_threads():
 def source_hash():
     """Hash of the tensor-core SDNet kernel's sources (the kernel and its headers)."""
     h = hashlib.sha256()
-    for name in ("mf_mlp_bf16.cu", "mf_wait.cuh", "mf_internal.cuh"):
+    for name in ("mf_mlp_bf16.cu", "mf_tc.cuh", "mf_wait.cuh", "mf_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2308_14258_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
