@@ -532,7 +532,7 @@ mf_status run_pass_fused(mf_trainer* t, int C, int F, int n, const float* G, con
                          float gscale, double lscale, double* loss_slot, cudaStream_t st) {
   const int H = t->H, NH = t->NH;
   const int R = F * n;
-  const int n_tiles = R * C / 64;
+  const int n_tiles = mf::tc_tiles(R, C);
   const size_t img = mf::tc_image_bytes();
   auto wimg = [&](int l) { return static_cast<const char*>(t->timg) + (size_t)(l - 1) * 2 * img; };
   const int ctas = mf::tc_partial_ctas(), pg = mf::tc_partial_groups();
@@ -566,6 +566,7 @@ mf_status run_pass_fused(mf_trainer* t, int C, int F, int n, const float* G, con
     bp.gwout_part = gwop;
     bp.gbout_part = gbop;
     bp.n_tiles = n_tiles;
+    bp.n_pts = R;
     bp.C = C;
     bp.top = l == NH ? 1 : 0;
     bp.status = t->status;

@@ -2,19 +2,21 @@
 // training step (Eq. 3, Algorithm 1), BF16 operands with FP32 accumulators, width 128.
 //
 // Orientation. A layer computes Z^T = W A^T with M = 128 output features (TMEM lanes)
-// and N = 64 GEMM rows of a tile: the four Taylor channels (value, d/dx, d/dy, Delta) of
-// 16 points, or 64 points of the value channel alone. Each epilogue thread then owns one
+// and N = 128 GEMM rows of a tile: the four Taylor channels (value, d/dx, d/dy, Delta) of
+// 32 points, or 128 points of the value channel alone. Each epilogue thread then owns one
 // feature and holds every channel of its points, which is what the chain rules of the
-// Taylor-mode tanh need (see mf_train.cu for the formulas).
+// Taylor-mode tanh need (see mf_train.cu for the formulas). Every MMA of a tile is a
+// 128 x 128 x 128 group.
 //
-// Activations and their gradients travel between layers in HBM as BF16 tiles of 64
-// GEMM rows x 128 features, 16 KB each, stored feature-major: feature k owns 128 bytes
-// (its 64 rows, row r = channel x (points per tile) + point), 16-byte chunk c (rows
-// 8c..8c+7) at chunk c ^ (k mod 8). This is byte for byte the 128-byte-swizzled operand
-// layout, so one bulk copy loads a tile that the MMAs read directly: as an MN-major
-// operand with N = rows and K = features (Z = W A^T, and gA^T = W^T g_Z^T), or as a
-// K-major operand with N = features and K = rows (g_W = g_Z^T A). An epilogue thread owns
-// one feature and so reads and writes its 128 bytes with 16-byte accesses.
+// Activations and their gradients travel between layers in HBM as BF16 tiles of 128
+// GEMM rows x 128 features, 32 KB each (row r = channel x (points per tile) + point),
+// stored as two halves of 64 rows, each feature-major: in half h feature k owns 128
+// bytes, and the 16-byte chunk c (rows 64h + 8c .. 64h + 8c + 7) sits at chunk c ^ (k mod 8).
+// Each half is byte for byte the 128-byte-swizzled operand layout, so one bulk copy loads
+// a tile that the MMAs read directly: as an MN-major operand with N = rows (two 64-row
+// atoms 16 KB apart) and K = features (Z = W A^T, and gA^T = W^T g_Z^T), or half by half
+// as a K-major operand with N = features and K = rows (g_W = g_Z^T A). An epilogue thread
+// owns one feature and so reads and writes its rows with 16-byte accesses.
 //
 // Forward kernel (hidden layers 1..NH-1): load tile A_{l-1}; MMA into TMEM; epilogue
 // applies the Taylor-mode tanh and writes tile A_l. Pre-activations are never stored.
@@ -29,14 +31,16 @@
 // top) go to global memory and are added up in a fixed order afterwards, so results do
 // not depend on timing.
 //
-// Roles per CTA (persistent, one CTA per SM, static tile schedule t = CTA + i x CTAs;
-// the forward keeps four input tiles in flight, the backward two): warp 0 lane 0 issues
-// the MMAs, warp 1 lane 0 issues the bulk loads, warps 2-9 are the epilogue (feature
-// quadrant q = w mod 4, the TMEM lanes warp w may read; point half (w-2)/4). Every wait
-// is bounded (mf_wait.cuh);
-// after an abort the epilogue warps keep stepping through their loop without work, so
-// that every named barrier is reached by every warp, and the CTA drains its MMAs and
-// bulk copies before it frees TMEM and exits.
+// The value channel of the data points is padded to whole tiles: the first layer writes
+// zero rows past the last point, every later row of the padding stays finite, and the top
+// layer gives those rows a zero residual, so their g_Z, gA and g_W contributions are 0.
+//
+// Roles per CTA (persistent, one CTA per SM, static tile schedule t = CTA + i x CTAs):
+// warp 0 lane 0 issues the MMAs, warp 1 lane 0 issues the bulk loads, the other warps are
+// the epilogue (feature quadrant q = w mod 4, the TMEM lanes warp w may read). Every wait
+// is bounded (mf_wait.cuh); after an abort the epilogue warps keep stepping through their
+// loop without work, so that every named barrier is reached by every warp, and the CTA
+// drains its MMAs and bulk copies before it frees TMEM and exits.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -50,22 +54,28 @@ namespace mf {
 namespace {
 
 constexpr int kW = 128;                        // width H on the fused path
-constexpr int kTR = 64;                        // GEMM rows per tile
-constexpr uint32_t kTile = kTR * kW * 2;       // 16 KB
+constexpr int kTR = 128;                       // GEMM rows per tile
+constexpr uint32_t kHalf = 64 * kW * 2;        // 16 KB: 64 rows of a tile
+constexpr uint32_t kTile = 2 * kHalf;          // 32 KB
 constexpr uint32_t kWImg = kW * kW * 2;        // 32 KB
-constexpr int kEpi = 8;                        // epilogue warps
+constexpr int kEpi = 8;                        // epilogue warps (forward)
 constexpr int kThreadsTc = (2 + kEpi) * 32;    // MMA warp, load warp, epilogue
-constexpr int kStagesF = 8;                    // input tiles in flight per CTA (forward)
+constexpr int kStagesF = 5;                    // input tiles in flight per CTA (forward)
 constexpr uint32_t kIdescRows = idesc_bf16_bmn(128, kTR);  // B = tile, N = rows (MN-major)
 constexpr uint32_t kIdescGW = idesc_bf16(128, kW);          // B = tile, N = features (K-major)
 
-// Byte offset of the 16-byte chunk holding rows 8c..8c+7 of feature k in a tile.
+// Byte offset of the 16-byte chunk holding rows 8c..8c+7 (c = 0..15) of feature k.
 __host__ __device__ __forceinline__ uint32_t tile_chunk(int k, int c) {
-  return (uint32_t)k * 128u + ((uint32_t)(c ^ (k & 7)) << 4);
+  return (uint32_t)(c >> 3) * kHalf + (uint32_t)k * 128u + ((uint32_t)((c & 7) ^ (k & 7)) << 4);
 }
-// K-step ks (features 16ks..16ks+15) of a tile read MN-major (N = 64 rows = one atom).
+// K step ks (features 16ks..16ks+15) of a tile read MN-major: N = 128 rows in two 64-row
+// atoms kHalf apart (leading byte offset), 8-feature groups 1 KB apart (stride byte offset).
 __device__ __forceinline__ uint64_t desc_rows(uint32_t tile, int ks) {
-  return desc_sw128_mn(tile + (uint32_t)ks * 2048u, 8192u, 1024u);
+  return desc_sw128_mn(tile + (uint32_t)ks * 2048u, kHalf, 1024u);
+}
+// Offset of K step ks (rows 16ks..16ks+15) of a tile read K-major, half by half.
+__device__ __forceinline__ uint32_t kstep_rows(int ks) {
+  return (uint32_t)(ks >> 2) * kHalf + (uint32_t)(ks & 3) * 32u;
 }
 
 __device__ __forceinline__ uint4 ld_shared_v4(uint32_t addr) {
@@ -85,6 +95,12 @@ __device__ __forceinline__ void unpack8(uint4 v, float* f) {
     f[2 * i] = __uint_as_float(w[i] << 16);
     f[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
   }
+}
+
+// BF16 value i (0..7) of a 16-byte chunk, as a float
+__device__ __forceinline__ float bf16_word(const uint4& u, int i) {
+  const uint32_t w = (i >> 1) == 0 ? u.x : (i >> 1) == 1 ? u.y : (i >> 1) == 2 ? u.z : u.w;
+  return (i & 1) ? __uint_as_float(w & 0xffff0000u) : __uint_as_float(w << 16);
 }
 
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* v) {
@@ -130,9 +146,6 @@ __device__ __forceinline__ void weights_to_tmem(const uint8_t* __restrict__ img,
   tmem_st16(tcol + ((uint32_t)(32 * q) << 16) + (uint32_t)(16 * cq), v);
 }
 
-// Points and GEMM rows of a tile for C channels.
-__device__ __forceinline__ int pts_per_tile(int C) { return kTR / C; }
-
 struct Smem {
   uint32_t base;
   __device__ uint32_t bar(int i) const { return base + 8u * (uint32_t)i; }
@@ -140,9 +153,35 @@ struct Smem {
 
 // ------------------------------------------------------------------ forward kernel
 
-// barriers: 1+s in_full[s]; 9+s in_empty[s]; 17+b acc_full[b]; 19+b acc_empty[b]; 21 drain
-constexpr int kFwdBars = 22;
-enum { kFInF = 1, kFInE = 9, kFAccF = 17, kFAccE = 19, kFDrain = 21 };
+// barriers: 1+s in_full[s]; 6+s in_empty[s]; 11+b acc_full[b]; 13+b acc_empty[b]; 15 drain
+constexpr int kFwdBars = 16;
+enum { kFInF = 1, kFInE = 6, kFAccF = 11, kFAccE = 13, kFDrain = 15 };
+
+// Taylor-mode tanh of 8 points of one feature (value, d/dx, d/dy, Delta channels) from
+// the accumulator words v[ch][0..7], written as one 16-byte chunk per channel.
+__device__ __forceinline__ void fwd_taylor8(const uint32_t (&v)[4][8], float bj, uint32_t stage, int j, int c0) {
+  uint32_t w[4][4];
+#pragma unroll
+  for (int i = 0; i < 8; i += 2) {
+    float o[4][2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const float z = __uint_as_float(v[0][i + u]) + bj;
+      const float zx = __uint_as_float(v[1][i + u]), zy = __uint_as_float(v[2][i + u]), zl = __uint_as_float(v[3][i + u]);
+      float a, sd;
+      tanh_sech2(z, a, sd);
+      o[0][u] = a;
+      o[1][u] = sd * zx;
+      o[2][u] = sd * zy;
+      o[3][u] = fmaf(-2.0f * a * sd, zx * zx + zy * zy, sd * zl);
+    }
+#pragma unroll
+    for (int ch = 0; ch < 4; ++ch) w[ch][i >> 1] = pack2(o[ch][0], o[ch][1]);
+  }
+  // channel ch of points 8 c0 .. 8 c0 + 7: chunk 4 ch + c0
+#pragma unroll
+  for (int ch = 0; ch < 4; ++ch) st_shared_v4(stage + tile_chunk(j, 4 * ch + c0), w[ch][0], w[ch][1], w[ch][2], w[ch][3]);
+}
 
 __global__ void __launch_bounds__(kThreadsTc, 1) tc_fwd_kernel(const __grid_constant__ TcFwdParams P) {
   extern __shared__ uint8_t smem_raw[];
@@ -157,7 +196,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) tc_fwd_kernel(const __grid_cons
   volatile int* abort_flag = reinterpret_cast<volatile int*>(gen + (sBar - base) + 8 * kFwdBars + 8);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int C = P.C, PT = pts_per_tile(C);
+  const int C = P.C;
   const int n_it = P.n_tiles > (int)blockIdx.x ? (P.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStagesF; ++s) { mbar_init(S.bar(kFInF + s), 1); mbar_init(S.bar(kFInE + s), 1); }
@@ -167,15 +206,15 @@ __global__ void __launch_bounds__(kThreadsTc, 1) tc_fwd_kernel(const __grid_cons
     fence_barrier_init();
   }
   if (warp == 0) {
-    tmem_alloc(smem_addr(tmem_holder), 256);
+    tmem_alloc(smem_addr(tmem_holder), 512);
     tmem_relinquish();
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
-  // TMEM columns: accumulators [0, 128) (two buffers of 64), W as the A operand [128, 192)
-  const uint32_t Wt = tmem + 128;
+  // TMEM columns: accumulators [0, 256) (two buffers of 128), W as the A operand [256, 320)
+  const uint32_t Wt = tmem + 256;
   if (warp >= 2) {
     const int e = warp - 2;
     weights_to_tmem(static_cast<const uint8_t*>(P.wimg), Wt, warp & 3, lane, 2 * (e >> 2));
@@ -229,7 +268,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) tc_fwd_kernel(const __grid_cons
     __syncwarp();
   } else {
     // a warp reads the TMEM lane quadrant (warp index mod 4): warps 2-5 and 6-9 each cover
-    // all four quadrants, one point half each
+    // all four quadrants, one half of the tile's points each
     const int e = warp - 2, q = warp & 3, hh = e >> 2;
     const int j = 32 * q + lane;
     const float bj = P.bias[j];
@@ -244,49 +283,39 @@ __global__ void __launch_bounds__(kThreadsTc, 1) tc_fwd_kernel(const __grid_cons
         tc_fence_after();
         const uint32_t acc = tmem + (uint32_t)(b * kTR) + lane_off;
         if (C == 4) {
-          uint32_t v[4][8];
+          // points 16 hh .. 16 hh + 15 of the tile's 32: two groups of 8
+          uint32_t v0[4][8], v1[4][8];
 #pragma unroll
-          for (int ch = 0; ch < 4; ++ch) tmem_ld8(acc + (uint32_t)(ch * 16 + 8 * hh), v[ch]);
+          for (int ch = 0; ch < 4; ++ch) {
+            tmem_ld8(acc + (uint32_t)(ch * 32 + 16 * hh), v0[ch]);
+            tmem_ld8(acc + (uint32_t)(ch * 32 + 16 * hh + 8), v1[ch]);
+          }
           tmem_wait_ld();
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(S.bar(kFAccE + b));
-          float o[4][8];
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const float z = __uint_as_float(v[0][i]) + bj;
-            const float zx = __uint_as_float(v[1][i]), zy = __uint_as_float(v[2][i]), zl = __uint_as_float(v[3][i]);
-            float a, sd;
-            tanh_sech2(z, a, sd);
-            const float td = -2.0f * a * sd;
-            o[0][i] = a;
-            o[1][i] = sd * zx;
-            o[2][i] = sd * zy;
-            o[3][i] = fmaf(td, zx * zx + zy * zy, sd * zl);
-          }
-          // rows ch * 16 + 8 hh .. + 7 of feature j: chunk 2 ch + hh
-#pragma unroll
-          for (int ch = 0; ch < 4; ++ch)
-            st_shared_v4(stage + tile_chunk(j, 2 * ch + hh), pack2(o[ch][0], o[ch][1]), pack2(o[ch][2], o[ch][3]),
-                         pack2(o[ch][4], o[ch][5]), pack2(o[ch][6], o[ch][7]));
+          fwd_taylor8(v0, bj, stage, j, 2 * hh);
+          fwd_taylor8(v1, bj, stage, j, 2 * hh + 1);
         } else {
-          uint32_t v[32];
-          tmem_ld32(acc + (uint32_t)(32 * hh), *reinterpret_cast<uint32_t(*)[32]>(v));
+          // rows 64 hh .. 64 hh + 63: chunks 8 hh .. 8 hh + 7
+          uint32_t v[2][32];
+          tmem_ld32(acc + (uint32_t)(64 * hh), v[0]);
+          tmem_ld32(acc + (uint32_t)(64 * hh + 32), v[1]);
           tmem_wait_ld();
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(S.bar(kFAccE + b));
-          float o[32];
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            float sd;
-            tanh_sech2(__uint_as_float(v[i]) + bj, o[i], sd);
+          for (int c = 0; c < 8; ++c) {
+            float o[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              float sd;
+              tanh_sech2(__uint_as_float(v[c >> 2][8 * (c & 3) + i]) + bj, o[i], sd);
+            }
+            st_shared_v4(stage + tile_chunk(j, 8 * hh + c), pack2(o[0], o[1]), pack2(o[2], o[3]), pack2(o[4], o[5]),
+                         pack2(o[6], o[7]));
           }
-          // rows 32 hh .. + 31: chunks 4 hh .. 4 hh + 3
-#pragma unroll
-          for (int c = 0; c < 4; ++c)
-            st_shared_v4(stage + tile_chunk(j, 4 * hh + c), pack2(o[8 * c], o[8 * c + 1]), pack2(o[8 * c + 2], o[8 * c + 3]),
-                         pack2(o[8 * c + 4], o[8 * c + 5]), pack2(o[8 * c + 6], o[8 * c + 7]));
         }
         fence_proxy_async_smem();
       }
@@ -307,42 +336,33 @@ __global__ void __launch_bounds__(kThreadsTc, 1) tc_fwd_kernel(const __grid_cons
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    tmem_dealloc(tmem, 256);
+    tmem_dealloc(tmem, 512);
   }
-  (void)PT;
 }
 
 // ------------------------------------------------------------------ backward kernel
 
 // Backward kernel: 16 epilogue warps (feature quadrant q = w mod 4, point quarter
-// pq = (w-2)/4), three input stages, two g_Z^T buffers so that epilogue 1 of tile t+1
-// runs while MMAs 2 and 3 of tile t execute (epilogue order: 1(0), then per t: 1(t+1),
-// 2(t)). W and W^T are the A operands of MMAs 1 and 2 from tensor memory, which halves
-// the shared-memory operand traffic and leaves room for five input stages. Barriers:
-// 1..5 in_full[s]; 6..10 in_empty[s] (16 epilogue + 1 MMA arrivals); 11 d1_full;
-// 12 d1_empty; 13, 14 gz_full[buffer]; 15 d2_full; 16 d2_empty; 17 d3_done; 18 drain.
-// Each barrier is waited on before it can complete again.
+// pq = (w-2)/4). Shared memory: three A_{l-1} slots (each held from MMA 1 to MMA 3 of its
+// tile), two gA_l slots (held until epilogue 1 has read them), one g_Z^T tile and one
+// staging tile for gA_{l-1}: 224 KB. Epilogue order 1(0), then per t: 1(t+1), 2(t), so
+// that epilogue 1 of tile t+1 runs while MMAs 2 and 3 of tile t execute. W and W^T are the
+// A operands of MMAs 1 and 2 from tensor memory. Barriers: 1..3 a_full[slot];
+// 4..6 a_empty[slot] (MMA 3 done); 7, 8 g_full[slot]; 9, 10 g_empty[slot] (16 warps);
+// 11 d1_full; 12 d1_empty; 13 gz_full; 14 gz_empty (MMA 3 done); 15 d2_full (MMA 2 done);
+// 16 d2_empty; 17 d3_done; 18 drain. Each barrier is waited on before it can complete
+// again.
 constexpr int kEpiB = 16;
 constexpr int kThreadsB = (2 + kEpiB) * 32;
-constexpr int kStagesB = 5;
+constexpr int kSlotsA = 3;
+constexpr int kSlotsG = 2;
 constexpr int kBwdBars = 19;
-enum { kBInF = 1, kBInE = 6, kBD1F = 11, kBD1E = 12, kBGZ = 13, kBD2F = 15, kBD2E = 16, kBD3 = 17, kBDrain = 18 };
+enum {
+  kBAF = 1, kBAE = 4, kBGF = 7, kBGE = 9, kBD1F = 11, kBD1E = 12, kBGZF = 13, kBGZE = 14, kBD2F = 15, kBD2E = 16,
+  kBD3 = 17, kBDrain = 18
+};
 
-__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t* v) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
-               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
-               : "r"(taddr));
-}
-__device__ __forceinline__ uint2 ld_shared_v2(uint32_t addr) {
-  uint2 v;
-  asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(addr) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_shared_v2(uint32_t addr, uint32_t a, uint32_t b) {
-  asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(a), "r"(b) : "memory");
-}
-
-// Sum of v[0..N-1] (N = 4 or 16) over the 32 lanes of a warp: in the first log2 N
+// Sum of v[0..N-1] (N a power of 2 up to 32) over the 32 lanes of a warp: in the first log2 N
 // shuffle rounds each lane sends the half of its values its partner keeps, then the
 // remaining rounds finish the one value each lane is left with. Returns that sum; idx
 // receives which value it is.
@@ -370,37 +390,37 @@ __device__ __forceinline__ float warp_sum_n(const float (&v)[N], int lane, int& 
   return cur[0];
 }
 
-template <int C>
+template <int C, bool kTop>
 __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_constant__ TcBwdParams P) {
   constexpr int PT = kTR / C;     // points per tile
-  constexpr int NP = PT / 4;      // points per epilogue warp: 4 (C = 4) or 16 (C = 1)
+  constexpr int NP = PT / 4;      // points per epilogue thread: 8 (C = 4) or 32 (C = 1)
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_addr(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* gen = smem_raw + (base - raw);
-  const uint32_t sA = base;                              // kStagesB tiles of A_{l-1}
-  const uint32_t sG = sA + kStagesB * kTile;             // kStagesB tiles of gA_l
-  const uint32_t sGZT = sG + kStagesB * kTile;           // 2 g_Z^T tiles
-  const uint32_t sOut = sGZT + 2 * kTile;                // 2 staging tiles of gA_{l-1}
-  const uint32_t sBar = sOut + 2 * kTile;
+  const uint32_t sA = base;                              // kSlotsA tiles of A_{l-1}
+  const uint32_t sG = sA + kSlotsA * kTile;              // kSlotsG tiles of gA_l
+  const uint32_t sGZ = sG + kSlotsG * kTile;             // the g_Z^T tile
+  const uint32_t sOut = sGZ + kTile;                     // staging tile of gA_{l-1}
+  const uint32_t sBar = sOut + kTile;
   Smem S{sBar};
   uint8_t* genBar = gen + (sBar - base);
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(genBar + 8 * kBwdBars);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(genBar + 8 * kBwdBars + 8);
   // top layer only (no gA tiles are loaded there): the reduction scratch of the output
-  // layer, [2][4 quarters][4 quadrants][16 points], lives in the first gA stage
+  // layer, [2][4 quarters][4 quadrants][NP points], lives in the first gA slot
   float* red = reinterpret_cast<float*>(gen + (sG - base));
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const bool top = P.top != 0;
+  constexpr bool top = kTop;
   const int n_it = P.n_tiles > (int)blockIdx.x ? (P.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-  // TMEM columns: D1 = Z^T [0, 64), D2 = gA^T [64, 128), D3 = g_W [128, 256)
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStagesB; ++s) { mbar_init(S.bar(kBInF + s), 1); mbar_init(S.bar(kBInE + s), kEpiB + 1); }
+    for (int s = 0; s < kSlotsA; ++s) { mbar_init(S.bar(kBAF + s), 1); mbar_init(S.bar(kBAE + s), 1); }
+    for (int s = 0; s < kSlotsG; ++s) { mbar_init(S.bar(kBGF + s), 1); mbar_init(S.bar(kBGE + s), kEpiB); }
     mbar_init(S.bar(kBD1F), 1);
     mbar_init(S.bar(kBD1E), kEpiB);
-    mbar_init(S.bar(kBGZ), kEpiB);
-    mbar_init(S.bar(kBGZ + 1), kEpiB);
+    mbar_init(S.bar(kBGZF), kEpiB);
+    mbar_init(S.bar(kBGZE), 1);
     mbar_init(S.bar(kBD2F), 1);
     mbar_init(S.bar(kBD2E), kEpiB);
     mbar_init(S.bar(kBD3), 1);
@@ -416,9 +436,9 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
-  // TMEM columns: D1 = Z^T [0, 64), D2 = gA^T [64, 128), D3 = g_W [128, 256),
-  // W [256, 320) and W^T [320, 384) as A operands
-  const uint32_t D1 = tmem, D2 = tmem + 64, D3 = tmem + 128, Wt = tmem + 256, WTt = tmem + 320;
+  // TMEM columns: D1 = Z^T [0, 128), D2 = gA^T [128, 256), D3 = g_W [256, 384),
+  // W [384, 448) and W^T [448, 512) as A operands
+  const uint32_t D1 = tmem, D2 = tmem + 128, D3 = tmem + 256, Wt = tmem + 384, WTt = tmem + 448;
   if (warp >= 2) {
     const int cq = (warp - 2) >> 2;
     weights_to_tmem(static_cast<const uint8_t*>(P.wimg), Wt, warp & 3, lane, cq);
@@ -432,10 +452,10 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
   if (warp == 0) {
     if (lane == 0) {
       bool ok = true;
-      // MMA 1 (Z^T = W A^T) of tile `it`, once its tiles are in and D1 has been read out
+      // MMA 1 (Z^T = W A^T) of tile `it`, once its A tile is in and D1 has been read out
       auto mma1 = [&](int it) -> bool {
-        const int s = it % kStagesB;
-        if (!wait_spin(S.bar(kBInF + s), (uint32_t)((it / kStagesB) & 1), abort_flag, P.status)) return false;
+        const int s = it % kSlotsA;
+        if (!wait_spin(S.bar(kBAF + s), (uint32_t)((it / kSlotsA) & 1), abort_flag, P.status)) return false;
         if (it > 0 && !wait_spin(S.bar(kBD1E), (uint32_t)((it - 1) & 1), abort_flag, P.status)) return false;
         tc_fence_after();
         const uint32_t ta = sA + (uint32_t)s * kTile;
@@ -447,34 +467,34 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
         mma_commit(S.bar(kBD1F));
         return true;
       };
-      if (ok && n_it > 0) ok = mma1(0);
+      if (n_it > 0) ok = mma1(0);
       for (int it = 0; ok && it < n_it; ++it) {
-        const int s = it % kStagesB, zb = it & 1;
+        const int s = it % kSlotsA;
         const uint32_t ta = sA + (uint32_t)s * kTile;
-        const uint32_t gz = sGZT + (uint32_t)zb * kTile;
         // the next tile's recompute runs while epilogue 1 of this tile works
         if (it + 1 < n_it && !mma1(it + 1)) { ok = false; break; }
-        ok = wait_spin(S.bar(kBGZ + zb), (uint32_t)((it >> 1) & 1), abort_flag, P.status);
+        ok = wait_spin(S.bar(kBGZF), (uint32_t)(it & 1), abort_flag, P.status);
         if (ok && it > 0) ok = wait_spin(S.bar(kBD2E), (uint32_t)((it - 1) & 1), abort_flag, P.status);
         if (!ok) break;
         tc_fence_after();
         // MMA 2: gA^T = W^T g_Z^T (g_Z^T tile read MN-major: N = rows, K = features)
 #pragma unroll
         for (int ks = 0; ks < kW / 16; ++ks) {
-          if (ks == 0) mma_ts<0>(D2, WTt + (uint32_t)(8 * ks), desc_rows(gz, ks), kIdescRows);
-          else mma_ts<1>(D2, WTt + (uint32_t)(8 * ks), desc_rows(gz, ks), kIdescRows);
+          if (ks == 0) mma_ts<0>(D2, WTt + (uint32_t)(8 * ks), desc_rows(sGZ, ks), kIdescRows);
+          else mma_ts<1>(D2, WTt + (uint32_t)(8 * ks), desc_rows(sGZ, ks), kIdescRows);
         }
-        // MMA 3: g_W += g_Z^T A (A tile read K-major: N = features, K = rows)
-        const uint64_t gzd = desc_sw128(gz), tad = desc_sw128(ta);
+        mma_commit(S.bar(kBD2F));
+        // MMA 3: g_W += g_Z^T A (both tiles read K-major: M, N = features, K = rows)
+        const uint64_t gzd = desc_sw128(sGZ), tad = desc_sw128(ta);
 #pragma unroll
         for (int ks = 0; ks < kTR / 16; ++ks) {
-          const uint64_t a_op = desc_add(gzd, (uint32_t)ks * 32u);
-          const uint64_t b_op = desc_add(tad, (uint32_t)ks * 32u);
+          const uint64_t a_op = desc_add(gzd, kstep_rows(ks));
+          const uint64_t b_op = desc_add(tad, kstep_rows(ks));
           if (it == 0 && ks == 0) mma_ss<0>(D3, a_op, b_op, kIdescGW);
           else mma_ss<1>(D3, a_op, b_op, kIdescGW);
         }
-        mma_commit(S.bar(kBD2F));
-        mma_commit(S.bar(kBInE + s));
+        mma_commit(S.bar(kBGZE));
+        mma_commit(S.bar(kBAE + s));
       }
       mma_commit(S.bar(kBD3));  // every MMA issued, including the last g_W accumulation, done
       mma_commit(S.bar(kBDrain));
@@ -483,21 +503,35 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
     __syncwarp();
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t bytes = top ? kTile : 2 * kTile;
-      int issued = 0;
-      for (int it = 0; it < n_it; ++it) {
-        const int s = it % kStagesB;
-        if (it >= kStagesB &&
-            !wait_bounded(S.bar(kBInE + s), (uint32_t)(((it / kStagesB) - 1) & 1), abort_flag, P.status, true))
-          break;
+      // loads in the order they fall due: gA_l of tile it, then A_{l-1} of tile it+1
+      auto load = [&](int it, int slots, int full, int empty, uint32_t dst0, const uint8_t* src) -> bool {
+        const int s = it % slots;
+        if (it >= slots &&
+            !wait_bounded(S.bar(empty + s), (uint32_t)(((it / slots) - 1) & 1), abort_flag, P.status, true))
+          return false;
         const int t = (int)blockIdx.x + it * (int)gridDim.x;
-        mbar_arrive_expect_tx(S.bar(kBInF + s), bytes);
-        bulk_g2s(sA + (uint32_t)s * kTile, P.A_in + (size_t)t * kTile, kTile, S.bar(kBInF + s));
-        if (!top) bulk_g2s(sG + (uint32_t)s * kTile, P.gA_in + (size_t)t * kTile, kTile, S.bar(kBInF + s));
-        issued = it + 1;
+        mbar_arrive_expect_tx(S.bar(full + s), kTile);
+        bulk_g2s(dst0 + (uint32_t)s * kTile, src + (size_t)t * kTile, kTile, S.bar(full + s));
+        return true;
+      };
+      int na = 0, ng = 0;
+      bool ok = n_it > 0 && load(0, kSlotsA, kBAF, kBAE, sA, P.A_in);
+      if (ok) na = 1;
+      for (int it = 0; ok && it < n_it; ++it) {
+        if (!top) {
+          ok = load(it, kSlotsG, kBGF, kBGE, sG, P.gA_in);
+          if (ok) ng = it + 1;
+        }
+        if (ok && it + 1 < n_it) {
+          ok = load(it + 1, kSlotsA, kBAF, kBAE, sA, P.A_in);
+          if (ok) na = it + 2;
+        }
       }
-      for (int it = (issued > kStagesB ? issued - kStagesB : 0); it < issued; ++it)
-        wait_bounded(S.bar(kBInF + it % kStagesB), (uint32_t)((it / kStagesB) & 1), abort_flag, P.status, false);
+      // every load issued has landed before shared memory can go away
+      for (int i = (na > kSlotsA ? na - kSlotsA : 0); i < na; ++i)
+        wait_bounded(S.bar(kBAF + i % kSlotsA), (uint32_t)((i / kSlotsA) & 1), abort_flag, P.status, false);
+      for (int i = (ng > kSlotsG ? ng - kSlotsG : 0); i < ng; ++i)
+        wait_bounded(S.bar(kBGF + i % kSlotsG), (uint32_t)((i / kSlotsG) & 1), abort_flag, P.status, false);
     }
     __syncwarp();
   } else {
@@ -509,198 +543,233 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
     const float wo = top ? P.wout[j] : 0.f;
     const uint32_t lane_off = (uint32_t)(32 * q) << 16;
     const int p0 = pq * NP;
-    // rows ch * PT + p0 .. + NP - 1 of feature j: C = 4 -> 8 bytes (half a chunk) per
-    // channel, C = 1 -> two 16-byte chunks
-    auto row_addr = [&](uint32_t tile, int ch) -> uint32_t {
-      const int r = ch * PT + p0;
-      return tile + tile_chunk(j, r >> 3) + (uint32_t)(r & 7) * 2u;
-    };
+    // chunk of channel ch of this thread's points: C = 4 -> one chunk (8 points) per
+    // channel, C = 1 -> chunks 4 pq .. 4 pq + 3 (cc = 0..3)
+    auto chunk = [&](int ch, int cc) -> int { return C == 4 ? 4 * ch + pq : 4 * pq + cc; };
     float gb = 0.f, gwo = 0.f, gbo = 0.f;
     double lsum = 0.0;
     bool ok = true;
 
     // ---- epilogue 1 of tile it: g_Z from the recomputed Z and the incoming gradient
     auto epi1 = [&](int it) {
-      const int s = it % kStagesB, zb = it & 1;
+      const int sgs = it % kSlotsG;
       const int t = (int)blockIdx.x + it * (int)gridDim.x;
-      const uint32_t sg = sG + (uint32_t)s * kTile;
-      const uint32_t gzt = sGZT + (uint32_t)zb * kTile;
-      float z[NP], zx[NP], zy[NP], zl[NP];
+      const uint32_t sg = sG + (uint32_t)sgs * kTile;
+      float* rb = red + (it & 1) * (16 * NP);  // top: [4 quarters][4 quadrants][NP points]
       if (ok) ok = wait_warp(S.bar(kBD1F), (uint32_t)(it & 1), abort_flag, P.status);
-      if (ok && !top) ok = wait_warp(S.bar(kBInF + s), (uint32_t)((it / kStagesB) & 1), abort_flag, P.status);
-      if (ok) {
-        tc_fence_after();
-        if constexpr (C == 4) {
-          uint32_t v[4][4];
+      if (ok && !top) ok = wait_warp(S.bar(kBGF + sgs), (uint32_t)((it / kSlotsG) & 1), abort_flag, P.status);
+      if (ok) tc_fence_after();
+      if constexpr (C == 4) {
+        // D1 columns of the 8 points: z, z_x, z_y, Delta z; D1 and the gA slot are released
+        // as soon as they are read
+        uint32_t v[4][8];
+        uint4 gin[4];  // incoming gradient chunks, one per channel, as BF16 pairs
+        if (ok) {
 #pragma unroll
-          for (int ch = 0; ch < 4; ++ch) tmem_ld4(D1 + lane_off + (uint32_t)(ch * 16 + p0), v[ch]);
+          for (int ch = 0; ch < 4; ++ch) tmem_ld8(D1 + lane_off + (uint32_t)(ch * PT + p0), v[ch]);
+          if (!top)
+#pragma unroll
+            for (int ch = 0; ch < 4; ++ch) gin[ch] = ld_shared_v4(sg + tile_chunk(j, 4 * ch + pq));
           tmem_wait_ld();
-#pragma unroll
-          for (int i = 0; i < NP; ++i) {
-            z[i] = __uint_as_float(v[0][i]) + bj;
-            zx[i] = __uint_as_float(v[1][i]);
-            zy[i] = __uint_as_float(v[2][i]);
-            zl[i] = __uint_as_float(v[3][i]);
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) {
+            mbar_arrive(S.bar(kBD1E));
+            if (!top) mbar_arrive(S.bar(kBGE + sgs));
           }
         } else {
-          uint32_t v[16];
-          tmem_ld16(D1 + lane_off + (uint32_t)p0, v);
-          tmem_wait_ld();
 #pragma unroll
-          for (int i = 0; i < NP; ++i) z[i] = __uint_as_float(v[i]) + bj;
+          for (int ch = 0; ch < 4; ++ch)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[ch][i] = 0u;
         }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(S.bar(kBD1E));
-      } else {
+        float la[8], gu[8];  // top: Delta a of the points, and the gradient reaching Delta a
+        if (top) {
+          // Delta u = w_out . Delta a over the 128 features: shuffles (warp_sum_n) and the
+          // four quadrant warps of this point quarter
+          float part[8];
 #pragma unroll
-        for (int i = 0; i < NP; ++i) { z[i] = 0.f; zx[i] = 0.f; zy[i] = 0.f; zl[i] = 0.f; }
-      }
-      // top layer: the output layer and the loss, u = w_out . a + b_out (data) or
-      // Delta u = w_out . Delta a (collocation), summed over the 128 features by the
-      // shuffles of warp_sum_n and the four quadrant warps of this point quarter
-      // a = tanh z and s = sech^2 z of this thread's points, computed once
-      float ta[NP], ts[NP];
+          for (int i = 0; i < 8; ++i) {
+            float a, sd;
+            tanh_sech2(__uint_as_float(v[0][i]) + bj, a, sd);
+            const float zx = __uint_as_float(v[1][i]), zy = __uint_as_float(v[2][i]);
+            la[i] = fmaf(-2.0f * a * sd, zx * zx + zy * zy, sd * __uint_as_float(v[3][i]));
+            part[i] = wo * la[i];
+          }
+          int idx;
+          const float tot = warp_sum_n<8>(part, lane, idx);
+          // the scratch alternates between tiles, so one barrier per tile suffices: a
+          // quarter's warps rewrite a half only after all of them passed the barrier of
+          // the tile after the one that read it
+          if ((lane & 3) == 0) rb[(pq * 4 + q) * NP + idx] = tot;
+          named_barrier_sync(2 + pq, 128);
 #pragma unroll
-      for (int i = 0; i < NP; ++i) tanh_sech2(z[i], ta[i], ts[i]);
-      float gu[NP];
-      if (top) {
-        float part[NP];
-#pragma unroll
-        for (int i = 0; i < NP; ++i) {
-          if constexpr (C == 4) part[i] = wo * fmaf(-2.0f * ta[i] * ts[i], zx[i] * zx[i] + zy[i] * zy[i], ts[i] * zl[i]);
-          else part[i] = wo * ta[i];
-        }
-        int idx;
-        const float tot = warp_sum_n<NP>(part, lane, idx);
-        constexpr int kLanesPerValue = 32 / NP;
-        // the scratch alternates between tiles, so one barrier per tile suffices: a
-        // quarter's warps rewrite a half only after all of them passed the barrier of
-        // the tile after the one that read it
-        float* rb = red + (it & 1) * 256;
-        if ((lane & (kLanesPerValue - 1)) == 0) rb[(pq * 4 + q) * 16 + idx] = tot;
-        named_barrier_sync(2 + pq, 128);
-#pragma unroll
-        for (int i = 0; i < NP; ++i) {
-          const float sum = rb[(pq * 4 + 0) * 16 + i] + rb[(pq * 4 + 1) * 16 + i] + rb[(pq * 4 + 2) * 16 + i] +
-                            rb[(pq * 4 + 3) * 16 + i];
-          float d = sum;                                                       // Delta u
-          if constexpr (C == 1) d = sum + *P.bout - P.Y[(size_t)t * PT + p0 + i];  // u - y
-          gu[i] = P.gscale * d;
-          if (q == 0 && lane == 0 && ok) {
-            lsum += (double)d * (double)d;
-            if constexpr (C == 1) gbo += gu[i];
+          for (int i = 0; i < 8; ++i) {
+            const float d = rb[(pq * 4 + 0) * NP + i] + rb[(pq * 4 + 1) * NP + i] + rb[(pq * 4 + 2) * NP + i] +
+                            rb[(pq * 4 + 3) * NP + i];  // Delta u: collocation tiles are always full
+            const float g = P.gscale * d;
+            gu[i] = g * wo;
+            gwo = fmaf(g, la[i], gwo);
+            if (q == 0 && lane == 0 && ok) lsum += (double)d * (double)d;
           }
         }
-      }
-      if (ok) {
-        float o[C][NP];
-        if constexpr (C == 4) {
-          float ga[4][NP];
-          if (top) {
+        // MMA 3 of tile it-1 has finished reading the g_Z^T tile this tile rewrites
+        if (ok && it > 0) ok = wait_warp(S.bar(kBGZE), (uint32_t)((it - 1) & 1), abort_flag, P.status);
+        if (ok) {
+          uint32_t w[4][4];
 #pragma unroll
-            for (int i = 0; i < NP; ++i) { ga[0][i] = 0.f; ga[1][i] = 0.f; ga[2][i] = 0.f; ga[3][i] = gu[i] * wo; }
-          } else {
+          for (int i = 0; i < 8; i += 2) {
+            float o[4][2];
 #pragma unroll
-            for (int ch = 0; ch < 4; ++ch) {
-              const uint2 w = ld_shared_v2(row_addr(sg, ch));
-              ga[ch][0] = __uint_as_float(w.x << 16);
-              ga[ch][1] = __uint_as_float(w.x & 0xffff0000u);
-              ga[ch][2] = __uint_as_float(w.y << 16);
-              ga[ch][3] = __uint_as_float(w.y & 0xffff0000u);
+            for (int u = 0; u < 2; ++u) {
+              const int k = i + u;
+              float a, sd;
+              tanh_sech2(__uint_as_float(v[0][k]) + bj, a, sd);
+              const float zx = __uint_as_float(v[1][k]), zy = __uint_as_float(v[2][k]), zl = __uint_as_float(v[3][k]);
+              float ga[4];
+              if (top) {
+                ga[0] = 0.f; ga[1] = 0.f; ga[2] = 0.f; ga[3] = gu[k];
+              } else {
+#pragma unroll
+                for (int ch = 0; ch < 4; ++ch) ga[ch] = bf16_word(gin[ch], k);
+              }
+              const float td = -2.0f * a * sd;
+              const float tp = -2.0f * sd * sd + 4.0f * a * a * sd;
+              const float q2 = zx * zx + zy * zy;
+              const float g0 = ga[0] * sd + (ga[1] * zx + ga[2] * zy) * td + ga[3] * fmaf(tp, q2, td * zl);
+              o[0][u] = g0;
+              o[1][u] = fmaf(ga[1], sd, 2.0f * ga[3] * td * zx);
+              o[2][u] = fmaf(ga[2], sd, 2.0f * ga[3] * td * zy);
+              o[3][u] = ga[3] * sd;
+              gb += g0;
             }
-          }
 #pragma unroll
-          for (int i = 0; i < NP; ++i) {
-            const float a = ta[i], sd = ts[i];
-            const float td = -2.0f * a * sd;
-            const float tp = -2.0f * sd * sd + 4.0f * a * a * sd;
-            const float q2 = zx[i] * zx[i] + zy[i] * zy[i];
-            const float gal = ga[3][i];
-            if (top) gwo = fmaf(gu[i], fmaf(td, q2, sd * zl[i]), gwo);
-            const float g0 = ga[0][i] * sd + (ga[1][i] * zx[i] + ga[2][i] * zy[i]) * td + gal * fmaf(tp, q2, td * zl[i]);
-            o[0][i] = g0;
-            o[1][i] = fmaf(ga[1][i], sd, 2.0f * gal * td * zx[i]);
-            o[2][i] = fmaf(ga[2][i], sd, 2.0f * gal * td * zy[i]);
-            o[3][i] = gal * sd;
-            gb += g0;
+            for (int ch = 0; ch < 4; ++ch) w[ch][i >> 1] = pack2(o[ch][0], o[ch][1]);
           }
 #pragma unroll
           for (int ch = 0; ch < 4; ++ch)
-            st_shared_v2(row_addr(gzt, ch), pack2(o[ch][0], o[ch][1]), pack2(o[ch][2], o[ch][3]));
-        } else {
-          float ga[NP];
-          if (top) {
-#pragma unroll
-            for (int i = 0; i < NP; ++i) ga[i] = gu[i] * wo;
-          } else {
-            unpack8(ld_shared_v4(sg + tile_chunk(j, p0 >> 3)), ga);
-            unpack8(ld_shared_v4(sg + tile_chunk(j, (p0 >> 3) + 1)), ga + 8);
-          }
-#pragma unroll
-          for (int i = 0; i < NP; ++i) {
-            const float a = ta[i], sd = ts[i];
-            if (top) gwo = fmaf(gu[i], a, gwo);
-            o[0][i] = ga[i] * sd;
-            gb += o[0][i];
-          }
-#pragma unroll
-          for (int c = 0; c < 2; ++c)
-            st_shared_v4(gzt + tile_chunk(j, (p0 >> 3) + c), pack2(o[0][8 * c], o[0][8 * c + 1]),
-                         pack2(o[0][8 * c + 2], o[0][8 * c + 3]), pack2(o[0][8 * c + 4], o[0][8 * c + 5]),
-                         pack2(o[0][8 * c + 6], o[0][8 * c + 7]));
+            st_shared_v4(sGZ + tile_chunk(j, 4 * ch + pq), w[ch][0], w[ch][1], w[ch][2], w[ch][3]);
         }
+      } else {
+        // value channel: 32 points per thread in groups of 8, each group read from D1 (and
+        // the gA slot) when it is worked on; both are released after the last group
+        if (top) {
+          // u = w_out . a + b_out over the 128 features
+#pragma unroll 1
+          for (int g8 = 0; g8 < 4; ++g8) {
+            uint32_t v[8];
+            if (ok) {
+              tmem_ld8(D1 + lane_off + (uint32_t)(p0 + 8 * g8), v);
+              tmem_wait_ld();
+            }
+            float part[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              float a, sd;
+              tanh_sech2(ok ? __uint_as_float(v[i]) + bj : 0.f, a, sd);
+              part[i] = wo * a;
+            }
+            int idx;
+            const float tot = warp_sum_n<8>(part, lane, idx);
+            if ((lane & 3) == 0) rb[(pq * 4 + q) * NP + 8 * g8 + idx] = tot;
+          }
+          named_barrier_sync(2 + pq, 128);
+        }
+        if (ok && it > 0) ok = wait_warp(S.bar(kBGZE), (uint32_t)((it - 1) & 1), abort_flag, P.status);
+        const float bo = top ? *P.bout : 0.f;
+#pragma unroll 1
+        for (int g8 = 0; g8 < 4; ++g8) {
+          uint32_t v[8];
+          uint4 gin = make_uint4(0u, 0u, 0u, 0u);
+          if (ok) {
+            tmem_ld8(D1 + lane_off + (uint32_t)(p0 + 8 * g8), v);
+            if (!top) gin = ld_shared_v4(sg + tile_chunk(j, 4 * pq + g8));
+            tmem_wait_ld();
+          }
+          float o[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int k = 8 * g8 + i;
+            float a, sd;
+            tanh_sech2(ok ? __uint_as_float(v[i]) + bj : 0.f, a, sd);
+            float ga;
+            if (top) {
+              const float sum = rb[(pq * 4 + 0) * NP + k] + rb[(pq * 4 + 1) * NP + k] + rb[(pq * 4 + 2) * NP + k] +
+                                rb[(pq * 4 + 3) * NP + k];
+              // u - y; the padding past the last data point has no residual
+              const int pt = t * PT + p0 + k;
+              const float d = pt < P.n_pts ? sum + bo - P.Y[pt] : 0.f;
+              const float g = P.gscale * d;
+              ga = g * wo;
+              gwo = fmaf(g, a, gwo);
+              if (q == 0 && lane == 0 && ok) {
+                lsum += (double)d * (double)d;
+                gbo += g;
+              }
+            } else {
+              ga = bf16_word(gin, i);
+            }
+            o[i] = ga * sd;
+            gb += o[i];
+          }
+          if (ok)
+            st_shared_v4(sGZ + tile_chunk(j, 4 * pq + g8), pack2(o[0], o[1]), pack2(o[2], o[3]), pack2(o[4], o[5]),
+                         pack2(o[6], o[7]));
+        }
+        if (ok) {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) {
+            mbar_arrive(S.bar(kBD1E));
+            if (!top) mbar_arrive(S.bar(kBGE + sgs));
+          }
+        }
+      }
+      if (ok) {
         fence_proxy_async_smem();
         __syncwarp();
-        if (lane == 0) {
-          mbar_arrive(S.bar(kBGZ + zb));
-          mbar_arrive(S.bar(kBInE + s));
-        }
+        if (lane == 0) mbar_arrive(S.bar(kBGZF));
       }
     };
 
-    // ---- epilogue 2 of tile it: the gA_{l-1} tile (row = this thread's input feature),
-    // written to staging tile it mod 2. One barrier per tile: before it, thread 0 waits
-    // until the store of tile it-1 has read its staging tile, which tile it+1 rewrites.
+    // ---- epilogue 2 of tile it: the gA_{l-1} tile (row = this thread's input feature).
+    // Two barriers: the store of tile it-1 has read the staging tile before anyone
+    // rewrites it, and every row is written before thread 0 stores the tile.
     auto epi2 = [&](int it) {
       const int t = (int)blockIdx.x + it * (int)gridDim.x;
-      const uint32_t sOutB = sOut + (uint32_t)(it & 1) * kTile;
+      uint32_t v[C == 4 ? 4 : 1][C == 4 ? 8 : 32];
       if (ok) ok = wait_warp(S.bar(kBD2F), (uint32_t)(it & 1), abort_flag, P.status);
       if (ok) {
         tc_fence_after();
         if constexpr (C == 4) {
-          uint32_t v[4][4];
 #pragma unroll
-          for (int ch = 0; ch < 4; ++ch) tmem_ld4(D2 + lane_off + (uint32_t)(ch * 16 + p0), v[ch]);
-          tmem_wait_ld();
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(S.bar(kBD2E));
-#pragma unroll
-          for (int ch = 0; ch < 4; ++ch)
-            st_shared_v2(row_addr(sOutB, ch), pack2(__uint_as_float(v[ch][0]), __uint_as_float(v[ch][1])),
-                         pack2(__uint_as_float(v[ch][2]), __uint_as_float(v[ch][3])));
+          for (int ch = 0; ch < 4; ++ch) tmem_ld8(D2 + lane_off + (uint32_t)(ch * PT + p0), v[ch]);
         } else {
-          uint32_t v[16];
-          tmem_ld16(D2 + lane_off + (uint32_t)p0, v);
-          tmem_wait_ld();
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(S.bar(kBD2E));
-#pragma unroll
-          for (int c = 0; c < 2; ++c)
-            st_shared_v4(sOutB + tile_chunk(j, (p0 >> 3) + c),
-                         pack2(__uint_as_float(v[8 * c]), __uint_as_float(v[8 * c + 1])),
-                         pack2(__uint_as_float(v[8 * c + 2]), __uint_as_float(v[8 * c + 3])),
-                         pack2(__uint_as_float(v[8 * c + 4]), __uint_as_float(v[8 * c + 5])),
-                         pack2(__uint_as_float(v[8 * c + 6]), __uint_as_float(v[8 * c + 7])));
+          tmem_ld32(D2 + lane_off + (uint32_t)p0, v[0]);
         }
-        fence_proxy_async_smem();
+        tmem_wait_ld();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(S.bar(kBD2E));
       }
       if (e == 0 && lane == 0) bulk_wait_read<0>();
       named_barrier_sync(1, kEpiB * 32);
+      if (ok) {
+#pragma unroll
+        for (int ch = 0; ch < C; ++ch)
+#pragma unroll
+          for (int cc = 0; cc < NP / 8; ++cc) {
+            const uint32_t* w = v[ch] + 8 * cc;
+            st_shared_v4(sOut + tile_chunk(j, chunk(ch, cc)), pack2(__uint_as_float(w[0]), __uint_as_float(w[1])),
+                         pack2(__uint_as_float(w[2]), __uint_as_float(w[3])),
+                         pack2(__uint_as_float(w[4]), __uint_as_float(w[5])),
+                         pack2(__uint_as_float(w[6]), __uint_as_float(w[7])));
+          }
+        fence_proxy_async_smem();
+      }
+      named_barrier_sync(1, kEpiB * 32);
       if (e == 0 && lane == 0 && ok && !*abort_flag) {
-        bulk_s2g(P.gA_out + (size_t)t * kTile, sOutB, kTile);
+        bulk_s2g(P.gA_out + (size_t)t * kTile, sOut, kTile);
         bulk_commit();
       }
     };
@@ -719,7 +788,7 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
     if (ok && n_it > 0) {
       tc_fence_after();
       uint32_t v[32];
-      tmem_ld32(D3 + lane_off + (uint32_t)k0, *reinterpret_cast<uint32_t(*)[32]>(v));
+      tmem_ld32(D3 + lane_off + (uint32_t)k0, v);
       tmem_wait_ld();
 #pragma unroll
       for (int i = 0; i < 32; i += 4)
@@ -751,15 +820,21 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
 
 // A_0 tiles: the input-split first layer (Eq. 8), z = Bf[f] + b0 + W2 x (FP32), in Taylor
 // mode (z_x = W2[:,0], z_y = W2[:,1], Delta z = 0). One thread per (feature, 8 points):
-// each channel of the 8 points is one 16-byte chunk of the feature's row.
+// each channel of the 8 points is one 16-byte chunk of the feature's rows. Rows past the
+// last point (the padding of the last tile) are written as zeros.
 __global__ void tc_first_fwd_kernel(const float* __restrict__ Bf, const float* __restrict__ W0,
                                     const float* __restrict__ b0, const float* __restrict__ X, int n, int R, int C,
-                                    uint8_t* __restrict__ A0) {
+                                    int R_pad, uint8_t* __restrict__ A0) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (R / 8) * kW) return;
+  if (idx >= (R_pad / 8) * kW) return;
   const int k = idx % kW, pt0 = 8 * (idx / kW);
-  const int f = pt0 / n;
   const int PT = kTR / C, tile = pt0 / PT, p = pt0 % PT;
+  uint8_t* tb = A0 + (size_t)tile * kTile;
+  if (pt0 >= R) {
+    for (int c = 0; c < C; ++c) *reinterpret_cast<uint4*>(tb + tile_chunk(k, (c * PT + p) >> 3)) = make_uint4(0, 0, 0, 0);
+    return;
+  }
+  const int f = pt0 / n;
   const float w2x = W0[(size_t)k * 130 + 128], w2y = W0[(size_t)k * 130 + 129];
   const float bk = Bf[(size_t)f * kW + k] + b0[k];
   const float lap = w2x * w2x + w2y * w2y;
@@ -774,7 +849,6 @@ __global__ void tc_first_fwd_kernel(const float* __restrict__ Bf, const float* _
     o[2][i] = sd * w2y;
     o[3][i] = -2.0f * a * sd * lap;
   }
-  uint8_t* tb = A0 + (size_t)tile * kTile;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     if (c >= C) break;
@@ -875,8 +949,9 @@ __global__ void tc_sum_float_kernel(const float* __restrict__ part, int n, float
   *out += s;
 }
 
-constexpr size_t kFwdSmem = 1024 + kStagesF * kTile + 2 * kTile + 8 * kFwdBars + 64;
-constexpr size_t kBwdSmem = 1024 + 2 * kStagesB * kTile + 2 * kTile + 2 * kTile + 8 * kBwdBars + 16 + 64;
+constexpr size_t kFwdSmem = 1024 + kStagesF * kTile + 2 * kTile + 8 * kFwdBars + 16 + 64;
+constexpr size_t kBwdSmem = 1024 + (kSlotsA + kSlotsG + 2) * kTile + 8 * kBwdBars + 16 + 64;
+static_assert(kFwdSmem <= 232448, "forward kernel shared memory");
 static_assert(kBwdSmem <= 232448, "backward kernel shared memory");
 
 int grid_for(int n_tiles) {
@@ -892,6 +967,7 @@ int grid_for(int n_tiles) {
 }  // namespace
 
 size_t tc_tile_bytes() { return kTile; }
+int tc_tiles(int R, int C) { return (int)(((long long)R * C + kTR - 1) / kTR); }
 int tc_partial_groups() { return 4; }
 size_t tc_image_bytes() { return kWImg; }
 int tc_partial_ctas() { return grid_for(1 << 30); }
@@ -904,8 +980,9 @@ cudaError_t tc_pack_weights(const float* W, void* img, void* imgT, cudaStream_t 
 
 cudaError_t tc_first_fwd(const float* Bf, const float* W0, const float* b0, const float* X, int n, int R, int C,
                          void* A0, cudaStream_t st) {
-  const int threads = (R / 8) * kW;
-  tc_first_fwd_kernel<<<(threads + 255) / 256, 256, 0, st>>>(Bf, W0, b0, X, n, R, C, static_cast<uint8_t*>(A0));
+  const int R_pad = tc_tiles(R, C) * (kTR / C);
+  const int threads = (R_pad / 8) * kW;
+  tc_first_fwd_kernel<<<(threads + 255) / 256, 256, 0, st>>>(Bf, W0, b0, X, n, R, C, R_pad, static_cast<uint8_t*>(A0));
   return cudaGetLastError();
 }
 
@@ -927,15 +1004,16 @@ cudaError_t tc_layer_fwd(const TcFwdParams& p, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <int C>
+template <int C, bool kTop>
 cudaError_t launch_bwd(const TcBwdParams& p, int grid, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tc_bwd_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdSmem);
+    cudaError_t e =
+        cudaFuncSetAttribute(tc_bwd_kernel<C, kTop>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdSmem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  tc_bwd_kernel<C><<<grid, kThreadsB, kBwdSmem, st>>>(p);
+  tc_bwd_kernel<C, kTop><<<grid, kThreadsB, kBwdSmem, st>>>(p);
   return cudaGetLastError();
 }
 
@@ -943,8 +1021,8 @@ cudaError_t tc_layer_bwd(const TcBwdParams& p, int* grid_used, cudaStream_t st) 
   const int grid = p.n_tiles > 0 ? grid_for(p.n_tiles) : 0;
   if (grid_used) *grid_used = grid;
   if (grid == 0) return cudaSuccess;
-  if (p.C == 4) return launch_bwd<4>(p, grid, st);
-  if (p.C == 1) return launch_bwd<1>(p, grid, st);
+  if (p.C == 4) return p.top ? launch_bwd<4, true>(p, grid, st) : launch_bwd<4, false>(p, grid, st);
+  if (p.C == 1) return p.top ? launch_bwd<1, true>(p, grid, st) : launch_bwd<1, false>(p, grid, st);
   return cudaErrorInvalidValue;
 }
 

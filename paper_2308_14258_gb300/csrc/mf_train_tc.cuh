@@ -35,12 +35,14 @@ struct TcBwdParams {
   float* gwout_part;     // top: [CTAs][4][128]
   float* gbout_part;     // top: [CTAs][4]
   int n_tiles;
+  int n_pts;             // points of the pass (the value channel's last tile may be padded)
   int C;
   int top;
   int* status;
 };
 
-size_t tc_tile_bytes();     // bytes of one 64 x 128 BF16 tile
+size_t tc_tile_bytes();     // bytes of one 128 x 128 BF16 tile
+int tc_tiles(int R, int C); // tiles of R points with C channels (the last one padded)
 size_t tc_image_bytes();    // bytes of one 128 x 128 BF16 weight image
 int tc_partial_ctas();      // most CTAs a backward launch uses (partial-buffer rows)
 int tc_partial_groups();    // partial sums per CTA of g_b, g_wout, g_bout and the loss
