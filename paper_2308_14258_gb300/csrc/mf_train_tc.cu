@@ -84,9 +84,9 @@ __device__ __forceinline__ uint4 ld_shared_v4(uint32_t addr) {
                : "memory");
   return v;
 }
-__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
-  return (uint32_t)bf16_bits(lo) | ((uint32_t)bf16_bits(hi) << 16);
-}
+// two floats as one BF16 pair (round to nearest even), lo in the low half: one paired
+// conversion instead of two single ones
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) { return pack_bf16x2(lo, hi); }
 // the 8 BF16 values of a chunk as floats
 __device__ __forceinline__ void unpack8(uint4 v, float* f) {
   const uint32_t w[4] = {v.x, v.y, v.z, v.w};
@@ -95,6 +95,17 @@ __device__ __forceinline__ void unpack8(uint4 v, float* f) {
     f[2 * i] = __uint_as_float(w[i] << 16);
     f[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
   }
+}
+
+// Register reallocation between the warpgroups of a CTA (all four warps of a warpgroup
+// execute it; the increase waits until the registers it needs have been given back).
+template <int N>
+__device__ __forceinline__ void setmaxnreg_dec() {
+  asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(N));
+}
+template <int N>
+__device__ __forceinline__ void setmaxnreg_inc() {
+  asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(N));
 }
 
 // BF16 value i (0..7) of a 16-byte chunk, as a float
@@ -144,6 +155,16 @@ __device__ __forceinline__ void weights_to_tmem(const uint8_t* __restrict__ img,
     v[4 * c] = w.x; v[4 * c + 1] = w.y; v[4 * c + 2] = w.z; v[4 * c + 3] = w.w;
   }
   tmem_st16(tcol + ((uint32_t)(32 * q) << 16) + (uint32_t)(16 * cq), v);
+}
+
+// Bounded waits, inline (the backward kernel reallocates registers between warpgroups,
+// so it calls no out-of-line function): a single thread (wait_fast) or a whole warp
+// (wait_warp_fast, which continues only if every lane saw the phase complete).
+__device__ __forceinline__ bool wait_fast(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status) {
+  return wait_spin_inl(bar, parity, abort_flag, status);
+}
+__device__ __forceinline__ bool wait_warp_fast(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status) {
+  return __all_sync(0xffffffffu, wait_spin_inl(bar, parity, abort_flag, status));
 }
 
 struct Smem {
@@ -230,8 +251,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) tc_fwd_kernel(const __grid_cons
       bool ok = true;
       for (int it = 0; ok && it < n_it; ++it) {
         const int s = it % kStagesF, b = it & 1;
-        ok = wait_spin(S.bar(kFInF + s), (uint32_t)((it / kStagesF) & 1), abort_flag, P.status);
-        if (ok && it >= 2) ok = wait_spin(S.bar(kFAccE + b), (uint32_t)(((it >> 1) - 1) & 1), abort_flag, P.status);
+        ok = wait_fast(S.bar(kFInF + s), (uint32_t)((it / kStagesF) & 1), abort_flag, P.status);
+        if (ok && it >= 2) ok = wait_fast(S.bar(kFAccE + b), (uint32_t)(((it >> 1) - 1) & 1), abort_flag, P.status);
         if (!ok) break;
         tc_fence_after();
         const uint32_t tin = sIn + (uint32_t)s * kTile;
@@ -277,7 +298,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) tc_fwd_kernel(const __grid_cons
     for (int it = 0; it < n_it; ++it) {
       const int b = it & 1;
       const int t = (int)blockIdx.x + it * (int)gridDim.x;
-      if (ok) ok = wait_warp(S.bar(kFAccF + b), (uint32_t)((it >> 1) & 1), abort_flag, P.status);
+      if (ok) ok = wait_warp_fast(S.bar(kFAccF + b), (uint32_t)((it >> 1) & 1), abort_flag, P.status);
       const uint32_t stage = sOut + (uint32_t)b * kTile;
       if (ok) {
         tc_fence_after();
@@ -342,8 +363,15 @@ __global__ void __launch_bounds__(kThreadsTc, 1) tc_fwd_kernel(const __grid_cons
 
 // ------------------------------------------------------------------ backward kernel
 
-// Backward kernel: 16 epilogue warps (feature quadrant q = w mod 4, point quarter
-// pq = (w-2)/4). Shared memory: three A_{l-1} slots (each held from MMA 1 to MMA 3 of its
+// Backward kernel: 20 warps in five warpgroups. Warpgroup 0 holds the MMA issuer (warp
+// 0) and the load issuer (warp 1); warps 4-19 are the epilogue (feature quadrant
+// q = w mod 4, point quarter pq = (w-4)/4). The CTA is launched with kRegsLaunch registers
+// per thread; warpgroup 0 then gives registers back (setmaxnreg.dec to kRegsIssue) and the
+// epilogue takes them (setmaxnreg.inc to kRegsEpi), so that its chain-rule arithmetic runs
+// without spills: 128 kRegsIssue + 512 kRegsEpi <= 640 kRegsLaunch. Every warp returns to
+// kRegsLaunch before the common tail of the kernel; the warps of a warpgroup pass a named
+// barrier between two setmaxnreg instructions (barrier 6 for warpgroup 0, 1 for the
+// epilogue). Shared memory: three A_{l-1} slots (each held from MMA 1 to MMA 3 of its
 // tile), two gA_l slots (held until epilogue 1 has read them), one g_Z^T tile and one
 // staging tile for gA_{l-1}: 224 KB. Epilogue order 1(0), then per t: 1(t+1), 2(t), so
 // that epilogue 1 of tile t+1 runs while MMAs 2 and 3 of tile t execute. W and W^T are the
@@ -353,7 +381,14 @@ __global__ void __launch_bounds__(kThreadsTc, 1) tc_fwd_kernel(const __grid_cons
 // 16 d2_empty; 17 d3_done; 18 drain. Each barrier is waited on before it can complete
 // again.
 constexpr int kEpiB = 16;
-constexpr int kThreadsB = (2 + kEpiB) * 32;
+constexpr int kEpiWarp0 = 4;                        // first epilogue warp
+constexpr int kThreadsB = (kEpiWarp0 + kEpiB) * 32;  // 640
+constexpr int kRegsLaunch = 96;                     // 65536 / 640, rounded down to a multiple of 8
+constexpr int kRegsIssue = 56;
+constexpr int kRegsEpi = 104;
+static_assert(128 * kRegsIssue + 32 * kEpiB * kRegsEpi <= kThreadsB * kRegsLaunch,
+              "the register split must fit in the launch allocation");
+static_assert(32 * (kRegsIssue + 4 * kRegsEpi) <= 16384, "registers of one SM sub-partition");
 constexpr int kSlotsA = 3;
 constexpr int kSlotsG = 2;
 constexpr int kBwdBars = 19;
@@ -439,8 +474,8 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
   // TMEM columns: D1 = Z^T [0, 128), D2 = gA^T [128, 256), D3 = g_W [256, 384),
   // W [384, 448) and W^T [448, 512) as A operands
   const uint32_t D1 = tmem, D2 = tmem + 128, D3 = tmem + 256, Wt = tmem + 384, WTt = tmem + 448;
-  if (warp >= 2) {
-    const int cq = (warp - 2) >> 2;
+  if (warp >= kEpiWarp0) {
+    const int cq = (warp - kEpiWarp0) >> 2;
     weights_to_tmem(static_cast<const uint8_t*>(P.wimg), Wt, warp & 3, lane, cq);
     weights_to_tmem(static_cast<const uint8_t*>(P.wimgT), WTt, warp & 3, lane, cq);
     tmem_wait_st();
@@ -448,96 +483,104 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-
-  if (warp == 0) {
-    if (lane == 0) {
-      bool ok = true;
-      // MMA 1 (Z^T = W A^T) of tile `it`, once its A tile is in and D1 has been read out
-      auto mma1 = [&](int it) -> bool {
-        const int s = it % kSlotsA;
-        if (!wait_spin(S.bar(kBAF + s), (uint32_t)((it / kSlotsA) & 1), abort_flag, P.status)) return false;
-        if (it > 0 && !wait_spin(S.bar(kBD1E), (uint32_t)((it - 1) & 1), abort_flag, P.status)) return false;
-        tc_fence_after();
-        const uint32_t ta = sA + (uint32_t)s * kTile;
-#pragma unroll
-        for (int ks = 0; ks < kW / 16; ++ks) {
-          if (ks == 0) mma_ts<0>(D1, Wt + (uint32_t)(8 * ks), desc_rows(ta, ks), kIdescRows);
-          else mma_ts<1>(D1, Wt + (uint32_t)(8 * ks), desc_rows(ta, ks), kIdescRows);
+  // warpgroup 0 (issuers) gives registers to the epilogue warpgroups and takes them
+  // back at the end, each warpgroup at one setmaxnreg site
+  if (warp < kEpiWarp0) {
+    setmaxnreg_dec<kRegsIssue>();
+    if (warp == 0) {
+      if (lane == 0) {
+        bool ok = true;
+        // MMA 1 (Z^T = W A^T) of tile `it`, once its A tile is in and D1 has been read out
+        auto mma1 = [&](int it) -> bool {
+          const int s = it % kSlotsA;
+          if (!wait_fast(S.bar(kBAF + s), (uint32_t)((it / kSlotsA) & 1), abort_flag, P.status)) return false;
+          if (it > 0 && !wait_fast(S.bar(kBD1E), (uint32_t)((it - 1) & 1), abort_flag, P.status)) return false;
+          tc_fence_after();
+          const uint32_t ta = sA + (uint32_t)s * kTile;
+  #pragma unroll
+          for (int ks = 0; ks < kW / 16; ++ks) {
+            if (ks == 0) mma_ts<0>(D1, Wt + (uint32_t)(8 * ks), desc_rows(ta, ks), kIdescRows);
+            else mma_ts<1>(D1, Wt + (uint32_t)(8 * ks), desc_rows(ta, ks), kIdescRows);
+          }
+          mma_commit(S.bar(kBD1F));
+          return true;
+        };
+        if (n_it > 0) ok = mma1(0);
+        for (int it = 0; ok && it < n_it; ++it) {
+          const int s = it % kSlotsA;
+          const uint32_t ta = sA + (uint32_t)s * kTile;
+          // the next tile's recompute runs while epilogue 1 of this tile works
+          if (it + 1 < n_it && !mma1(it + 1)) { ok = false; break; }
+          ok = wait_fast(S.bar(kBGZF), (uint32_t)(it & 1), abort_flag, P.status);
+          if (ok && it > 0) ok = wait_fast(S.bar(kBD2E), (uint32_t)((it - 1) & 1), abort_flag, P.status);
+          if (!ok) break;
+          tc_fence_after();
+          // MMA 2: gA^T = W^T g_Z^T (g_Z^T tile read MN-major: N = rows, K = features)
+  #pragma unroll
+          for (int ks = 0; ks < kW / 16; ++ks) {
+            if (ks == 0) mma_ts<0>(D2, WTt + (uint32_t)(8 * ks), desc_rows(sGZ, ks), kIdescRows);
+            else mma_ts<1>(D2, WTt + (uint32_t)(8 * ks), desc_rows(sGZ, ks), kIdescRows);
+          }
+          mma_commit(S.bar(kBD2F));
+          // MMA 3: g_W += g_Z^T A (both tiles read K-major: M, N = features, K = rows)
+          const uint64_t gzd = desc_sw128(sGZ), tad = desc_sw128(ta);
+  #pragma unroll
+          for (int ks = 0; ks < kTR / 16; ++ks) {
+            const uint64_t a_op = desc_add(gzd, kstep_rows(ks));
+            const uint64_t b_op = desc_add(tad, kstep_rows(ks));
+            if (it == 0 && ks == 0) mma_ss<0>(D3, a_op, b_op, kIdescGW);
+            else mma_ss<1>(D3, a_op, b_op, kIdescGW);
+          }
+          mma_commit(S.bar(kBGZE));
+          mma_commit(S.bar(kBAE + s));
         }
-        mma_commit(S.bar(kBD1F));
-        return true;
-      };
-      if (n_it > 0) ok = mma1(0);
-      for (int it = 0; ok && it < n_it; ++it) {
-        const int s = it % kSlotsA;
-        const uint32_t ta = sA + (uint32_t)s * kTile;
-        // the next tile's recompute runs while epilogue 1 of this tile works
-        if (it + 1 < n_it && !mma1(it + 1)) { ok = false; break; }
-        ok = wait_spin(S.bar(kBGZF), (uint32_t)(it & 1), abort_flag, P.status);
-        if (ok && it > 0) ok = wait_spin(S.bar(kBD2E), (uint32_t)((it - 1) & 1), abort_flag, P.status);
-        if (!ok) break;
-        tc_fence_after();
-        // MMA 2: gA^T = W^T g_Z^T (g_Z^T tile read MN-major: N = rows, K = features)
-#pragma unroll
-        for (int ks = 0; ks < kW / 16; ++ks) {
-          if (ks == 0) mma_ts<0>(D2, WTt + (uint32_t)(8 * ks), desc_rows(sGZ, ks), kIdescRows);
-          else mma_ts<1>(D2, WTt + (uint32_t)(8 * ks), desc_rows(sGZ, ks), kIdescRows);
-        }
-        mma_commit(S.bar(kBD2F));
-        // MMA 3: g_W += g_Z^T A (both tiles read K-major: M, N = features, K = rows)
-        const uint64_t gzd = desc_sw128(sGZ), tad = desc_sw128(ta);
-#pragma unroll
-        for (int ks = 0; ks < kTR / 16; ++ks) {
-          const uint64_t a_op = desc_add(gzd, kstep_rows(ks));
-          const uint64_t b_op = desc_add(tad, kstep_rows(ks));
-          if (it == 0 && ks == 0) mma_ss<0>(D3, a_op, b_op, kIdescGW);
-          else mma_ss<1>(D3, a_op, b_op, kIdescGW);
-        }
-        mma_commit(S.bar(kBGZE));
-        mma_commit(S.bar(kBAE + s));
+        mma_commit(S.bar(kBD3));  // every MMA issued, including the last g_W accumulation, done
+        mma_commit(S.bar(kBDrain));
+        wait_bounded_inl(S.bar(kBDrain), 0, abort_flag, P.status, false);
       }
-      mma_commit(S.bar(kBD3));  // every MMA issued, including the last g_W accumulation, done
-      mma_commit(S.bar(kBDrain));
-      wait_bounded(S.bar(kBDrain), 0, abort_flag, P.status, false);
-    }
-    __syncwarp();
-  } else if (warp == 1) {
-    if (lane == 0) {
-      // loads in the order they fall due: gA_l of tile it, then A_{l-1} of tile it+1
-      auto load = [&](int it, int slots, int full, int empty, uint32_t dst0, const uint8_t* src) -> bool {
-        const int s = it % slots;
-        if (it >= slots &&
-            !wait_bounded(S.bar(empty + s), (uint32_t)(((it / slots) - 1) & 1), abort_flag, P.status, true))
-          return false;
-        const int t = (int)blockIdx.x + it * (int)gridDim.x;
-        mbar_arrive_expect_tx(S.bar(full + s), kTile);
-        bulk_g2s(dst0 + (uint32_t)s * kTile, src + (size_t)t * kTile, kTile, S.bar(full + s));
-        return true;
-      };
-      int na = 0, ng = 0;
-      bool ok = n_it > 0 && load(0, kSlotsA, kBAF, kBAE, sA, P.A_in);
-      if (ok) na = 1;
-      for (int it = 0; ok && it < n_it; ++it) {
-        if (!top) {
-          ok = load(it, kSlotsG, kBGF, kBGE, sG, P.gA_in);
-          if (ok) ng = it + 1;
+      __syncwarp();
+    } else if (warp == 1) {
+      if (lane == 0) {
+        // loads in the order they fall due: gA_l of tile it, then A_{l-1} of tile it+1
+        auto load = [&](int it, int slots, int full, int empty, uint32_t dst0, const uint8_t* src) -> bool {
+          const int s = it % slots;
+          if (it >= slots &&
+              !wait_bounded_inl(S.bar(empty + s), (uint32_t)(((it / slots) - 1) & 1), abort_flag, P.status, true))
+            return false;
+          const int t = (int)blockIdx.x + it * (int)gridDim.x;
+          mbar_arrive_expect_tx(S.bar(full + s), kTile);
+          bulk_g2s(dst0 + (uint32_t)s * kTile, src + (size_t)t * kTile, kTile, S.bar(full + s));
+          return true;
+        };
+        int na = 0, ng = 0;
+        bool ok = n_it > 0 && load(0, kSlotsA, kBAF, kBAE, sA, P.A_in);
+        if (ok) na = 1;
+        for (int it = 0; ok && it < n_it; ++it) {
+          if (!top) {
+            ok = load(it, kSlotsG, kBGF, kBGE, sG, P.gA_in);
+            if (ok) ng = it + 1;
+          }
+          if (ok && it + 1 < n_it) {
+            ok = load(it + 1, kSlotsA, kBAF, kBAE, sA, P.A_in);
+            if (ok) na = it + 2;
+          }
         }
-        if (ok && it + 1 < n_it) {
-          ok = load(it + 1, kSlotsA, kBAF, kBAE, sA, P.A_in);
-          if (ok) na = it + 2;
-        }
+        // every load issued has landed before shared memory can go away
+        for (int i = (na > kSlotsA ? na - kSlotsA : 0); i < na; ++i)
+          wait_bounded_inl(S.bar(kBAF + i % kSlotsA), (uint32_t)((i / kSlotsA) & 1), abort_flag, P.status, false);
+        for (int i = (ng > kSlotsG ? ng - kSlotsG : 0); i < ng; ++i)
+          wait_bounded_inl(S.bar(kBGF + i % kSlotsG), (uint32_t)((i / kSlotsG) & 1), abort_flag, P.status, false);
       }
-      // every load issued has landed before shared memory can go away
-      for (int i = (na > kSlotsA ? na - kSlotsA : 0); i < na; ++i)
-        wait_bounded(S.bar(kBAF + i % kSlotsA), (uint32_t)((i / kSlotsA) & 1), abort_flag, P.status, false);
-      for (int i = (ng > kSlotsG ? ng - kSlotsG : 0); i < ng; ++i)
-        wait_bounded(S.bar(kBGF + i % kSlotsG), (uint32_t)((i / kSlotsG) & 1), abort_flag, P.status, false);
+      __syncwarp();
     }
-    __syncwarp();
+    // the four warps of a warpgroup synchronise between two setmaxnreg instructions
+    named_barrier_sync(6, 128);
+    setmaxnreg_inc<kRegsLaunch>();
   } else {
+    setmaxnreg_inc<kRegsEpi>();
     // a warp reads the TMEM lane quadrant (warp index mod 4); the 16 warps cover the four
     // quadrants for each of the four point quarters of a tile
-    const int e = warp - 2, q = warp & 3, pq = e >> 2;
+    const int e = warp - kEpiWarp0, q = warp & 3, pq = e >> 2;
     const int j = 32 * q + lane;  // feature (D1, D3 lanes) / input feature k (D2 lanes)
     const float bj = P.bias[j];
     const float wo = top ? P.wout[j] : 0.f;
@@ -556,8 +599,8 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
       const int t = (int)blockIdx.x + it * (int)gridDim.x;
       const uint32_t sg = sG + (uint32_t)sgs * kTile;
       float* rb = red + (it & 1) * (16 * NP);  // top: [4 quarters][4 quadrants][NP points]
-      if (ok) ok = wait_warp(S.bar(kBD1F), (uint32_t)(it & 1), abort_flag, P.status);
-      if (ok && !top) ok = wait_warp(S.bar(kBGF + sgs), (uint32_t)((it / kSlotsG) & 1), abort_flag, P.status);
+      if (ok) ok = wait_warp_fast(S.bar(kBD1F), (uint32_t)(it & 1), abort_flag, P.status);
+      if (ok && !top) ok = wait_warp_fast(S.bar(kBGF + sgs), (uint32_t)((it / kSlotsG) & 1), abort_flag, P.status);
       if (ok) tc_fence_after();
       if constexpr (C == 4) {
         // D1 columns of the 8 points: z, z_x, z_y, Delta z; D1 and the gA slot are released
@@ -603,6 +646,8 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
           // the tile after the one that read it
           if ((lane & 3) == 0) rb[(pq * 4 + q) * NP + idx] = tot;
           named_barrier_sync(2 + pq, 128);
+          // the tile's squared residuals are summed in FP32, the running total in FP64
+          float lt = 0.f;
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
             const float d = rb[(pq * 4 + 0) * NP + i] + rb[(pq * 4 + 1) * NP + i] + rb[(pq * 4 + 2) * NP + i] +
@@ -610,11 +655,12 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
             const float g = P.gscale * d;
             gu[i] = g * wo;
             gwo = fmaf(g, la[i], gwo);
-            if (q == 0 && lane == 0 && ok) lsum += (double)d * (double)d;
+            lt = fmaf(d, d, lt);
           }
+          if (q == 0 && lane == 0 && ok) lsum += (double)lt;
         }
         // MMA 3 of tile it-1 has finished reading the g_Z^T tile this tile rewrites
-        if (ok && it > 0) ok = wait_warp(S.bar(kBGZE), (uint32_t)((it - 1) & 1), abort_flag, P.status);
+        if (ok && it > 0) ok = wait_warp_fast(S.bar(kBGZE), (uint32_t)((it - 1) & 1), abort_flag, P.status);
         if (ok) {
           uint32_t w[4][4];
 #pragma unroll
@@ -675,8 +721,9 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
           }
           named_barrier_sync(2 + pq, 128);
         }
-        if (ok && it > 0) ok = wait_warp(S.bar(kBGZE), (uint32_t)((it - 1) & 1), abort_flag, P.status);
+        if (ok && it > 0) ok = wait_warp_fast(S.bar(kBGZE), (uint32_t)((it - 1) & 1), abort_flag, P.status);
         const float bo = top ? *P.bout : 0.f;
+        float lt = 0.f, gt = 0.f;  // top: the tile's squared residuals and their gradients
 #pragma unroll 1
         for (int g8 = 0; g8 < 4; ++g8) {
           uint32_t v[8];
@@ -702,10 +749,8 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
               const float g = P.gscale * d;
               ga = g * wo;
               gwo = fmaf(g, a, gwo);
-              if (q == 0 && lane == 0 && ok) {
-                lsum += (double)d * (double)d;
-                gbo += g;
-              }
+              lt = fmaf(d, d, lt);
+              gt += g;
             } else {
               ga = bf16_word(gin, i);
             }
@@ -715,6 +760,10 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
           if (ok)
             st_shared_v4(sGZ + tile_chunk(j, 4 * pq + g8), pack2(o[0], o[1]), pack2(o[2], o[3]), pack2(o[4], o[5]),
                          pack2(o[6], o[7]));
+        }
+        if (top && q == 0 && lane == 0 && ok) {
+          lsum += (double)lt;
+          gbo += gt;
         }
         if (ok) {
           tc_fence_before();
@@ -734,11 +783,12 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
 
     // ---- epilogue 2 of tile it: the gA_{l-1} tile (row = this thread's input feature).
     // Two barriers: the store of tile it-1 has read the staging tile before anyone
-    // rewrites it, and every row is written before thread 0 stores the tile.
+    // rewrites it, and every row is written before thread 0 stores the tile. D2 is
+    // released after the staging writes.
     auto epi2 = [&](int it) {
       const int t = (int)blockIdx.x + it * (int)gridDim.x;
       uint32_t v[C == 4 ? 4 : 1][C == 4 ? 8 : 32];
-      if (ok) ok = wait_warp(S.bar(kBD2F), (uint32_t)(it & 1), abort_flag, P.status);
+      if (ok) ok = wait_warp_fast(S.bar(kBD2F), (uint32_t)(it & 1), abort_flag, P.status);
       if (ok) {
         tc_fence_after();
         if constexpr (C == 4) {
@@ -748,9 +798,6 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
           tmem_ld32(D2 + lane_off + (uint32_t)p0, v[0]);
         }
         tmem_wait_ld();
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(S.bar(kBD2E));
       }
       if (e == 0 && lane == 0) bulk_wait_read<0>();
       named_barrier_sync(1, kEpiB * 32);
@@ -766,6 +813,11 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
                          pack2(__uint_as_float(w[6]), __uint_as_float(w[7])));
           }
         fence_proxy_async_smem();
+        // D2 is released only now: MMAs 2 and 3 of the next tile, which it lets start,
+        // read shared memory at full rate and would slow these stores down
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(S.bar(kBD2E));
       }
       named_barrier_sync(1, kEpiB * 32);
       if (e == 0 && lane == 0 && ok && !*abort_flag) {
@@ -782,7 +834,7 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
     if (e == 0 && lane == 0) bulk_wait_all<0>();
     // per-CTA partial sums: g_W (this warp's quadrant of rows, quarter of columns), g_b,
     // and at the top the output layer and the loss
-    if (ok && n_it > 0) ok = wait_warp(S.bar(kBD3), 0, abort_flag, P.status);
+    if (ok && n_it > 0) ok = wait_warp_fast(S.bar(kBD3), 0, abort_flag, P.status);
     float* gwp = P.gW_part + (size_t)blockIdx.x * kW * kW;
     const int k0 = 32 * pq;
     if (ok && n_it > 0) {
@@ -806,6 +858,8 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
         P.gbout_part[blockIdx.x * 4 + pq] = ok ? gbo : 0.f;
       }
     }
+    named_barrier_sync(1, kEpiB * 32);
+    setmaxnreg_dec<kRegsLaunch>();
   }
 
   tc_fence_before();
@@ -916,30 +970,42 @@ __global__ void tc_pack_kernel(const float* __restrict__ W, uint16_t* __restrict
   img[off / 2] = bf16_bits(v);
 }
 
-// out[j] (+)= sum over b < nblk of part[b * stride + j] (one thread per j): four
-// interleaved partial sums (b mod 4) for latency, combined in a fixed order.
+// out[j] (+)= sum over b < nblk of part[b * stride + j]. A block covers 32 columns with
+// 8 row groups (group r adds rows r, r + 8, ... into two interleaved sums); the group sums
+// are combined in a fixed order, so the result does not depend on timing.
 __global__ void tc_colsum_kernel(const float* __restrict__ part, int nblk, int stride, int n, float* __restrict__ out,
                                  int accumulate) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-  int b = 0;
-  for (; b + 4 <= nblk; b += 4) {
-    s0 += part[(size_t)b * stride + j];
-    s1 += part[(size_t)(b + 1) * stride + j];
-    s2 += part[(size_t)(b + 2) * stride + j];
-    s3 += part[(size_t)(b + 3) * stride + j];
+  __shared__ float sm[8][32];
+  const int c = threadIdx.x & 31, r = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + c;
+  float s0 = 0.f, s1 = 0.f;
+  if (j < n) {
+    int b = r;
+    for (; b + 8 < nblk; b += 16) {
+      s0 += part[(size_t)b * stride + j];
+      s1 += part[(size_t)(b + 8) * stride + j];
+    }
+    if (b < nblk) s0 += part[(size_t)b * stride + j];
   }
-  for (; b < nblk; ++b) s0 += part[(size_t)b * stride + j];
-  const float s = (s0 + s1) + (s2 + s3);
-  out[j] = accumulate ? out[j] + s : s;
+  sm[r][c] = s0 + s1;
+  __syncthreads();
+  if (r == 0 && j < n) {
+    float t = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += sm[k][c];
+    out[j] = accumulate ? out[j] + t : t;
+  }
 }
 
+// *out += scale x (sum of part[0..n)), one warp: lane l adds part[l], part[l + 32], ...,
+// then the 32 lane sums are combined by a fixed butterfly, so the result does not depend
+// on timing.
 __global__ void tc_sum_double_kernel(const double* __restrict__ part, int n, double scale, double* __restrict__ out) {
-  if (threadIdx.x != 0) return;
   double s = 0.0;
-  for (int i = 0; i < n; ++i) s += part[i];
-  *out += s * scale;
+  for (int i = threadIdx.x; i < n; i += 32) s += part[i];
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+  if (threadIdx.x == 0) *out += s * scale;
 }
 
 __global__ void tc_sum_float_kernel(const float* __restrict__ part, int n, float* __restrict__ out) {
@@ -1027,7 +1093,7 @@ cudaError_t tc_layer_bwd(const TcBwdParams& p, int* grid_used, cudaStream_t st) 
 }
 
 cudaError_t tc_colsum(const float* part, int nblk, int stride, int n, float* out, int accumulate, cudaStream_t st) {
-  tc_colsum_kernel<<<(n + 63) / 64, 64, 0, st>>>(part, nblk, stride, n, out, accumulate);
+  tc_colsum_kernel<<<(n + 31) / 32, 256, 0, st>>>(part, nblk, stride, n, out, accumulate);
   return cudaGetLastError();
 }
 

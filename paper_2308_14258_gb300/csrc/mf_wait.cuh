@@ -33,8 +33,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 // Bounded wait on an mbarrier phase; false once the CTA is aborting or after the limit.
-__device__ __noinline__ bool wait_bounded(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status,
-                                          bool honour_abort, unsigned long long limit_ns = kWaitLimitNs) {
+// The _inl forms are for kernels that reallocate registers between warpgroups (a called
+// function has one register budget); the others are out-of-line copies of the same loop.
+__device__ __forceinline__ bool wait_bounded_inl(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status,
+                                                 bool honour_abort, unsigned long long limit_ns = kWaitLimitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = globaltimer();
   while (true) {
@@ -46,6 +48,10 @@ __device__ __noinline__ bool wait_bounded(uint32_t bar, uint32_t parity, volatil
       return false;
     }
   }
+}
+__device__ __noinline__ bool wait_bounded(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status,
+                                          bool honour_abort, unsigned long long limit_ns = kWaitLimitNs) {
+  return wait_bounded_inl(bar, parity, abort_flag, status, honour_abort, limit_ns);
 }
 
 __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
@@ -63,8 +69,8 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
 // Spinning bounded wait: polls the phase without suspending (a suspended try_wait wakes
 // a few hundred cycles after the phase completes, which sits on the critical path);
 // the abort flag and the time limit are checked every 64 polls.
-__device__ __noinline__ bool wait_spin(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status,
-                                       unsigned long long limit_ns = kWaitLimitNs) {
+__device__ __forceinline__ bool wait_spin_inl(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status,
+                                              unsigned long long limit_ns = kWaitLimitNs) {
   if (mbar_test(bar, parity)) return true;
   const unsigned long long t0 = globaltimer();
   for (uint32_t i = 1;; ++i) {
@@ -78,6 +84,10 @@ __device__ __noinline__ bool wait_spin(uint32_t bar, uint32_t parity, volatile i
       }
     }
   }
+}
+__device__ __noinline__ bool wait_spin(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status,
+                                       unsigned long long limit_ns = kWaitLimitNs) {
+  return wait_spin_inl(bar, parity, abort_flag, status, limit_ns);
 }
 
 // Warp-uniform form: every lane waits, and the warp continues only if all lanes saw
