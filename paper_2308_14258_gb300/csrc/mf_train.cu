@@ -585,10 +585,11 @@ mf_status run_pass_fused(mf_trainer* t, int C, int F, int n, const float* G, con
   }
   // first layer: W2 columns and b0 from all rows, W1 through per-function sums
   const int nblk = R / kRB;
-  const int ncol = (H + 31) / 32;
   TR_CUDA(mf::tc_first_bwd(t->Bf, t->w, t->w + t->off_b0, X, n, R, C, gbuf[cur], t->part, st),
           "train: first layer backward");
-  for (int q = 0; q < 3; ++q) colsum_kernel<<<ncol, 1024, 0, st>>>(t->part + q * H, nblk, 3 * H, H, t->sums + q * H, 0);
+  // the per-CTA g_W buffer is free again here and holds the first stage of the sums
+  TR_CUDA(mf::tc_colsum_tall(t->part, nblk, 3 * H, 3 * H, t->tc_gw, ctas * H * H, t->sums, 0, st),
+          "train: first layer sums");
   add_w2_b0_kernel<<<1, H, 0, st>>>(t->sums, H, t->g, t->g + t->off_b0);
   per_function_sum_kernel<<<F, H, 0, st>>>(t->part, n / kRB, H, t->S);
   TR_CUDA(cudaGetLastError(), "train: first layer gradients");

@@ -873,83 +873,111 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
 // ------------------------------------------------------------------ first layer
 
 // A_0 tiles: the input-split first layer (Eq. 8), z = Bf[f] + b0 + W2 x (FP32), in Taylor
-// mode (z_x = W2[:,0], z_y = W2[:,1], Delta z = 0). One thread per (feature, 8 points):
-// each channel of the 8 points is one 16-byte chunk of the feature's rows. Rows past the
-// last point (the padding of the last tile) are written as zeros.
-__global__ void tc_first_fwd_kernel(const float* __restrict__ Bf, const float* __restrict__ W0,
-                                    const float* __restrict__ b0, const float* __restrict__ X, int n, int R, int C,
-                                    int R_pad, uint8_t* __restrict__ A0) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (R_pad / 8) * kW) return;
-  const int k = idx % kW, pt0 = 8 * (idx / kW);
-  const int PT = kTR / C, tile = pt0 / PT, p = pt0 % PT;
-  uint8_t* tb = A0 + (size_t)tile * kTile;
-  if (pt0 >= R) {
-    for (int c = 0; c < C; ++c) *reinterpret_cast<uint4*>(tb + tile_chunk(k, (c * PT + p) >> 3)) = make_uint4(0, 0, 0, 0);
-    return;
-  }
-  const int f = pt0 / n;
+// mode (z_x = W2[:,0], z_y = W2[:,1], Delta z = 0). One block of 128 threads per tile:
+// thread k computes feature k, 8 points at a time (each channel of the 8 points is one
+// 16-byte chunk), into the tile in shared memory; the block then writes the 32 KB tile
+// out with coalesced 16-byte stores. Rows past the last point (the padding of the last
+// tile) are zeros.
+__global__ void __launch_bounds__(kW) tc_first_fwd_kernel(const float* __restrict__ Bf, const float* __restrict__ W0,
+                                                          const float* __restrict__ b0, const float* __restrict__ X,
+                                                          int n, int R, int C, uint8_t* __restrict__ A0) {
+  __shared__ __align__(16) uint8_t tile_s[kTile];
+  const int k = threadIdx.x;
+  const int PT = kTR / C, t = blockIdx.x;
+  const uint32_t ts = smem_addr(tile_s);
   const float w2x = W0[(size_t)k * 130 + 128], w2y = W0[(size_t)k * 130 + 129];
-  const float bk = Bf[(size_t)f * kW + k] + b0[k];
   const float lap = w2x * w2x + w2y * w2y;
-  float o[4][8];
+  const float bk0 = b0[k];
+  for (int p = 0; p < PT; p += 8) {
+    const int pt0 = t * PT + p;
+    if (pt0 >= R) {
+      for (int c = 0; c < C; ++c) st_shared_v4(ts + tile_chunk(k, (c * PT + p) >> 3), 0u, 0u, 0u, 0u);
+      continue;
+    }
+    const float bk = Bf[(size_t)(pt0 / n) * kW + k] + bk0;
+    uint32_t w[4][4];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const float x = X[2 * (size_t)(pt0 + i)], y = X[2 * (size_t)(pt0 + i) + 1];
-    float a, sd;
-    tanh_sech2(fmaf(w2y, y, fmaf(w2x, x, bk)), a, sd);
-    o[0][i] = a;
-    o[1][i] = sd * w2x;
-    o[2][i] = sd * w2y;
-    o[3][i] = -2.0f * a * sd * lap;
-  }
+    for (int i = 0; i < 8; i += 2) {
+      float o[4][2];
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    if (c >= C) break;
-    *reinterpret_cast<uint4*>(tb + tile_chunk(k, (c * PT + p) >> 3)) =
-        make_uint4(pack2(o[c][0], o[c][1]), pack2(o[c][2], o[c][3]), pack2(o[c][4], o[c][5]), pack2(o[c][6], o[c][7]));
+      for (int u = 0; u < 2; ++u) {
+        const float x = X[2 * (size_t)(pt0 + i + u)], y = X[2 * (size_t)(pt0 + i + u) + 1];
+        float a, sd;
+        tanh_sech2(fmaf(w2y, y, fmaf(w2x, x, bk)), a, sd);
+        o[0][u] = a;
+        o[1][u] = sd * w2x;
+        o[2][u] = sd * w2y;
+        o[3][u] = -2.0f * a * sd * lap;
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) w[c][i >> 1] = pack2(o[c][0], o[c][1]);
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      if (c < C) st_shared_v4(ts + tile_chunk(k, (c * PT + p) >> 3), w[c][0], w[c][1], w[c][2], w[c][3]);
   }
+  __syncthreads();
+  const uint4* src = reinterpret_cast<const uint4*>(tile_s);
+  uint4* dst = reinterpret_cast<uint4*>(A0 + (size_t)t * kTile);
+#pragma unroll 4
+  for (int i = threadIdx.x; i < (int)(kTile / 16); i += kW) dst[i] = src[i];
 }
 
 // First-layer backward from the gA_0 tiles: g_z, g_zx, g_zy per (point, feature) and
 // the block partials of sum g_z, sum g_z x + g_zx, sum g_z y + g_zy ([3][128] per block
-// of 64 points; a block never spans two functions since n is a multiple of 64).
-__global__ void tc_first_bwd_kernel(const float* __restrict__ Bf, const float* __restrict__ W0,
-                                    const float* __restrict__ b0, const float* __restrict__ X, int n, int R, int C,
-                                    const uint8_t* __restrict__ gA0, float* __restrict__ part) {
+// of 64 points; a block never spans two functions since n is a multiple of 64). The
+// block's rows of gA_0 (two tiles for the four channels, one 64-row half of a tile for the
+// value channel) are first copied to shared memory with coalesced 16-byte loads.
+__global__ void __launch_bounds__(kW) tc_first_bwd_kernel(const float* __restrict__ Bf, const float* __restrict__ W0,
+                                                          const float* __restrict__ b0, const float* __restrict__ X,
+                                                          int n, int R, int C, const uint8_t* __restrict__ gA0,
+                                                          float* __restrict__ part) {
+  __shared__ __align__(16) uint8_t tile_s[kTile];
   const int j = threadIdx.x;  // 128 threads: one feature, 64 points
   const float w2x = W0[(size_t)j * 130 + 128], w2y = W0[(size_t)j * 130 + 129];
   const float bj = b0[j];
   const float lap = w2x * w2x + w2y * w2y;
   const int PT = kTR / C;
+  const uint32_t ts = smem_addr(tile_s);
   float s0 = 0.f, sx = 0.f, sy = 0.f;
-  const int pt1 = min(R, (blockIdx.x + 1) * 64);
-  for (int pt0 = blockIdx.x * 64; pt0 < pt1; pt0 += 8) {
-    const int f = pt0 / n;
+  const int pt_begin = blockIdx.x * 64;
+  const int piece = C == 4 ? PT : 64;  // points per shared-memory piece
+  for (int q0 = pt_begin; q0 < pt_begin + 64 && q0 < R; q0 += piece) {
+    // the piece: tile q0 / PT (C = 4), or its 64-row half holding points q0 .. q0 + 63 (C = 1)
+    const uint32_t base_off = C == 4 ? 0u : (uint32_t)((q0 % PT) / 64) * kHalf;
+    const uint32_t bytes = C == 4 ? kTile : kHalf;
+    const uint4* src = reinterpret_cast<const uint4*>(gA0 + (size_t)(q0 / PT) * kTile + base_off);
+    __syncthreads();  // the previous piece has been read
+    uint4* dst = reinterpret_cast<uint4*>(tile_s);
+#pragma unroll 4
+    for (int i = threadIdx.x; i < (int)(bytes / 16); i += kW) dst[i] = src[i];
+    __syncthreads();
+    const int f = q0 / n;
     const float bk = Bf[(size_t)f * kW + j] + bj;
-    const uint8_t* tb = gA0 + (size_t)(pt0 / PT) * kTile;
-    const int p = pt0 % PT;
-    float ga[4][8];
+    for (int pt0 = q0; pt0 < q0 + piece; pt0 += 8) {
+      const int p = pt0 % PT;
+      float ga[4][8];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      if (c < C) unpack8(*reinterpret_cast<const uint4*>(tb + tile_chunk(j, (c * PT + p) >> 3)), ga[c]);
-      else
+      for (int c = 0; c < 4; ++c) {
+        if (c < C) unpack8(ld_shared_v4(ts + tile_chunk(j, (c * PT + p) >> 3) - base_off), ga[c]);
+        else
 #pragma unroll
-        for (int i = 0; i < 8; ++i) ga[c][i] = 0.f;
-    }
+          for (int i = 0; i < 8; ++i) ga[c][i] = 0.f;
+      }
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const float x = X[2 * (size_t)(pt0 + i)], y = X[2 * (size_t)(pt0 + i) + 1];
-      float a, sd;
-      tanh_sech2(fmaf(w2y, y, fmaf(w2x, x, bk)), a, sd);
-      const float td = -2.0f * a * sd;
-      const float tp = -2.0f * sd * sd + 4.0f * a * a * sd;
-      const float gz = ga[0][i] * sd + (ga[1][i] * w2x + ga[2][i] * w2y) * td + ga[3][i] * tp * lap;
-      const float gzx = fmaf(ga[1][i], sd, 2.0f * ga[3][i] * td * w2x);
-      const float gzy = fmaf(ga[2][i], sd, 2.0f * ga[3][i] * td * w2y);
-      s0 += gz;
-      sx += fmaf(gz, x, gzx);
-      sy += fmaf(gz, y, gzy);
+      for (int i = 0; i < 8; ++i) {
+        const float x = X[2 * (size_t)(pt0 + i)], y = X[2 * (size_t)(pt0 + i) + 1];
+        float a, sd;
+        tanh_sech2(fmaf(w2y, y, fmaf(w2x, x, bk)), a, sd);
+        const float td = -2.0f * a * sd;
+        const float tp = -2.0f * sd * sd + 4.0f * a * a * sd;
+        const float gz = ga[0][i] * sd + (ga[1][i] * w2x + ga[2][i] * w2y) * td + ga[3][i] * tp * lap;
+        const float gzx = fmaf(ga[1][i], sd, 2.0f * ga[3][i] * td * w2x);
+        const float gzy = fmaf(ga[2][i], sd, 2.0f * ga[3][i] * td * w2y);
+        s0 += gz;
+        sx += fmaf(gz, x, gzx);
+        sy += fmaf(gz, y, gzy);
+      }
     }
   }
   float* o = part + (size_t)blockIdx.x * 3 * kW;
@@ -994,6 +1022,35 @@ __global__ void tc_colsum_kernel(const float* __restrict__ part, int nblk, int s
 #pragma unroll
     for (int k = 0; k < 8; ++k) t += sm[k][c];
     out[j] = accumulate ? out[j] + t : t;
+  }
+}
+
+// Column sums of a tall matrix (nrows x ncols, row stride `stride`), first stage: block
+// (x, g) adds rows [g rpc, (g + 1) rpc) of columns 32x .. 32x + 31 into scratch[g][col]
+// (8 row groups per block, combined in a fixed order). The second stage is
+// tc_colsum_kernel over the G rows of scratch.
+__global__ void tc_colsum_stage1_kernel(const float* __restrict__ part, int nrows, int stride, int ncols, int rpc,
+                                        float* __restrict__ scratch) {
+  __shared__ float sm[8][32];
+  const int c = threadIdx.x & 31, r = threadIdx.x >> 5;
+  const int col = blockIdx.x * 32 + c;
+  const int r0 = blockIdx.y * rpc, r1 = min(nrows, r0 + rpc);
+  float s0 = 0.f, s1 = 0.f;
+  if (col < ncols) {
+    int b = r0 + r;
+    for (; b + 8 < r1; b += 16) {
+      s0 += part[(size_t)b * stride + col];
+      s1 += part[(size_t)(b + 8) * stride + col];
+    }
+    if (b < r1) s0 += part[(size_t)b * stride + col];
+  }
+  sm[r][c] = s0 + s1;
+  __syncthreads();
+  if (r == 0 && col < ncols) {
+    float t = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += sm[k][c];
+    scratch[(size_t)blockIdx.y * ncols + col] = t;
   }
 }
 
@@ -1046,9 +1103,9 @@ cudaError_t tc_pack_weights(const float* W, void* img, void* imgT, cudaStream_t 
 
 cudaError_t tc_first_fwd(const float* Bf, const float* W0, const float* b0, const float* X, int n, int R, int C,
                          void* A0, cudaStream_t st) {
-  const int R_pad = tc_tiles(R, C) * (kTR / C);
-  const int threads = (R_pad / 8) * kW;
-  tc_first_fwd_kernel<<<(threads + 255) / 256, 256, 0, st>>>(Bf, W0, b0, X, n, R, C, R_pad, static_cast<uint8_t*>(A0));
+  const int tiles = tc_tiles(R, C);
+  if (tiles == 0) return cudaSuccess;
+  tc_first_fwd_kernel<<<tiles, kW, 0, st>>>(Bf, W0, b0, X, n, R, C, static_cast<uint8_t*>(A0));
   return cudaGetLastError();
 }
 
@@ -1094,6 +1151,18 @@ cudaError_t tc_layer_bwd(const TcBwdParams& p, int* grid_used, cudaStream_t st) 
 
 cudaError_t tc_colsum(const float* part, int nblk, int stride, int n, float* out, int accumulate, cudaStream_t st) {
   tc_colsum_kernel<<<(n + 31) / 32, 256, 0, st>>>(part, nblk, stride, n, out, accumulate);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_colsum_tall(const float* part, int nrows, int stride, int ncols, float* scratch, int scratch_floats,
+                           float* out, int accumulate, cudaStream_t st) {
+  int groups = (nrows + 255) / 256;
+  if (groups > 64) groups = 64;
+  if (groups < 1) groups = 1;
+  if ((size_t)groups * ncols > (size_t)scratch_floats) return cudaErrorInvalidValue;
+  const int rpc = (nrows + groups - 1) / groups;
+  tc_colsum_stage1_kernel<<<dim3((ncols + 31) / 32, groups), 256, 0, st>>>(part, nrows, stride, ncols, rpc, scratch);
+  tc_colsum_kernel<<<(ncols + 31) / 32, 256, 0, st>>>(scratch, groups, ncols, ncols, out, accumulate);
   return cudaGetLastError();
 }
 

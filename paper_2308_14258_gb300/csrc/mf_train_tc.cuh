@@ -54,6 +54,10 @@ cudaError_t tc_first_bwd(const float* Bf, const float* W0, const float* b0, cons
 cudaError_t tc_layer_fwd(const TcFwdParams& p, cudaStream_t st);
 cudaError_t tc_layer_bwd(const TcBwdParams& p, int* grid_used, cudaStream_t st);
 cudaError_t tc_colsum(const float* part, int nblk, int stride, int n, float* out, int accumulate, cudaStream_t st);
+// out (+)= column sums of a tall nrows x ncols matrix in two deterministic stages, with
+// scratch (at least 64 x ncols floats) for the partial sums
+cudaError_t tc_colsum_tall(const float* part, int nrows, int stride, int ncols, float* scratch, int scratch_floats,
+                           float* out, int accumulate, cudaStream_t st);
 cudaError_t tc_sum_double(const double* part, int n, double scale, double* out, cudaStream_t st);
 cudaError_t tc_sum_float(const float* part, int n, float* out, cudaStream_t st);
 
