@@ -34,6 +34,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -569,6 +570,14 @@ mf_status run_pass_fused(mf_trainer* t, int C, int F, int n, const float* G, con
     bp.n_pts = R;
     bp.C = C;
     bp.top = l == NH ? 1 : 0;
+    // layer 1 below the top also runs the first layer's backward (no gA_0 tiles)
+    bp.first = (l == 1 && NH >= 2) ? 1 : 0;
+    bp.Bf = t->Bf;
+    bp.W0 = t->w;
+    bp.b0 = t->w + t->off_b0;
+    bp.X = X;
+    bp.n = n;
+    bp.part32 = t->part;
     bp.status = t->status;
     int grid = 0;
     TR_CUDA(mf::tc_layer_bwd(bp, &grid, st), "train: fused backward");
@@ -583,15 +592,20 @@ mf_status run_pass_fused(mf_trainer* t, int C, int F, int n, const float* G, con
     }
     cur ^= 1;
   }
-  // first layer: W2 columns and b0 from all rows, W1 through per-function sums
-  const int nblk = R / kRB;
-  TR_CUDA(mf::tc_first_bwd(t->Bf, t->w, t->w + t->off_b0, X, n, R, C, gbuf[cur], t->part, st),
-          "train: first layer backward");
+  // first layer: W2 columns and b0 from all rows, W1 through per-function sums. Partial
+  // sums per 32 points from the layer-1 backward kernel, or (one hidden layer) per 64
+  // points from the first-layer kernel on the gA_0 tiles.
+  int group = 32;
+  if (NH == 1) {
+    group = kRB;
+    TR_CUDA(mf::tc_first_bwd(t->Bf, t->w, t->w + t->off_b0, X, n, R, C, gbuf[cur], t->part, st),
+            "train: first layer backward");
+  }
   // the per-CTA g_W buffer is free again here and holds the first stage of the sums
-  TR_CUDA(mf::tc_colsum_tall(t->part, nblk, 3 * H, 3 * H, t->tc_gw, ctas * H * H, t->sums, 0, st),
+  TR_CUDA(mf::tc_colsum_tall(t->part, R / group, 3 * H, 3 * H, t->tc_gw, ctas * H * H, t->sums, 0, st),
           "train: first layer sums");
   add_w2_b0_kernel<<<1, H, 0, st>>>(t->sums, H, t->g, t->g + t->off_b0);
-  per_function_sum_kernel<<<F, H, 0, st>>>(t->part, n / kRB, H, t->S);
+  per_function_sum_kernel<<<F, H, 0, st>>>(t->part, n / group, H, t->S);
   TR_CUDA(cudaGetLastError(), "train: first layer gradients");
   TR_BLAS(gemm_boundary_grad(t, G, F), "train: boundary gradient GEMM");
   return MF_OK;
@@ -748,7 +762,9 @@ mf_status mf_create_trainer(const mf_train_desc* d, const float* weights, mf_tra
   alloc(&t->gZ, C4 * es);
   alloc((void**)&t->Bf, (size_t)t->Fmax * H * 4);
   alloc((void**)&t->S, (size_t)t->Fmax * H * 4);
-  alloc((void**)&t->part, nblk_max * 3 * H * 4 + nblk_max * 4);
+  // row-block partials (64 rows) of the GEMM engine, or per-32-point first-layer partials
+  // of the fused engine
+  alloc((void**)&t->part, std::max(nblk_max * 3 * H * 4 + nblk_max * 4, (t->Rmax / 32 + 1) * 3 * H * 4));
   alloc((void**)&t->sums, 3 * H * 4);
   alloc((void**)&t->lpart, nblk_max * 8);
   alloc((void**)&t->loss, 4 * 8);

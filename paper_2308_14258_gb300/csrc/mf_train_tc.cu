@@ -425,7 +425,7 @@ __device__ __forceinline__ float warp_sum_n(const float (&v)[N], int lane, int& 
   return cur[0];
 }
 
-template <int C, bool kTop>
+template <int C, bool kTop, bool kFirst>
 __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_constant__ TcBwdParams P) {
   constexpr int PT = kTR / C;     // points per tile
   constexpr int NP = PT / 4;      // points per epilogue thread: 8 (C = 4) or 32 (C = 1)
@@ -781,12 +781,103 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
       }
     };
 
+    // ---- epilogue 2 of layer 1 (kFirst): gA_0 of this thread's points stays on chip and
+    // goes through the first layer's backward (Eq. 8 in Taylor mode, the formulas of
+    // tc_first_bwd_kernel) into per-32-point partial sums of g_z, g_z x + g_zx and
+    // g_z y + g_zy for feature j; no gA_0 tile is written.
+    const float w2x = kFirst ? P.W0[(size_t)j * 130 + 128] : 0.f;
+    const float w2y = kFirst ? P.W0[(size_t)j * 130 + 129] : 0.f;
+    const float lap = w2x * w2x + w2y * w2y;
+    const float b0j = kFirst ? P.b0[j] : 0.f;
+    auto epi2_first = [&](int it, int t) {
+      const int pt_q = t * PT + p0;  // this thread's first point
+      const float bk = pt_q < P.n_pts ? P.Bf[(size_t)(pt_q / P.n) * kW + j] + b0j : 0.f;
+      uint32_t v[C == 4 ? 4 : 1][C == 4 ? 8 : 32];
+      if (ok) ok = wait_warp_fast(S.bar(kBD2F), (uint32_t)(it & 1), abort_flag, P.status);
+      if (ok) {
+        tc_fence_after();
+        if constexpr (C == 4) {
+#pragma unroll
+          for (int ch = 0; ch < 4; ++ch) tmem_ld8(D2 + lane_off + (uint32_t)(ch * PT + p0), v[ch]);
+        } else {
+          tmem_ld32(D2 + lane_off + (uint32_t)p0, v[0]);
+        }
+        tmem_wait_ld();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(S.bar(kBD2E));
+      }
+      float s0 = 0.f, sx = 0.f, sy = 0.f;
+      if (ok) {
+#pragma unroll
+        for (int g8 = 0; g8 < NP / 8; ++g8) {
+          const int pt0 = pt_q + 8 * g8;
+          if (pt0 >= P.n_pts) break;  // padding of the value channel's last tile
+          const float4* xp = reinterpret_cast<const float4*>(P.X + 2 * (size_t)pt0);
+          float xy[16];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float4 q4 = xp[u];
+            xy[4 * u] = q4.x; xy[4 * u + 1] = q4.y; xy[4 * u + 2] = q4.z; xy[4 * u + 3] = q4.w;
+          }
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const float x = xy[2 * i], y = xy[2 * i + 1];
+            float a, sd;
+            tanh_sech2(fmaf(w2y, y, fmaf(w2x, x, bk)), a, sd);
+            if constexpr (C == 4) {
+              const float g0 = __uint_as_float(v[0][i]), g1 = __uint_as_float(v[1][i]);
+              const float g2 = __uint_as_float(v[2][i]), g3 = __uint_as_float(v[3][i]);
+              const float td = -2.0f * a * sd;
+              const float tp = -2.0f * sd * sd + 4.0f * a * a * sd;
+              const float gz = g0 * sd + (g1 * w2x + g2 * w2y) * td + g3 * tp * lap;
+              s0 += gz;
+              sx += fmaf(gz, x, fmaf(g1, sd, 2.0f * g3 * td * w2x));
+              sy += fmaf(gz, y, fmaf(g2, sd, 2.0f * g3 * td * w2y));
+            } else {
+              const float gz = __uint_as_float(v[0][8 * g8 + i]) * sd;
+              s0 += gz;
+              sx = fmaf(gz, x, sx);
+              sy = fmaf(gz, y, sy);
+            }
+          }
+        }
+      }
+      if constexpr (C == 4) {
+        // the tile's 32 points are one group: the four point quarters are added through
+        // shared memory (the idle staging tile), alternating halves so that one barrier
+        // per tile suffices
+        float* r2 = reinterpret_cast<float*>(gen + (sOut - base)) + (it & 1) * (4 * 3 * kW);
+        r2[(pq * 3 + 0) * kW + j] = s0;
+        r2[(pq * 3 + 1) * kW + j] = sx;
+        r2[(pq * 3 + 2) * kW + j] = sy;
+        named_barrier_sync(1, kEpiB * 32);
+        if (pq == 0 && ok) {
+          float* o = P.part32 + (size_t)t * 3 * kW;
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            o[c * kW + j] = (r2[c * kW + j] + r2[(3 + c) * kW + j]) + (r2[(6 + c) * kW + j] + r2[(9 + c) * kW + j]);
+        }
+      } else {
+        // each point quarter (32 points) is one group
+        if (ok && pt_q < P.n_pts) {
+          float* o = P.part32 + (size_t)(pt_q / 32) * 3 * kW;
+          o[j] = s0;
+          o[kW + j] = sx;
+          o[2 * kW + j] = sy;
+        }
+      }
+    };
+
     // ---- epilogue 2 of tile it: the gA_{l-1} tile (row = this thread's input feature).
     // Two barriers: the store of tile it-1 has read the staging tile before anyone
     // rewrites it, and every row is written before thread 0 stores the tile. D2 is
     // released after the staging writes.
     auto epi2 = [&](int it) {
       const int t = (int)blockIdx.x + it * (int)gridDim.x;
+      if constexpr (kFirst) {
+        epi2_first(it, t);
+      } else {
       uint32_t v[C == 4 ? 4 : 1][C == 4 ? 8 : 32];
       if (ok) ok = wait_warp_fast(S.bar(kBD2F), (uint32_t)(it & 1), abort_flag, P.status);
       if (ok) {
@@ -823,6 +914,7 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
       if (e == 0 && lane == 0 && ok && !*abort_flag) {
         bulk_s2g(P.gA_out + (size_t)t * kTile, sOut, kTile);
         bulk_commit();
+      }
       }
     };
 
@@ -1127,25 +1219,33 @@ cudaError_t tc_layer_fwd(const TcFwdParams& p, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <int C, bool kTop>
+template <int C, bool kTop, bool kFirst>
 cudaError_t launch_bwd(const TcBwdParams& p, int grid, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e =
-        cudaFuncSetAttribute(tc_bwd_kernel<C, kTop>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdSmem);
+    cudaError_t e = cudaFuncSetAttribute(tc_bwd_kernel<C, kTop, kFirst>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kBwdSmem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  tc_bwd_kernel<C, kTop><<<grid, kThreadsB, kBwdSmem, st>>>(p);
+  tc_bwd_kernel<C, kTop, kFirst><<<grid, kThreadsB, kBwdSmem, st>>>(p);
   return cudaGetLastError();
+}
+
+template <int C>
+cudaError_t launch_bwd_c(const TcBwdParams& p, int grid, cudaStream_t st) {
+  if (p.top && p.first) return cudaErrorInvalidValue;  // depth 2: the first layer runs on its own
+  if (p.top) return launch_bwd<C, true, false>(p, grid, st);
+  if (p.first) return launch_bwd<C, false, true>(p, grid, st);
+  return launch_bwd<C, false, false>(p, grid, st);
 }
 
 cudaError_t tc_layer_bwd(const TcBwdParams& p, int* grid_used, cudaStream_t st) {
   const int grid = p.n_tiles > 0 ? grid_for(p.n_tiles) : 0;
   if (grid_used) *grid_used = grid;
   if (grid == 0) return cudaSuccess;
-  if (p.C == 4) return p.top ? launch_bwd<4, true>(p, grid, st) : launch_bwd<4, false>(p, grid, st);
-  if (p.C == 1) return p.top ? launch_bwd<1, true>(p, grid, st) : launch_bwd<1, false>(p, grid, st);
+  if (p.C == 4) return launch_bwd_c<4>(p, grid, st);
+  if (p.C == 1) return launch_bwd_c<1>(p, grid, st);
   return cudaErrorInvalidValue;
 }
 

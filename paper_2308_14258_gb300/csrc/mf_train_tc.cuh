@@ -38,6 +38,15 @@ struct TcBwdParams {
   int n_pts;             // points of the pass (the value channel's last tile may be padded)
   int C;
   int top;
+  // first = 1 (layer 1 below the top): the first layer's backward runs in the epilogue
+  // and gA_0 is not written; partial sums per 32 points go to part32 [n_pts / 32][3][128]
+  int first;
+  const float* Bf;       // W1 g per function [F][128]
+  const float* W0;       // first-layer weights [128][130] (W1 | W2)
+  const float* b0;       // [128]
+  const float* X;        // point coordinates [n_pts][2]
+  int n;                 // points per function
+  float* part32;
   int* status;
 };
 

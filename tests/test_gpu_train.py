@@ -258,16 +258,18 @@ def test_full_size_workload(m):
     assert e2 <= 3e-2, e2
 
 
-@pytest.mark.parametrize("F,Nc,Nb,mf", [
-    (4, 128, 128, 4),    # the paper's 6 x 128 shape, a few tiles
-    (3, 64, 64, 3),      # ragged tile counts per CTA, both passes
-    (5, 192, 128, 2),    # chunks of 2 functions
-    (1, 64, 64, 1),      # one tile per CTA
+@pytest.mark.parametrize("F,Nc,Nb,mf,depth", [
+    (4, 128, 128, 4, 6),    # the paper's 6 x 128 shape, a few tiles
+    (3, 64, 64, 3, 6),      # ragged tile counts per CTA, both passes
+    (5, 192, 128, 2, 6),    # chunks of 2 functions
+    (1, 64, 64, 1, 6),      # one tile per CTA; the value channel's only tile half padded
+    (3, 64, 192, 3, 3),     # two hidden layers: the first layer's backward in layer 1's kernel
+    (2, 128, 64, 2, 2),     # one hidden layer, top and first at once: separate first-layer kernel
 ])
-def test_fused_engine_matches_gemm_engine_and_oracle(m, F, Nc, Nb, mf):
+def test_fused_engine_matches_gemm_engine_and_oracle(m, F, Nc, Nb, mf, depth):
     """The fused tensor-core engine (BF16, width 128) against the GEMM engine on the same
     batch, and both against the FP64 oracle."""
-    width, depth = 128, 6
+    width = 128
     w = I.xavier_sdnet(I.SDNetShape(width, depth), 8, bias_scale=0.1)
     Gn, Xcn, Xbn, Ybn = batch(F, Nc, Nb, 8)
     dev = to_dev(Gn, Xcn, Xbn, Ybn)
