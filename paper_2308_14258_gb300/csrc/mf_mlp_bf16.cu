@@ -85,7 +85,9 @@ __device__ __forceinline__ uint32_t act_bf16x2(float a0, float a1) {
 // Within a phase each warp pair first writes K half 0, signals it, then K half 1, so the
 // next layer's first MMAs start before the phase ends; accumulators are therefore
 // double-buffered per slot in TMEM (layer parity picks the buffer). All waits on this
-// path spin (see wait_spin): a suspended wait wakes hundreds of cycles late.
+// path spin inline (wait_spin_inl): a suspended wait wakes hundreds of cycles late, and
+// an out-of-line call costs about as much as the wait it makes on a phase that is
+// already complete.
 
 constexpr int kSlots = 2;
 
@@ -130,7 +132,7 @@ __device__ __forceinline__ void mma_issuer(const Bf16Params& P, int s, uint32_t 
       const uint32_t acc = acc0 + (uint32_t)((m & 1) * H);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        ok = wait_spin(h == 0 ? bar_act0 : bar_act1, h == 0 ? ph0 : ph1, abort_flag, P.status);
+        ok = wait_spin_inl(h == 0 ? bar_act0 : bar_act1, h == 0 ? ph0 : ph1, abort_flag, P.status);
         if (!ok) break;
         if (h == 0) ph0 ^= 1u; else ph1 ^= 1u;
         tc_fence_after();
@@ -191,7 +193,7 @@ __device__ __forceinline__ void epilogue(const Bf16Params& P, int s, int q, int 
     const bool need = (s == 1) || (e > 0 ? slot_tile(P, k, 1) < P.n_tiles
                                          : (k > 0 && slot_tile(P, k - 1, 1) < P.n_tiles));
     if (!need) return true;
-    const bool r = wait_warp(tok_wait, tok_ph, abort_flag, P.status);
+    const bool r = wait_warp_inl(tok_wait, tok_ph, abort_flag, P.status);
     tok_ph ^= 1u;
     return r;
   };
@@ -238,7 +240,7 @@ __device__ __forceinline__ void epilogue(const Bf16Params& P, int s, int q, int 
 #pragma unroll
     for (int m = 1; m <= NH; ++m) {
       if (!ok) break;
-      ok = wait_warp(bar_acc, acc_ph, abort_flag, P.status);
+      ok = wait_warp_inl(bar_acc, acc_ph, abort_flag, P.status);
       if (!ok) break;
       acc_ph ^= 1u;
       ok = take_turn(k, m);

@@ -164,7 +164,7 @@ __device__ __forceinline__ bool wait_fast(uint32_t bar, uint32_t parity, volatil
   return wait_spin_inl(bar, parity, abort_flag, status);
 }
 __device__ __forceinline__ bool wait_warp_fast(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status) {
-  return __all_sync(0xffffffffu, wait_spin_inl(bar, parity, abort_flag, status));
+  return wait_warp_inl(bar, parity, abort_flag, status);
 }
 
 struct Smem {

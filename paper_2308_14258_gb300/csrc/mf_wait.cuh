@@ -96,6 +96,11 @@ __device__ __forceinline__ bool wait_warp(uint32_t bar, uint32_t parity, volatil
   const bool ok = wait_spin(bar, parity, abort_flag, status);
   return __all_sync(0xffffffffu, ok);
 }
+// The same with the spin inline: no call on the hot path (a phase that is already
+// complete costs one test instead of a call and return).
+__device__ __forceinline__ bool wait_warp_inl(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status) {
+  return __all_sync(0xffffffffu, wait_spin_inl(bar, parity, abort_flag, status));
+}
 
 }  // namespace
 }  // namespace mf
