@@ -112,7 +112,28 @@ __device__ __forceinline__ int slot_tile(const Bf16Params& P, int round, int slo
 
 // MMA issue for one slot (a single thread): per tile and hidden layer m, the K steps of
 // K half 0 once that half of the activations is written, then K half 1, then one commit.
-template <int H, int NH>
+constexpr bool kGeluInlineIssue = false;
+constexpr bool kGeluInlineEpi = false;
+
+// How the hand-off waits are compiled, per activation (measured): inline spins for tanh;
+// for GELU, whose longer epilogue the inline spins slow down, the two constants above.
+template <int ACT>
+struct HotWaits {
+  static constexpr bool kIssue = ACT == kActTanh ? true : kGeluInlineIssue;
+  static constexpr bool kEpi = ACT == kActTanh ? true : kGeluInlineEpi;
+};
+template <bool kInline>
+__device__ __forceinline__ bool hot_spin(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status) {
+  if constexpr (kInline) return wait_spin_inl(bar, parity, abort_flag, status);
+  else return wait_spin(bar, parity, abort_flag, status);
+}
+template <bool kInline>
+__device__ __forceinline__ bool hot_wait_warp(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status) {
+  if constexpr (kInline) return wait_warp_inl(bar, parity, abort_flag, status);
+  else return wait_warp(bar, parity, abort_flag, status);
+}
+
+template <int H, int NH, int ACT>
 __device__ __forceinline__ void mma_issuer(const Bf16Params& P, int s, uint32_t tmem, uint32_t sA, uint32_t sW,
                                            uint32_t bar_act0, uint32_t bar_act1, uint32_t bar_acc,
                                            volatile int* abort_flag) {
@@ -132,7 +153,7 @@ __device__ __forceinline__ void mma_issuer(const Bf16Params& P, int s, uint32_t 
       const uint32_t acc = acc0 + (uint32_t)((m & 1) * H);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        ok = wait_spin_inl(h == 0 ? bar_act0 : bar_act1, h == 0 ? ph0 : ph1, abort_flag, P.status);
+        ok = hot_spin<HotWaits<ACT>::kIssue>(h == 0 ? bar_act0 : bar_act1, h == 0 ? ph0 : ph1, abort_flag, P.status);
         if (!ok) break;
         if (h == 0) ph0 ^= 1u; else ph1 ^= 1u;
         tc_fence_after();
@@ -193,7 +214,7 @@ __device__ __forceinline__ void epilogue(const Bf16Params& P, int s, int q, int 
     const bool need = (s == 1) || (e > 0 ? slot_tile(P, k, 1) < P.n_tiles
                                          : (k > 0 && slot_tile(P, k - 1, 1) < P.n_tiles));
     if (!need) return true;
-    const bool r = wait_warp_inl(tok_wait, tok_ph, abort_flag, P.status);
+    const bool r = hot_wait_warp<HotWaits<ACT>::kEpi>(tok_wait, tok_ph, abort_flag, P.status);
     tok_ph ^= 1u;
     return r;
   };
@@ -240,7 +261,7 @@ __device__ __forceinline__ void epilogue(const Bf16Params& P, int s, int q, int 
 #pragma unroll
     for (int m = 1; m <= NH; ++m) {
       if (!ok) break;
-      ok = wait_warp_inl(bar_acc, acc_ph, abort_flag, P.status);
+      ok = hot_wait_warp<HotWaits<ACT>::kEpi>(bar_acc, acc_ph, abort_flag, P.status);
       if (!ok) break;
       acc_ph ^= 1u;
       ok = take_turn(k, m);
@@ -341,7 +362,7 @@ __global__ void __launch_bounds__(kThreadsBf16, 1) mlp_bf16_kernel(const __grid_
           bulk_g2s(sW + (uint32_t)l * H * H * 2, P.wimg + (size_t)l * H * H * 2, H * H * 2, bar(0));
       }
       if (wait_bounded(bar(0), 0, abort_flag, P.status, true))
-        mma_issuer<H, NH>(P, s, tmem, sA, sW, bar(1 + 2 * s), bar(2 + 2 * s), bar(5 + s), abort_flag);
+        mma_issuer<H, NH, ACT>(P, s, tmem, sA, sW, bar(1 + 2 * s), bar(2 + 2 * s), bar(5 + s), abort_flag);
       // drain: every MMA this thread issued has completed before TMEM is released
       mma_commit(bar(7 + s));
       wait_bounded(bar(7 + s), 0, abort_flag, P.status, false);
