@@ -43,7 +43,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # the kernel source is unchanged (keyed by the source hash).
 NCU_TRAFFIC = {
     # ncu --set full, colour 0 of the L = 64 grid: dram__bytes_read 2.64 MB + write 0.31 MB
-    "103c7ae845fd9786": 2948608,
+    "5b9868327d21a1ea": 2950144,
 }
 
 
@@ -286,18 +286,19 @@ def measure_train(args, m, I, torch, np, stream, rank):
     for _ in range(3):
         first_loss = tr.step(*tdev, 1e-3, stream=stream)[0]
     kt = max(3, min(args.steps, 10))
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(kt):
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(kt + 1)]
+    ev[0].record(stream)
+    for i in range(kt):
         last_loss = tr.step(*tdev, 1e-3, stream=stream)[0]
-    e1.record(stream)
-    e1.synchronize()
-    t = e0.elapsed_time(e1) / 1e3
+        ev[i + 1].record(stream)
+    ev[-1].synchronize()
+    t = ev[0].elapsed_time(ev[-1]) / 1e3
+    step_ms = sorted(ev[i].elapsed_time(ev[i + 1]) for i in range(kt))
     # layer-GEMM flops: forward 2 H^2 per channel and layer, backward twice that;
     # 4 Taylor channels per collocation point, 1 channel per data point
     gemm_flop = 3 * 2 * H * H * NH * (4 * F * Nc + F * Nb)
     train = {"value": kt / t, "unit": "train steps/s", "ms_per_step": 1e3 * t / kt,
+             "step_ms_median": step_ms[kt // 2], "step_ms_max": step_ms[-1],
              "workload": f"{F} functions (8-mode harmonic, seed 3) x ({Nc} collocation + {Nb} boundary points), "
                          "SDNet 6x128 tanh, BF16, fused tensor-core layer kernels (Taylor-mode forward, "
                          "recomputing backward), LAMB",

@@ -45,35 +45,44 @@ __device__ __forceinline__ float residual5(float e, float w, float n, float s, f
   return s4 + ((e1 + e2) + (e3 + e4));
 }
 
-// Per-point work is FP32 (FP64 throughput is low on this part); every 8 points of a
-// thread are folded into FP64 accumulators, so FP64 carries the long sums.
+// Per-point work is FP32 (FP64 throughput is low on this part); a thread's points of a
+// row (up to 8 per pass) are folded into FP64 accumulators, so FP64 carries the long sums.
 __global__ void __launch_bounds__(kThreads)
 reduce_grid_kernel(const float* __restrict__ u, const float* __restrict__ prev, int nx, int ny,
                    double* __restrict__ partial, int residual) {
   double sd = 0.0, sp = 0.0, rmax = 0.0, rsq = 0.0;
   float fd = 0.f, fp = 0.f, fr = 0.f, fmx = 0.f;
-  int n = 0;
   for (int iy = blockIdx.x; iy < ny; iy += gridDim.x) {
     const float* row = u + (size_t)iy * nx;
+    const float* prow = prev ? prev + (size_t)iy * nx : nullptr;
     const bool inner_row = residual && iy > 0 && iy < ny - 1;
-    for (int ix = threadIdx.x; ix < nx; ix += kThreads) {
-      const float c = row[ix];
-      if (prev) {
-        const float p = prev[(size_t)iy * nx + ix];
-        const float d = c - p;
-        fd = fmaf(d, d, fd);
-        fp = fmaf(p, p, fp);
+    // up to 8 points of the row per thread per pass, all loads issued before use; the
+    // FP32 partial sums of a pass are folded into FP64
+    for (int ix0 = threadIdx.x; ix0 < nx; ix0 += 8 * kThreads) {
+      float c[8], pv[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int ix = ix0 + k * kThreads;
+        c[k] = ix < nx ? row[ix] : 0.f;
+        pv[k] = (prow && ix < nx) ? prow[ix] : 0.f;
       }
-      if (inner_row && ix > 0 && ix < nx - 1) {
-        const float r = residual5(row[ix + 1], row[ix - 1], row[ix + nx], row[ix - (size_t)nx], c);
-        fmx = fmaxf(fmx, fabsf(r));
-        fr = fmaf(r, r, fr);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int ix = ix0 + k * kThreads;
+        if (ix >= nx) break;
+        if (prow) {
+          const float d = c[k] - pv[k];
+          fd = fmaf(d, d, fd);
+          fp = fmaf(pv[k], pv[k], fp);
+        }
+        if (inner_row && ix > 0 && ix < nx - 1) {
+          const float r = residual5(row[ix + 1], row[ix - 1], row[ix + nx], row[ix - (size_t)nx], c[k]);
+          fmx = fmaxf(fmx, fabsf(r));
+          fr = fmaf(r, r, fr);
+        }
       }
-      if (++n == 8) {
-        sd += (double)fd; sp += (double)fp; rsq += (double)fr;
-        fd = fp = fr = 0.f;
-        n = 0;
-      }
+      sd += (double)fd; sp += (double)fp; rsq += (double)fr;
+      fd = fp = fr = 0.f;
     }
   }
   sd += (double)fd; sp += (double)fp; rsq += (double)fr;
