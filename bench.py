@@ -294,6 +294,7 @@ def measure_train(args, m, I, torch, np, stream, rank):
     ev[-1].synchronize()
     t = ev[0].elapsed_time(ev[-1]) / 1e3
     step_ms = sorted(ev[i].elapsed_time(ev[i + 1]) for i in range(kt))
+    e0, e1 = ev[0], ev[-1]  # reused below for the comparison engines
     # layer-GEMM flops: forward 2 H^2 per channel and layer, backward twice that;
     # 4 Taylor channels per collocation point, 1 channel per data point
     gemm_flop = 3 * 2 * H * H * NH * (4 * F * Nc + F * Nb)

@@ -627,14 +627,15 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
             for (int i = 0; i < 8; ++i) v[ch][i] = 0u;
         }
         float la[8], gu[8];  // top: Delta a of the points, and the gradient reaching Delta a
+        float ta[8], ts[8];  // top: tanh and sech^2 of the points, kept for the chain rule
         if (top) {
           // Delta u = w_out . Delta a over the 128 features: shuffles (warp_sum_n) and the
           // four quadrant warps of this point quarter
           float part[8];
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
-            float a, sd;
-            tanh_sech2(__uint_as_float(v[0][i]) + bj, a, sd);
+            tanh_sech2(__uint_as_float(v[0][i]) + bj, ta[i], ts[i]);
+            const float a = ta[i], sd = ts[i];
             const float zx = __uint_as_float(v[1][i]), zy = __uint_as_float(v[2][i]);
             la[i] = fmaf(-2.0f * a * sd, zx * zx + zy * zy, sd * __uint_as_float(v[3][i]));
             part[i] = wo * la[i];
@@ -670,7 +671,12 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
             for (int u = 0; u < 2; ++u) {
               const int k = i + u;
               float a, sd;
-              tanh_sech2(__uint_as_float(v[0][k]) + bj, a, sd);
+              if (top) {
+                a = ta[k];
+                sd = ts[k];
+              } else {
+                tanh_sech2(__uint_as_float(v[0][k]) + bj, a, sd);
+              }
               const float zx = __uint_as_float(v[1][k]), zy = __uint_as_float(v[2][k]), zl = __uint_as_float(v[3][k]);
               float ga[4];
               if (top) {
@@ -1146,6 +1152,37 @@ __global__ void tc_colsum_stage1_kernel(const float* __restrict__ part, int nrow
   }
 }
 
+// Column sums of several layers' partials at once: layer l = blockIdx.y has an
+// nrows x ncols matrix at part + l layer_stride, added into out + off[l]; per column the
+// same 8-row-group scheme as tc_colsum_kernel.
+struct TcLayerOffsets {
+  long long off[kTcMaxLayers];
+};
+__global__ void tc_colsum_layers_kernel(const float* __restrict__ part, size_t layer_stride, int nrows, int ncols,
+                                        float* __restrict__ out, const TcLayerOffsets offs) {
+  __shared__ float sm[8][32];
+  const int c = threadIdx.x & 31, r = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + c;
+  const float* pl = part + (size_t)blockIdx.y * layer_stride;
+  float s0 = 0.f, s1 = 0.f;
+  if (j < ncols) {
+    int b = r;
+    for (; b + 8 < nrows; b += 16) {
+      s0 += pl[(size_t)b * ncols + j];
+      s1 += pl[(size_t)(b + 8) * ncols + j];
+    }
+    if (b < nrows) s0 += pl[(size_t)b * ncols + j];
+  }
+  sm[r][c] = s0 + s1;
+  __syncthreads();
+  if (r == 0 && j < ncols) {
+    float t = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += sm[k][c];
+    out[offs.off[blockIdx.y] + j] += t;
+  }
+}
+
 // *out += scale x (sum of part[0..n)), one warp: lane l adds part[l], part[l + 32], ...,
 // then the 32 lane sums are combined by a fixed butterfly, so the result does not depend
 // on timing.
@@ -1263,6 +1300,15 @@ cudaError_t tc_colsum_tall(const float* part, int nrows, int stride, int ncols, 
   const int rpc = (nrows + groups - 1) / groups;
   tc_colsum_stage1_kernel<<<dim3((ncols + 31) / 32, groups), 256, 0, st>>>(part, nrows, stride, ncols, rpc, scratch);
   tc_colsum_kernel<<<(ncols + 31) / 32, 256, 0, st>>>(scratch, groups, ncols, ncols, out, accumulate);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_colsum_layers(const float* part, int n_layers, size_t layer_stride, int nrows, int ncols, float* out,
+                             const long long* out_off, cudaStream_t st) {
+  if (n_layers < 1 || n_layers > kTcMaxLayers) return cudaErrorInvalidValue;
+  TcLayerOffsets o{};
+  for (int l = 0; l < n_layers; ++l) o.off[l] = out_off[l];
+  tc_colsum_layers_kernel<<<dim3((ncols + 31) / 32, n_layers), 256, 0, st>>>(part, layer_stride, nrows, ncols, out, o);
   return cudaGetLastError();
 }
 
