@@ -36,11 +36,12 @@
 // layer gives those rows a zero residual, so their g_Z, gA and g_W contributions are 0.
 //
 // Roles per CTA (persistent, one CTA per SM, static tile schedule t = CTA + i x CTAs):
-// warp 0 lane 0 issues the MMAs, warp 1 lane 0 issues the bulk loads, the other warps are
-// the epilogue (feature quadrant q = w mod 4, the TMEM lanes warp w may read). Every wait
-// is bounded (mf_wait.cuh); after an abort the epilogue warps keep stepping through their
-// loop without work, so that every named barrier is reached by every warp, and the CTA
-// drains its MMAs and bulk copies before it frees TMEM and exits.
+// warp 0 lane 0 issues the MMAs, warp 1 lane 0 issues the bulk loads, and the epilogue
+// warps (warps 2-9 of the forward kernel, 4-19 of the backward kernel) each own the
+// feature quadrant q = w mod 4, the TMEM lanes warp w may read. Every wait is bounded
+// (mf_wait.cuh); after an abort the epilogue warps keep stepping through their loop
+// without work, so that every named barrier is reached by every warp, and the CTA drains
+// its MMAs and bulk copies before it frees TMEM and exits.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -798,6 +799,16 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
     auto epi2_first = [&](int it, int t) {
       const int pt_q = t * PT + p0;  // this thread's first point
       const float bk = pt_q < P.n_pts ? P.Bf[(size_t)(pt_q / P.n) * kW + j] + b0j : 0.f;
+      // the 8 points' coordinates (four channels) are loaded before the wait on D2
+      float xy4[C == 4 ? 16 : 1];
+      if constexpr (C == 4) {
+        const float4* xp = reinterpret_cast<const float4*>(P.X + 2 * (size_t)pt_q);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float4 q4 = xp[u];
+          xy4[4 * u] = q4.x; xy4[4 * u + 1] = q4.y; xy4[4 * u + 2] = q4.z; xy4[4 * u + 3] = q4.w;
+        }
+      }
       uint32_t v[C == 4 ? 4 : 1][C == 4 ? 8 : 32];
       if (ok) ok = wait_warp_fast(S.bar(kBD2F), (uint32_t)(it & 1), abort_flag, P.status);
       if (ok) {
@@ -819,12 +830,17 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
         for (int g8 = 0; g8 < NP / 8; ++g8) {
           const int pt0 = pt_q + 8 * g8;
           if (pt0 >= P.n_pts) break;  // padding of the value channel's last tile
-          const float4* xp = reinterpret_cast<const float4*>(P.X + 2 * (size_t)pt0);
           float xy[16];
+          if constexpr (C == 4) {
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const float4 q4 = xp[u];
-            xy[4 * u] = q4.x; xy[4 * u + 1] = q4.y; xy[4 * u + 2] = q4.z; xy[4 * u + 3] = q4.w;
+            for (int u = 0; u < 16; ++u) xy[u] = xy4[u];
+          } else {
+            const float4* xp = reinterpret_cast<const float4*>(P.X + 2 * (size_t)pt0);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const float4 q4 = xp[u];
+              xy[4 * u] = q4.x; xy[4 * u + 1] = q4.y; xy[4 * u + 2] = q4.z; xy[4 * u + 3] = q4.w;
+            }
           }
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
