@@ -379,8 +379,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1) tc_fwd_kernel(const __grid_cons
 // A operands of MMAs 1 and 2 from tensor memory. Barriers: 1..3 a_full[slot];
 // 4..6 a_empty[slot] (MMA 3 done); 7, 8 g_full[slot]; 9, 10 g_empty[slot] (16 warps);
 // 11 d1_full; 12 d1_empty; 13 gz_full; 14 gz_empty (MMA 3 done); 15 d2_full (MMA 2 done);
-// 16 d2_empty; 17 d3_done; 18 drain. Each barrier is waited on before it can complete
-// again.
+// 16 d2_empty; 17 d3_done; 18 drain; 19 gz_empty of the second g_Z^T buffer. The top
+// layer, which loads no gA tiles, keeps two g_Z^T buffers (the second in gA slot 1), so
+// that epilogue 1 of tile t need not wait for MMA 3 of tile t-1. Each barrier is waited
+// on before it can complete again.
 constexpr int kEpiB = 16;
 constexpr int kEpiWarp0 = 4;                        // first epilogue warp
 constexpr int kThreadsB = (kEpiWarp0 + kEpiB) * 32;  // 640
@@ -392,10 +394,10 @@ static_assert(128 * kRegsIssue + 32 * kEpiB * kRegsEpi <= kThreadsB * kRegsLaunc
 static_assert(32 * (kRegsIssue + 4 * kRegsEpi) <= 16384, "registers of one SM sub-partition");
 constexpr int kSlotsA = 3;
 constexpr int kSlotsG = 2;
-constexpr int kBwdBars = 19;
+constexpr int kBwdBars = 20;
 enum {
   kBAF = 1, kBAE = 4, kBGF = 7, kBGE = 9, kBD1F = 11, kBD1E = 12, kBGZF = 13, kBGZE = 14, kBD2F = 15, kBD2E = 16,
-  kBD3 = 17, kBDrain = 18
+  kBD3 = 17, kBDrain = 18, kBGZE1 = 19
 };
 
 // Sum of v[0..N-1] (N a power of 2 up to 32) over the 32 lanes of a warp: in the first log2 N
@@ -438,6 +440,10 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
   const uint32_t sG = sA + kSlotsA * kTile;              // kSlotsG tiles of gA_l
   const uint32_t sGZ = sG + kSlotsG * kTile;             // the g_Z^T tile
   const uint32_t sOut = sGZ + kTile;                     // staging tile of gA_{l-1}
+  // the g_Z^T buffer of tile `it` (two alternating buffers at the top), and the
+  // barrier its MMA 3 completes: it waits for tile it-1 (one buffer) or it-2 (two)
+  auto gz_buf = [&](int it) -> uint32_t { return (kTop && (it & 1)) ? sG + kTile : sGZ; };
+  auto gz_empty_bar = [&](int it) -> int { return (kTop && (it & 1)) ? kBGZE1 : kBGZE; };
   const uint32_t sBar = sOut + kTile;
   Smem S{sBar};
   uint8_t* genBar = gen + (sBar - base);
@@ -457,6 +463,7 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
     mbar_init(S.bar(kBD1E), kEpiB);
     mbar_init(S.bar(kBGZF), kEpiB);
     mbar_init(S.bar(kBGZE), 1);
+    mbar_init(S.bar(kBGZE1), 1);
     mbar_init(S.bar(kBD2F), 1);
     mbar_init(S.bar(kBD2E), kEpiB);
     mbar_init(S.bar(kBD3), 1);
@@ -519,12 +526,12 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
           // MMA 2: gA^T = W^T g_Z^T (g_Z^T tile read MN-major: N = rows, K = features)
   #pragma unroll
           for (int ks = 0; ks < kW / 16; ++ks) {
-            if (ks == 0) mma_ts<0>(D2, WTt + (uint32_t)(8 * ks), desc_rows(sGZ, ks), kIdescRows);
-            else mma_ts<1>(D2, WTt + (uint32_t)(8 * ks), desc_rows(sGZ, ks), kIdescRows);
+            if (ks == 0) mma_ts<0>(D2, WTt + (uint32_t)(8 * ks), desc_rows(gz_buf(it), ks), kIdescRows);
+            else mma_ts<1>(D2, WTt + (uint32_t)(8 * ks), desc_rows(gz_buf(it), ks), kIdescRows);
           }
           mma_commit(S.bar(kBD2F));
           // MMA 3: g_W += g_Z^T A (both tiles read K-major: M, N = features, K = rows)
-          const uint64_t gzd = desc_sw128(sGZ), tad = desc_sw128(ta);
+          const uint64_t gzd = desc_sw128(gz_buf(it)), tad = desc_sw128(ta);
   #pragma unroll
           for (int ks = 0; ks < kTR / 16; ++ks) {
             const uint64_t a_op = desc_add(gzd, kstep_rows(ks));
@@ -532,7 +539,7 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
             if (it == 0 && ks == 0) mma_ss<0>(D3, a_op, b_op, kIdescGW);
             else mma_ss<1>(D3, a_op, b_op, kIdescGW);
           }
-          mma_commit(S.bar(kBGZE));
+          mma_commit(S.bar(gz_empty_bar(it)));
           mma_commit(S.bar(kBAE + s));
         }
         mma_commit(S.bar(kBD3));  // every MMA issued, including the last g_W accumulation, done
@@ -591,8 +598,24 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
     // channel, C = 1 -> chunks 4 pq .. 4 pq + 3 (cc = 0..3)
     auto chunk = [&](int ch, int cc) -> int { return C == 4 ? 4 * ch + pq : 4 * pq + cc; };
     float gb = 0.f, gwo = 0.f, gbo = 0.f;
-    double lsum = 0.0;
+    // the running loss: FP32 pair with compensation (an FP64 add per tile on one lane
+    // costs hundreds of cycles and stalls its warp), turned into FP64 at the end
+    float lsum = 0.f, lcomp = 0.f;
+    auto loss_add = [&](float x) {
+      const float y = x - lcomp;
+      const float t2 = lsum + y;
+      lcomp = (t2 - lsum) - y;
+      lsum = t2;
+    };
     bool ok = true;
+
+    // MMA 3 of the tile that last used this tile's g_Z^T buffer has finished reading it
+    auto wait_gz_empty = [&](int it) -> bool {
+      const int back = kTop ? 2 : 1;
+      if (it < back) return true;
+      const int k = kTop ? (it >> 1) - 1 : it - 1;  // completion index of that barrier
+      return wait_warp_fast(S.bar(gz_empty_bar(it)), (uint32_t)(k & 1), abort_flag, P.status);
+    };
 
     // ---- epilogue 1 of tile it: g_Z from the recomputed Z and the incoming gradient
     auto epi1 = [&](int it) {
@@ -659,10 +682,10 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
             gwo = fmaf(g, la[i], gwo);
             lt = fmaf(d, d, lt);
           }
-          if (q == 0 && lane == 0 && ok) lsum += (double)lt;
+          if (ok) loss_add(lt);
         }
         // MMA 3 of tile it-1 has finished reading the g_Z^T tile this tile rewrites
-        if (ok && it > 0) ok = wait_warp_fast(S.bar(kBGZE), (uint32_t)((it - 1) & 1), abort_flag, P.status);
+        if (ok) ok = wait_gz_empty(it);
         if (ok) {
           uint32_t w[4][4];
 #pragma unroll
@@ -701,7 +724,7 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
           }
 #pragma unroll
           for (int ch = 0; ch < 4; ++ch)
-            st_shared_v4(sGZ + tile_chunk(j, 4 * ch + pq), w[ch][0], w[ch][1], w[ch][2], w[ch][3]);
+            st_shared_v4(gz_buf(it) + tile_chunk(j, 4 * ch + pq), w[ch][0], w[ch][1], w[ch][2], w[ch][3]);
         }
       } else {
         // value channel: 32 points per thread in groups of 8, each group read from D1 (and
@@ -728,7 +751,7 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
           }
           named_barrier_sync(2 + pq, 128);
         }
-        if (ok && it > 0) ok = wait_warp_fast(S.bar(kBGZE), (uint32_t)((it - 1) & 1), abort_flag, P.status);
+        if (ok) ok = wait_gz_empty(it);
         const float bo = top ? *P.bout : 0.f;
         float lt = 0.f, gt = 0.f;  // top: the tile's squared residuals and their gradients
 #pragma unroll 1
@@ -765,11 +788,11 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
             gb += o[i];
           }
           if (ok)
-            st_shared_v4(sGZ + tile_chunk(j, 4 * pq + g8), pack2(o[0], o[1]), pack2(o[2], o[3]), pack2(o[4], o[5]),
+            st_shared_v4(gz_buf(it) + tile_chunk(j, 4 * pq + g8), pack2(o[0], o[1]), pack2(o[2], o[3]), pack2(o[4], o[5]),
                          pack2(o[6], o[7]));
         }
-        if (top && q == 0 && lane == 0 && ok) {
-          lsum += (double)lt;
+        if (top && ok) {
+          loss_add(lt);
           gbo += gt;
         }
         if (ok) {
@@ -968,7 +991,7 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
     if (top) {
       P.gwout_part[((size_t)blockIdx.x * 4 + pq) * kW + j] = ok ? gwo : 0.f;
       if (q == 0 && lane == 0) {
-        P.loss_part[blockIdx.x * 4 + pq] = ok ? lsum : 0.0;
+        P.loss_part[blockIdx.x * 4 + pq] = ok ? (double)lsum - (double)lcomp : 0.0;
         P.gbout_part[blockIdx.x * 4 + pq] = ok ? gbo : 0.f;
       }
     }
