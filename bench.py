@@ -105,6 +105,11 @@ def barrier(world: int):
         dist.barrier()
 
 
+def aggregate_rate(units_per_rank: float, local_seconds: float, world: int) -> float:
+    """Whole-job rate of N replicas: all ranks' units over the slowest rank's time."""
+    return world * units_per_rank / max_over_ranks(local_seconds, world)
+
+
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
@@ -418,8 +423,8 @@ def main():
     torch.cuda.synchronize()
     clocks = sampler.stop()
     barrier(world)
-    total_s = max_over_ranks(sum(ms) / 1e3, world)
-    value = world * evals_per_sweep * args.steps / total_s
+    value = aggregate_rate(evals_per_sweep * args.steps, sum(ms) / 1e3, world)
+    total_s = world * evals_per_sweep * args.steps / value
 
     # FP32 path on the same workload (fewer steps: ~13x slower)
     k32 = max(2, args.steps // 8) if args.fp32_steps < 0 else args.fp32_steps
@@ -508,8 +513,7 @@ def main():
         grid.sweep(net, 1, "M", "bf16", stream=stream)
         grid.download(host_out, stream=stream, sync=True)
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
-    e2e_s = max_over_ranks(sum(e2e_ms) / 1e3, world)
-    e2e_value = world * evals_per_sweep * k_e2e / e2e_s
+    e2e_value = aggregate_rate(evals_per_sweep * k_e2e, sum(e2e_ms) / 1e3, world)
     nbytes = grid.nx * grid.ny * 4
 
     # accuracy of this run's BF16 sweep against the FP64 oracle on sampled subdomains

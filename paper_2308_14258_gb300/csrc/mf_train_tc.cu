@@ -684,7 +684,7 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
           }
           if (ok) loss_add(lt);
         }
-        // MMA 3 of tile it-1 has finished reading the g_Z^T tile this tile rewrites
+        // the g_Z^T buffer this tile rewrites is free again
         if (ok) ok = wait_gz_empty(it);
         if (ok) {
           uint32_t w[4][4];
