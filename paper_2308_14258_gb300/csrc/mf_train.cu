@@ -390,8 +390,10 @@ struct mf_trainer {
   // fused engine
   bool fused = false;
   void* timg = nullptr;            // [NH] x (W image, W^T image), BF16 swizzled
-  float* tc_gw = nullptr;          // [CTAs][H][H] per-CTA g_W
-  float* tc_small = nullptr;       // per-CTA g_b [CTAs][2][H], g_wout [CTAs][2][H], g_bout [CTAs][2]
+  float* tc_gw = nullptr;          // [NH][CTAs][H][H] per-layer, per-CTA g_W
+  float* tc_gb = nullptr;          // [NH][CTAs][4][H] per-layer, per-CTA g_b
+  float* tc_scratch = nullptr;     // [64][3 H] first stage of the first-layer sums
+  float* tc_small = nullptr;       // per-CTA g_wout [CTAs][4][H], g_bout [CTAs][4]
   double* tc_loss = nullptr;       // [CTAs][2]
   int* status = nullptr;           // device status word of the fused kernels
   int* h_status = nullptr;         // pinned mirror
@@ -537,9 +539,10 @@ mf_status run_pass_fused(mf_trainer* t, int C, int F, int n, const float* G, con
   const size_t img = mf::tc_image_bytes();
   auto wimg = [&](int l) { return static_cast<const char*>(t->timg) + (size_t)(l - 1) * 2 * img; };
   const int ctas = mf::tc_partial_ctas(), pg = mf::tc_partial_groups();
-  float* gbp = t->tc_small;
-  float* gwop = gbp + (size_t)ctas * pg * H;
+  float* gwop = t->tc_small;
   float* gbop = gwop + (size_t)ctas * pg * H;
+  const size_t gw_stride = (size_t)ctas * H * H, gb_stride = (size_t)ctas * pg * H;
+  int grid_used = 0;
   TR_BLAS(gemm_boundary(t, G, F), "train: boundary GEMM");
   TR_CUDA(mf::tc_first_fwd(t->Bf, t->w, t->w + t->off_b0, X, n, R, C, t->A[0], st), "train: first layer");
   for (int l = 1; l < NH; ++l) {
@@ -557,8 +560,8 @@ mf_status run_pass_fused(mf_trainer* t, int C, int F, int n, const float* G, con
     bp.wimg = wimg(l);
     bp.wimgT = wimg(l) + img;
     bp.bias = t->w + t->offb[l];
-    bp.gW_part = t->tc_gw;
-    bp.gb_part = gbp;
+    bp.gW_part = t->tc_gw + (size_t)(l - 1) * gw_stride;
+    bp.gb_part = t->tc_gb + (size_t)(l - 1) * gb_stride;
     bp.wout = t->w + t->off_wout;
     bp.bout = t->w + t->off_bout;
     bp.Y = Y;
@@ -581,16 +584,23 @@ mf_status run_pass_fused(mf_trainer* t, int C, int F, int n, const float* G, con
     bp.status = t->status;
     int grid = 0;
     TR_CUDA(mf::tc_layer_bwd(bp, &grid, st), "train: fused backward");
-    if (grid > 0) {
-      TR_CUDA(mf::tc_colsum(t->tc_gw, grid, H * H, H * H, t->g + t->offW[l], 1, st), "train: g_W");
-      TR_CUDA(mf::tc_colsum(gbp, pg * grid, H, H, t->g + t->offb[l], 1, st), "train: g_b");
-      if (l == NH) {
-        TR_CUDA(mf::tc_colsum(gwop, pg * grid, H, H, t->g + t->off_wout, 1, st), "train: g_wout");
-        if (C == 1) TR_CUDA(mf::tc_sum_float(gbop, pg * grid, t->g + t->off_bout, st), "train: g_bout");
-        TR_CUDA(mf::tc_sum_double(t->tc_loss, pg * grid, lscale, loss_slot, st), "train: loss");
-      }
+    grid_used = grid;
+    if (grid > 0 && l == NH) {
+      TR_CUDA(mf::tc_colsum(gwop, pg * grid, H, H, t->g + t->off_wout, 1, st), "train: g_wout");
+      if (C == 1) TR_CUDA(mf::tc_sum_float(gbop, pg * grid, t->g + t->off_bout, st), "train: g_bout");
+      TR_CUDA(mf::tc_sum_double(t->tc_loss, pg * grid, lscale, loss_slot, st), "train: loss");
     }
     cur ^= 1;
+  }
+  // g_W and g_b of every hidden layer, from the per-layer partial sums, in two launches
+  if (grid_used > 0) {
+    long long offW[mf::kTcMaxLayers], offb[mf::kTcMaxLayers];
+    for (int l = 1; l <= NH; ++l) {
+      offW[l - 1] = (long long)t->offW[l];
+      offb[l - 1] = (long long)t->offb[l];
+    }
+    TR_CUDA(mf::tc_colsum_layers(t->tc_gw, NH, gw_stride, grid_used, H * H, t->g, offW, st), "train: g_W");
+    TR_CUDA(mf::tc_colsum_layers(t->tc_gb, NH, gb_stride, pg * grid_used, H, t->g, offb, st), "train: g_b");
   }
   // first layer: W2 columns and b0 from all rows, W1 through per-function sums. Partial
   // sums per 32 points from the layer-1 backward kernel, or (one hidden layer) per 64
@@ -601,8 +611,7 @@ mf_status run_pass_fused(mf_trainer* t, int C, int F, int n, const float* G, con
     TR_CUDA(mf::tc_first_bwd(t->Bf, t->w, t->w + t->off_b0, X, n, R, C, gbuf[cur], t->part, st),
             "train: first layer backward");
   }
-  // the per-CTA g_W buffer is free again here and holds the first stage of the sums
-  TR_CUDA(mf::tc_colsum_tall(t->part, R / group, 3 * H, 3 * H, t->tc_gw, ctas * H * H, t->sums, 0, st),
+  TR_CUDA(mf::tc_colsum_tall(t->part, R / group, 3 * H, 3 * H, t->tc_scratch, 64 * 3 * H, t->sums, 0, st),
           "train: first layer sums");
   add_w2_b0_kernel<<<1, H, 0, st>>>(t->sums, H, t->g, t->g + t->off_b0);
   per_function_sum_kernel<<<F, H, 0, st>>>(t->part, n / group, H, t->S);
@@ -674,7 +683,8 @@ mf_status mf_destroy_trainer(mf_trainer* t) {
   cudaFree(t->w); cudaFree(t->g); cudaFree(t->m); cudaFree(t->v); cudaFree(t->r);
   cudaFree(t->wq); cudaFree(t->gA); cudaFree(t->gZ); cudaFree(t->Bf); cudaFree(t->S); cudaFree(t->part); cudaFree(t->sums);
   cudaFree(t->lpart); cudaFree(t->loss); cudaFree(t->ranges);
-  cudaFree(t->timg); cudaFree(t->tc_gw); cudaFree(t->tc_small); cudaFree(t->tc_loss); cudaFree(t->status);
+  cudaFree(t->timg); cudaFree(t->tc_gw); cudaFree(t->tc_gb); cudaFree(t->tc_scratch); cudaFree(t->tc_small);
+  cudaFree(t->tc_loss); cudaFree(t->status);
   cudaFreeHost(t->h_loss); cudaFreeHost(t->h_status);
   delete t;
   return MF_OK;
@@ -752,9 +762,11 @@ mf_status mf_create_trainer(const mf_train_desc* d, const float* weights, mf_tra
   if (t->fused) {
     const size_t ctas = (size_t)mf::tc_partial_ctas();
     alloc(&t->timg, (size_t)t->NH * 2 * mf::tc_image_bytes());
-    alloc((void**)&t->tc_gw, ctas * HH * 4);
+    alloc((void**)&t->tc_gw, (size_t)t->NH * ctas * HH * 4);
+    alloc((void**)&t->tc_gb, (size_t)t->NH * ctas * mf::tc_partial_groups() * H * 4);
+    alloc((void**)&t->tc_scratch, 64 * 3 * H * 4);
     const size_t pg = (size_t)mf::tc_partial_groups();
-    alloc((void**)&t->tc_small, (ctas * pg * H * 2 + ctas * pg) * 4);
+    alloc((void**)&t->tc_small, (ctas * pg * H + ctas * pg) * 4);
     alloc((void**)&t->tc_loss, ctas * pg * 8);
   }
   alloc((void**)&t->status, sizeof(int));

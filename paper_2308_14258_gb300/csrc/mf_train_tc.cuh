@@ -5,6 +5,8 @@
 
 namespace mf {
 
+constexpr int kTcMaxLayers = 8;  // hidden layers a batched column sum handles
+
 // Forward of one hidden layer over all tiles: A_out = Taylor-mode tanh(W A_in^T + b).
 struct TcFwdParams {
   const uint8_t* A_in;   // tiles of A_{l-1} (BF16, swizzled operand layout)
@@ -63,6 +65,10 @@ cudaError_t tc_first_bwd(const float* Bf, const float* W0, const float* b0, cons
 cudaError_t tc_layer_fwd(const TcFwdParams& p, cudaStream_t st);
 cudaError_t tc_layer_bwd(const TcBwdParams& p, int* grid_used, cudaStream_t st);
 cudaError_t tc_colsum(const float* part, int nblk, int stride, int n, float* out, int accumulate, cudaStream_t st);
+// out[off[l] + j] += sum over rows of layer l's nrows x ncols partials (at part + l
+// layer_stride), for l < n_layers, in one launch
+cudaError_t tc_colsum_layers(const float* part, int n_layers, size_t layer_stride, int nrows, int ncols, float* out,
+                             const long long* out_off, cudaStream_t st);
 // out (+)= column sums of a tall nrows x ncols matrix in two deterministic stages, with
 // scratch (at least 64 x ncols floats) for the partial sums
 cudaError_t tc_colsum_tall(const float* part, int nrows, int stride, int ncols, float* scratch, int scratch_floats,
