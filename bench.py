@@ -45,6 +45,12 @@ NCU_TRAFFIC = {
     # ncu --set full, colour 0 of the L = 64 grid: dram__bytes_read 2.64 MB + write 0.31 MB
     "5b9868327d21a1ea": 2950144,
 }
+# The unit that bounds the same kernel, from the same capture: the MUFU pipe (tanh),
+# sm__pipe_xu_cycles_active of elapsed; the tanh floor is 98,304 tanh per 128-row tile
+# at 16 per clock per SM.
+NCU_MUFU_BUSY = {
+    "5b9868327d21a1ea": 0.7233,
+}
 
 
 def parse():
@@ -564,7 +570,11 @@ def main():
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "peak_source": f"{peak_src} bf16_tflops_sustained",
                      "traffic": NCU_TRAFFIC.get(h), "per_launch_ms": per_launch_ms,
-                     "flops_per_launch": flops_per_launch},
+                     "flops_per_launch": flops_per_launch,
+                     "limiter": {"unit": "MUFU (tanh.approx)", "busy_frac_ncu": NCU_MUFU_BUSY.get(h),
+                                 "tanh_per_launch": evals_per_sweep / 4.0 * 6 * 128,
+                                 "tanh_floor_ms": evals_per_sweep / 4.0 * 6 * 128 / (16 * 152 * 2.07e9) * 1e3,
+                                 "source": "profiles/mlp_bf16_L64_ncu_full.md"}},
         "clocks": clocks,
     }
     if cpu is not None:
