@@ -68,6 +68,9 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--no-variant", action="store_true")
+    ap.add_argument("--train-functions", type=int, default=1024,
+                    help="functions in the training batch (1024 = the benchmark workload; fewer only for "
+                         "profiling captures)")
     ap.add_argument("--train-only", action="store_true",
                     help="run only the training-step measurement and print its JSON object (profiling aid)")
     return ap.parse_args()
@@ -288,7 +291,7 @@ def measure_train(args, m, I, torch, np, stream, rank):
     against the FP64 oracle on sampled functions."""
     # physics-informed training step (Eq. 3, Algorithm 1): 1024 functions x (1024 collocation
     # + 128 boundary points), SDNet 6x128, BF16, LAMB; ~8 GB working set (> L2)
-    F, Nc, Nb, H, NH = 1024, 1024, 128, 128, 5
+    F, Nc, Nb, H, NH = args.train_functions, 1024, 128, 128, 5
     tb = I.training_batch(F, Nc, 3)
     tdev = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
             for a in (tb.G, tb.Xc, tb.Xb, tb.Yb)]
@@ -315,7 +318,8 @@ def measure_train(args, m, I, torch, np, stream, rank):
                          "SDNet 6x128 tanh, BF16, fused tensor-core layer kernels (Taylor-mode forward, "
                          "recomputing backward), LAMB",
              "gemm_tflop_per_step": gemm_flop / 1e12, "gemm_tflops_achieved": gemm_flop * kt / t / 1e12,
-             "loss_after_warmup": first_loss, "loss_last": last_loss, "l2": "working set ~8 GB (> L2)"}
+             "loss_after_warmup": first_loss, "loss_last": last_loss,
+             "l2": f"working set ~{8.0 * F / 1024:.1f} GB (> L2)"}
     tpeak = load_peaks()[0].get("bf16_tflops_sustained")
     train["roofline"] = {"bound": "tensor", "achieved": train["gemm_tflops_achieved"], "peak": tpeak,
                          "unit": "TFLOP/s", "frac": train["gemm_tflops_achieved"] / tpeak,
