@@ -279,11 +279,11 @@ __global__ void colsum_kernel(const float* __restrict__ part, int nblk, int stri
 // S[f][j] = sum of the first layer's g_z over function f's points, from the block
 // partials (blocks_per_f = points per function / 64; a block never spans two functions).
 __global__ void per_function_sum_kernel(const float* __restrict__ part, int blocks_per_f, int H,
-                                        float* __restrict__ S) {
+                                        float* __restrict__ S, int accumulate) {
   const int f = blockIdx.x, j = threadIdx.x;
   float s = 0.f;
   for (int b = 0; b < blocks_per_f; ++b) s += part[(size_t)(f * blocks_per_f + b) * 3 * H + j];
-  S[(size_t)f * H + j] = s;
+  S[(size_t)f * H + j] = accumulate ? S[(size_t)f * H + j] + s : s;
 }
 
 __global__ void add_w2_b0_kernel(const float* __restrict__ sums3, int H, float* __restrict__ gW0, float* __restrict__ gb0) {
@@ -522,32 +522,49 @@ mf_status run_pass(mf_trainer* t, int C, int F, int n, const float* G, const flo
   TR_CUDA(cudaGetLastError(), "train: first layer backward");
   for (int q = 0; q < 3; ++q) colsum_kernel<<<ncol, 1024, 0, st>>>(t->part + q * H, nblk, 3 * H, H, t->sums + q * H, 0);
   add_w2_b0_kernel<<<1, H, 0, st>>>(t->sums, H, t->g, t->g + t->off_b0);
-  per_function_sum_kernel<<<F, H, 0, st>>>(t->part, n / kRB, H, t->S);
+  per_function_sum_kernel<<<F, H, 0, st>>>(t->part, n / kRB, H, t->S, 0);
   TR_CUDA(cudaGetLastError(), "train: first layer gradients");
   TR_BLAS(gemm_boundary_grad(t, G, F), "train: boundary gradient GEMM");
   return MF_OK;
 }
 
-// One pass on the fused engine: the first layer into A_0 tiles, the forward kernels of
+// One chunk of functions on the fused engine, both loss terms at once: the first layer
+// into A_0 tiles (collocation tiles first, then the data tiles), the forward kernels of
 // hidden layers 1..NH-1, then the backward kernels from the top (which also forms the
-// output layer and the loss) down, and the first-layer backward from the gA_0 tiles.
-mf_status run_pass_fused(mf_trainer* t, int C, int F, int n, const float* G, const float* X, const float* Y,
-                         float gscale, double lscale, double* loss_slot, cudaStream_t st) {
+// output layer and both losses) down; layer 1's kernel also runs the first layer's
+// backward (with one hidden layer a separate kernel does, from the gA_0 tiles).
+// term index 0: collocation points (four Taylor channels), 1: data points (value channel)
+struct FusedTerm {
+  int n;                 // points per function
+  const float* X;        // coordinates of the chunk's points
+  const float* Y;        // data targets (term 1)
+  float gscale;          // 2 / (points of the term in the whole batch)
+  double lscale;         // 1 / (points of the term in the whole batch)
+  double* loss_slot;     // device accumulator of the term's loss
+};
+
+mf_status run_chunk_fused(mf_trainer* t, int F, const float* G, const FusedTerm (&term)[2], cudaStream_t st) {
   const int H = t->H, NH = t->NH;
-  const int R = F * n;
-  const int n_tiles = mf::tc_tiles(R, C);
+  const int R[2] = {F * term[0].n, F * term[1].n};
+  const int nt[2] = {mf::tc_tiles(R[0], 4), mf::tc_tiles(R[1], 1)};
+  const size_t tile = mf::tc_tile_bytes();
   const size_t img = mf::tc_image_bytes();
   auto wimg = [&](int l) { return static_cast<const char*>(t->timg) + (size_t)(l - 1) * 2 * img; };
   const int ctas = mf::tc_partial_ctas(), pg = mf::tc_partial_groups();
   float* gwop = t->tc_small;
   float* gbop = gwop + (size_t)ctas * pg * H;
   const size_t gw_stride = (size_t)ctas * H * H, gb_stride = (size_t)ctas * pg * H;
+  // per-32-point first-layer partial sums of each term, one after the other
+  float* part32[2] = {t->part, t->part + (size_t)(R[0] / 32) * 3 * H};
   int grid_used = 0;
   TR_BLAS(gemm_boundary(t, G, F), "train: boundary GEMM");
-  TR_CUDA(mf::tc_first_fwd(t->Bf, t->w, t->w + t->off_b0, X, n, R, C, t->A[0], st), "train: first layer");
+  for (int k = 0; k < 2; ++k)
+    TR_CUDA(mf::tc_first_fwd(t->Bf, t->w, t->w + t->off_b0, term[k].X, term[k].n, R[k], k == 0 ? 4 : 1,
+                             static_cast<uint8_t*>(t->A[0]) + (k == 0 ? 0 : (size_t)nt[0] * tile), st),
+            "train: first layer");
   for (int l = 1; l < NH; ++l) {
     mf::TcFwdParams fp{static_cast<const uint8_t*>(t->A[l - 1]), static_cast<uint8_t*>(t->A[l]), wimg(l),
-                       t->w + t->offb[l], n_tiles, C, t->status};
+                       t->w + t->offb[l], nt[0], nt[0] + nt[1], t->status};
     TR_CUDA(mf::tc_layer_fwd(fp, st), "train: fused forward");
   }
   uint8_t* gbuf[2] = {static_cast<uint8_t*>(t->gZ), reinterpret_cast<uint8_t*>(t->gA)};
@@ -564,31 +581,35 @@ mf_status run_pass_fused(mf_trainer* t, int C, int F, int n, const float* G, con
     bp.gb_part = t->tc_gb + (size_t)(l - 1) * gb_stride;
     bp.wout = t->w + t->off_wout;
     bp.bout = t->w + t->off_bout;
-    bp.Y = Y;
-    bp.gscale = gscale;
-    bp.loss_part = t->tc_loss;
     bp.gwout_part = gwop;
     bp.gbout_part = gbop;
-    bp.n_tiles = n_tiles;
-    bp.n_pts = R;
-    bp.C = C;
+    for (int k = 0; k < 2; ++k) {
+      bp.term[k].n_tiles = nt[k];
+      bp.term[k].n_pts = R[k];
+      bp.term[k].n_per_fn = term[k].n;
+      bp.term[k].X = term[k].X;
+      bp.term[k].Y = term[k].Y;
+      bp.term[k].gscale = term[k].gscale;
+      bp.term[k].loss_part = t->tc_loss + (size_t)k * ctas * pg;
+      bp.term[k].part32 = part32[k];
+    }
     bp.top = l == NH ? 1 : 0;
     // layer 1 below the top also runs the first layer's backward (no gA_0 tiles)
     bp.first = (l == 1 && NH >= 2) ? 1 : 0;
     bp.Bf = t->Bf;
     bp.W0 = t->w;
     bp.b0 = t->w + t->off_b0;
-    bp.X = X;
-    bp.n = n;
-    bp.part32 = t->part;
     bp.status = t->status;
     int grid = 0;
     TR_CUDA(mf::tc_layer_bwd(bp, &grid, st), "train: fused backward");
     grid_used = grid;
     if (grid > 0 && l == NH) {
       TR_CUDA(mf::tc_colsum(gwop, pg * grid, H, H, t->g + t->off_wout, 1, st), "train: g_wout");
-      if (C == 1) TR_CUDA(mf::tc_sum_float(gbop, pg * grid, t->g + t->off_bout, st), "train: g_bout");
-      TR_CUDA(mf::tc_sum_double(t->tc_loss, pg * grid, lscale, loss_slot, st), "train: loss");
+      TR_CUDA(mf::tc_sum_float(gbop, pg * grid, t->g + t->off_bout, st), "train: g_bout");
+      for (int k = 0; k < 2; ++k)
+        TR_CUDA(mf::tc_sum_double(t->tc_loss + (size_t)k * ctas * pg, pg * grid, term[k].lscale, term[k].loss_slot,
+                                  st),
+                "train: loss");
     }
     cur ^= 1;
   }
@@ -602,21 +623,42 @@ mf_status run_pass_fused(mf_trainer* t, int C, int F, int n, const float* G, con
     TR_CUDA(mf::tc_colsum_layers(t->tc_gw, NH, gw_stride, grid_used, H * H, t->g, offW, st), "train: g_W");
     TR_CUDA(mf::tc_colsum_layers(t->tc_gb, NH, gb_stride, pg * grid_used, H, t->g, offb, st), "train: g_b");
   }
-  // first layer: W2 columns and b0 from all rows, W1 through per-function sums. Partial
-  // sums per 32 points from the layer-1 backward kernel, or (one hidden layer) per 64
-  // points from the first-layer kernel on the gA_0 tiles.
-  int group = 32;
-  if (NH == 1) {
-    group = kRB;
-    TR_CUDA(mf::tc_first_bwd(t->Bf, t->w, t->w + t->off_b0, X, n, R, C, gbuf[cur], t->part, st),
-            "train: first layer backward");
+  // first layer, per term: W2 columns and b0 from all rows, W1 through per-function sums
+  // (S of both terms added, then one GEMM). Partial sums per 32 points from the layer-1
+  // kernel, or (one hidden layer) per 64 points from the first-layer kernel on gA_0.
+  for (int k = 0; k < 2; ++k) {
+    const int C = k == 0 ? 4 : 1;
+    int group = 32;
+    float* part = part32[k];
+    if (NH == 1) {
+      group = kRB;
+      part = t->part;
+      TR_CUDA(mf::tc_first_bwd(t->Bf, t->w, t->w + t->off_b0, term[k].X, term[k].n, R[k], C,
+                               gbuf[cur] + (k == 0 ? 0 : (size_t)nt[0] * tile), part, st),
+              "train: first layer backward");
+    }
+    TR_CUDA(mf::tc_colsum_tall(part, R[k] / group, 3 * H, 3 * H, t->tc_scratch, 64 * 3 * H, t->sums, 0, st),
+            "train: first layer sums");
+    add_w2_b0_kernel<<<1, H, 0, st>>>(t->sums, H, t->g, t->g + t->off_b0);
+    per_function_sum_kernel<<<F, H, 0, st>>>(part, term[k].n / group, H, t->S, k);
   }
-  TR_CUDA(mf::tc_colsum_tall(t->part, R / group, 3 * H, 3 * H, t->tc_scratch, 64 * 3 * H, t->sums, 0, st),
-          "train: first layer sums");
-  add_w2_b0_kernel<<<1, H, 0, st>>>(t->sums, H, t->g, t->g + t->off_b0);
-  per_function_sum_kernel<<<F, H, 0, st>>>(t->part, n / group, H, t->S);
   TR_CUDA(cudaGetLastError(), "train: first layer gradients");
   TR_BLAS(gemm_boundary_grad(t, G, F), "train: boundary gradient GEMM");
+  return MF_OK;
+}
+
+// Both loss terms on the fused engine, in chunks of at most max_functions functions.
+mf_status run_terms_fused(mf_trainer* t, int F, int Nc, int Nb, const float* G, const float* Xc, const float* Xb,
+                          const float* Yb, cudaStream_t st) {
+  const double nc = (double)F * Nc, nb = (double)F * Nb;
+  for (int f0 = 0; f0 < F; f0 += t->Fmax) {
+    const int fc = F - f0 < t->Fmax ? F - f0 : t->Fmax;
+    const FusedTerm term[2] = {
+        {Nc, Xc + (size_t)f0 * Nc * 2, nullptr, (float)(2.0 / nc), 1.0 / nc, t->loss + 2},
+        {Nb, Xb + (size_t)f0 * Nb * 2, Yb + (size_t)f0 * Nb, (float)(2.0 / nb), 1.0 / nb, t->loss + 1}};
+    mf_status s = run_chunk_fused(t, fc, G + (size_t)f0 * kNB, term, st);
+    if (s != MF_OK) return s;
+  }
   return MF_OK;
 }
 
@@ -629,9 +671,7 @@ mf_status run_term(mf_trainer* t, int C, int F, int n, const float* G, const flo
     const float* Gc = G + (size_t)f0 * kNB;
     const float* Xc = X + (size_t)f0 * n * 2;
     const float* Yc = Y ? Y + (size_t)f0 * n : nullptr;
-    mf_status s = t->fused
-                      ? run_pass_fused(t, C, fc, n, Gc, Xc, Yc, (float)(2.0 / npts), 1.0 / npts, loss_slot, st)
-                  : t->precision == MF_PREC_BF16
+    mf_status s = t->precision == MF_PREC_BF16
                       ? run_pass<__nv_bfloat16>(t, C, fc, n, Gc, Xc, Yc, (float)(2.0 / npts), 1.0 / npts, loss_slot, st)
                       : run_pass<float>(t, C, fc, n, Gc, Xc, Yc, (float)(2.0 / npts), 1.0 / npts, loss_slot, st);
     if (s != MF_OK) return s;
@@ -737,6 +777,9 @@ mf_status mf_create_trainer(const mf_train_desc* d, const float* weights, mf_tra
       return tfail(MF_ERR_INVALID_ARG, "mf_create_trainer: non-finite weight");
     }
   const size_t es = esize(t), C4 = 4 * t->Rmax * H;
+  // fused engine: a tile buffer holds a chunk's collocation tiles (4 channels, 32 points
+  // each) followed by its data tiles (128 points each, the last one padded)
+  const size_t fused_tile_bytes = (t->Rmax / 32 + t->Rmax / 128 + 2) * mf::tc_tile_bytes();
   const size_t nblk_max = (t->Rmax + kRB - 1) / kRB;
   cudaError_t e = cudaSuccess;
   auto alloc = [&](void** p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); };
@@ -752,7 +795,7 @@ mf_status mf_create_trainer(const mf_train_desc* d, const float* weights, mf_tra
   for (int l = 0; l <= t->NH; ++l) {
     if (t->fused) {
       // activation tiles A_0..A_{NH-1} only: pre-activations are recomputed, never stored
-      if (l < t->NH) alloc(&t->A[l], C4 * es);
+      if (l < t->NH) alloc(&t->A[l], fused_tile_bytes);
       continue;
     }
     alloc(&t->A[l], C4 * es);
@@ -767,16 +810,16 @@ mf_status mf_create_trainer(const mf_train_desc* d, const float* weights, mf_tra
     alloc((void**)&t->tc_scratch, 64 * 3 * H * 4);
     const size_t pg = (size_t)mf::tc_partial_groups();
     alloc((void**)&t->tc_small, (ctas * pg * H + ctas * pg) * 4);
-    alloc((void**)&t->tc_loss, ctas * pg * 8);
+    alloc((void**)&t->tc_loss, 2 * ctas * pg * 8);
   }
   alloc((void**)&t->status, sizeof(int));
-  alloc((void**)&t->gA, C4 * 4);
-  alloc(&t->gZ, C4 * es);
+  alloc((void**)&t->gA, std::max(C4 * 4, fused_tile_bytes));
+  alloc(&t->gZ, std::max(C4 * es, fused_tile_bytes));
   alloc((void**)&t->Bf, (size_t)t->Fmax * H * 4);
   alloc((void**)&t->S, (size_t)t->Fmax * H * 4);
   // row-block partials (64 rows) of the GEMM engine, or per-32-point first-layer partials
   // of the fused engine
-  alloc((void**)&t->part, std::max(nblk_max * 3 * H * 4 + nblk_max * 4, (t->Rmax / 32 + 1) * 3 * H * 4));
+  alloc((void**)&t->part, std::max(nblk_max * 3 * H * 4 + nblk_max * 4, (2 * t->Rmax / 32 + 2) * 3 * H * 4));
   alloc((void**)&t->sums, 3 * H * 4);
   alloc((void**)&t->lpart, nblk_max * 8);
   alloc((void**)&t->loss, 4 * 8);
@@ -857,8 +900,12 @@ mf_status mf_train_grad(mf_trainer* t, int F, int Nc, int Nb, const float* G, co
   TR_CUDA(cudaMemsetAsync(t->status, 0, sizeof(int), st), "mf_train_grad: reset status");
   // Algorithm 1, step 1: data points (value channel only); step 2: collocation points
   // (four Taylor channels); the gradients of both terms accumulate in t->g.
-  s = run_term(t, 1, F, Nb, G, Xb, Yb, t->loss + 1, st);
-  if (s == MF_OK) s = run_term(t, 4, F, Nc, G, Xc, nullptr, t->loss + 2, st);
+  if (t->fused) {
+    s = run_terms_fused(t, F, Nc, Nb, G, Xc, Xb, Yb, st);
+  } else {
+    s = run_term(t, 1, F, Nb, G, Xb, Yb, t->loss + 1, st);
+    if (s == MF_OK) s = run_term(t, 4, F, Nc, G, Xc, nullptr, t->loss + 2, st);
+  }
   if (s != MF_OK) return s;
   TR_CUDA(cudaMemcpyAsync(t->h_loss, t->loss, 3 * sizeof(double), cudaMemcpyDeviceToHost, st), "mf_train_grad: loss");
   TR_CUDA(cudaMemcpyAsync(t->h_status, t->status, sizeof(int), cudaMemcpyDeviceToHost, st), "mf_train_grad: status");

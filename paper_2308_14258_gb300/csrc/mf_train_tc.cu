@@ -45,6 +45,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "mf_internal.cuh"
 #include "mf_tc.cuh"
 #include "mf_train_tc.cuh"
@@ -218,7 +220,6 @@ __global__ void __launch_bounds__(kThreadsTc, 1) tc_fwd_kernel(const __grid_cons
   volatile int* abort_flag = reinterpret_cast<volatile int*>(gen + (sBar - base) + 8 * kFwdBars + 8);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int C = P.C;
   const int n_it = P.n_tiles > (int)blockIdx.x ? (P.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStagesF; ++s) { mbar_init(S.bar(kFInF + s), 1); mbar_init(S.bar(kFInE + s), 1); }
@@ -304,8 +305,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) tc_fwd_kernel(const __grid_cons
       if (ok) {
         tc_fence_after();
         const uint32_t acc = tmem + (uint32_t)(b * kTR) + lane_off;
-        if (C == 4) {
-          // points 16 hh .. 16 hh + 15 of the tile's 32: two groups of 8
+        if (t < P.n_tiles4) {
+          // collocation tile, points 16 hh .. 16 hh + 15 of its 32: two groups of 8
           uint32_t v0[4][8], v1[4][8];
 #pragma unroll
           for (int ch = 0; ch < 4; ++ch) {
@@ -428,10 +429,15 @@ __device__ __forceinline__ float warp_sum_n(const float (&v)[N], int lane, int& 
   return cur[0];
 }
 
-template <int C, bool kTop, bool kFirst>
+template <bool kTop, bool kFirst>
 __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_constant__ TcBwdParams P) {
-  constexpr int PT = kTR / C;     // points per tile
-  constexpr int NP = PT / 4;      // points per epilogue thread: 8 (C = 4) or 32 (C = 1)
+  // tiles 0 .. n4-1 hold collocation points (C = 4 channels, 32 points: PT = 32, 8 points
+  // per epilogue thread), the rest the value channel of data points (C = 1, PT = 128, 32
+  // per thread); the epilogue takes the form of each tile
+  using C4 = std::integral_constant<int, 4>;
+  using C1 = std::integral_constant<int, 1>;
+  const int n4 = P.term[0].n_tiles;
+  const int n_all = n4 + P.term[1].n_tiles;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_addr(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -450,12 +456,12 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(genBar + 8 * kBwdBars);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(genBar + 8 * kBwdBars + 8);
   // top layer only (no gA tiles are loaded there): the reduction scratch of the output
-  // layer, [2][4 quarters][4 quadrants][NP points], lives in the first gA slot
+  // layer, [2][4 quarters][4 quadrants][up to 32 points], lives in the first gA slot
   float* red = reinterpret_cast<float*>(gen + (sG - base));
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr bool top = kTop;
-  const int n_it = P.n_tiles > (int)blockIdx.x ? (P.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int n_it = n_all > (int)blockIdx.x ? (n_all - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kSlotsA; ++s) { mbar_init(S.bar(kBAF + s), 1); mbar_init(S.bar(kBAE + s), 1); }
     for (int s = 0; s < kSlotsG; ++s) { mbar_init(S.bar(kBGF + s), 1); mbar_init(S.bar(kBGE + s), kEpiB); }
@@ -593,19 +599,15 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
     const float bj = P.bias[j];
     const float wo = top ? P.wout[j] : 0.f;
     const uint32_t lane_off = (uint32_t)(32 * q) << 16;
-    const int p0 = pq * NP;
-    // chunk of channel ch of this thread's points: C = 4 -> one chunk (8 points) per
-    // channel, C = 1 -> chunks 4 pq .. 4 pq + 3 (cc = 0..3)
-    auto chunk = [&](int ch, int cc) -> int { return C == 4 ? 4 * ch + pq : 4 * pq + cc; };
     float gb = 0.f, gwo = 0.f, gbo = 0.f;
-    // the running loss: FP32 pair with compensation (an FP64 add per tile on one lane
-    // costs hundreds of cycles and stalls its warp), turned into FP64 at the end
-    float lsum = 0.f, lcomp = 0.f;
-    auto loss_add = [&](float x) {
-      const float y = x - lcomp;
-      const float t2 = lsum + y;
-      lcomp = (t2 - lsum) - y;
-      lsum = t2;
+    // the running loss of each term: FP32 pair with compensation (an FP64 add per tile on
+    // one lane costs hundreds of cycles and stalls its warp), turned into FP64 at the end
+    float lsum[2] = {0.f, 0.f}, lcomp[2] = {0.f, 0.f};
+    auto loss_add = [&](int term, float x) {
+      const float y = x - lcomp[term];
+      const float t2 = lsum[term] + y;
+      lcomp[term] = (t2 - lsum[term]) - y;
+      lsum[term] = t2;
     };
     bool ok = true;
 
@@ -618,11 +620,16 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
     };
 
     // ---- epilogue 1 of tile it: g_Z from the recomputed Z and the incoming gradient
-    auto epi1 = [&](int it) {
+    auto epi1_c = [&](int it, int t, auto Cc) {
+      constexpr int C = decltype(Cc)::value;
+      constexpr int PT = kTR / C;   // points per tile
+      constexpr int NP = PT / 4;    // points per epilogue thread: 8 (C = 4) or 32 (C = 1)
+      const int p0 = pq * NP;
+      const TcTerm& T = P.term[C == 4 ? 0 : 1];
+      const int tl = C == 4 ? t : t - n4;  // the tile within its term
       const int sgs = it % kSlotsG;
-      const int t = (int)blockIdx.x + it * (int)gridDim.x;
       const uint32_t sg = sG + (uint32_t)sgs * kTile;
-      float* rb = red + (it & 1) * (16 * NP);  // top: [4 quarters][4 quadrants][NP points]
+      float* rb = red + (it & 1) * (16 * 32);  // top: [4 quarters][4 quadrants][NP points]
       if (ok) ok = wait_warp_fast(S.bar(kBD1F), (uint32_t)(it & 1), abort_flag, P.status);
       if (ok && !top) ok = wait_warp_fast(S.bar(kBGF + sgs), (uint32_t)((it / kSlotsG) & 1), abort_flag, P.status);
       if (ok) tc_fence_after();
@@ -677,12 +684,12 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
           for (int i = 0; i < 8; ++i) {
             const float d = rb[(pq * 4 + 0) * NP + i] + rb[(pq * 4 + 1) * NP + i] + rb[(pq * 4 + 2) * NP + i] +
                             rb[(pq * 4 + 3) * NP + i];  // Delta u: collocation tiles are always full
-            const float g = P.gscale * d;
+            const float g = T.gscale * d;
             gu[i] = g * wo;
             gwo = fmaf(g, la[i], gwo);
             lt = fmaf(d, d, lt);
           }
-          if (ok) loss_add(lt);
+          if (ok) loss_add(0, lt);
         }
         // the g_Z^T buffer this tile rewrites is free again
         if (ok) ok = wait_gz_empty(it);
@@ -774,9 +781,9 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
               const float sum = rb[(pq * 4 + 0) * NP + k] + rb[(pq * 4 + 1) * NP + k] + rb[(pq * 4 + 2) * NP + k] +
                                 rb[(pq * 4 + 3) * NP + k];
               // u - y; the padding past the last data point has no residual
-              const int pt = t * PT + p0 + k;
-              const float d = pt < P.n_pts ? sum + bo - P.Y[pt] : 0.f;
-              const float g = P.gscale * d;
+              const int pt = tl * PT + p0 + k;
+              const float d = pt < T.n_pts ? sum + bo - T.Y[pt] : 0.f;
+              const float g = T.gscale * d;
               ga = g * wo;
               gwo = fmaf(g, a, gwo);
               lt = fmaf(d, d, lt);
@@ -792,7 +799,7 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
                          pack2(o[6], o[7]));
         }
         if (top && ok) {
-          loss_add(lt);
+          loss_add(1, lt);
           gbo += gt;
         }
         if (ok) {
@@ -811,6 +818,8 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
       }
     };
 
+    auto tile_of = [&](int it) { return (int)blockIdx.x + it * (int)gridDim.x; };
+
     // ---- epilogue 2 of layer 1 (kFirst): gA_0 of this thread's points stays on chip and
     // goes through the first layer's backward (Eq. 8 in Taylor mode, the formulas of
     // tc_first_bwd_kernel) into per-32-point partial sums of g_z, g_z x + g_zx and
@@ -819,13 +828,19 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
     const float w2y = kFirst ? P.W0[(size_t)j * 130 + 129] : 0.f;
     const float lap = w2x * w2x + w2y * w2y;
     const float b0j = kFirst ? P.b0[j] : 0.f;
-    auto epi2_first = [&](int it, int t) {
-      const int pt_q = t * PT + p0;  // this thread's first point
-      const float bk = pt_q < P.n_pts ? P.Bf[(size_t)(pt_q / P.n) * kW + j] + b0j : 0.f;
+    auto epi2_first = [&](int it, int t, auto Cc) {
+      constexpr int C = decltype(Cc)::value;
+      constexpr int PT = kTR / C;
+      constexpr int NP = PT / 4;
+      const int p0 = pq * NP;
+      const TcTerm& T = P.term[C == 4 ? 0 : 1];
+      const int tl = C == 4 ? t : t - n4;
+      const int pt_q = tl * PT + p0;  // this thread's first point
+      const float bk = pt_q < T.n_pts ? P.Bf[(size_t)(pt_q / T.n_per_fn) * kW + j] + b0j : 0.f;
       // the 8 points' coordinates (four channels) are loaded before the wait on D2
       float xy4[C == 4 ? 16 : 1];
       if constexpr (C == 4) {
-        const float4* xp = reinterpret_cast<const float4*>(P.X + 2 * (size_t)pt_q);
+        const float4* xp = reinterpret_cast<const float4*>(T.X + 2 * (size_t)pt_q);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const float4 q4 = xp[u];
@@ -852,13 +867,13 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
 #pragma unroll
         for (int g8 = 0; g8 < NP / 8; ++g8) {
           const int pt0 = pt_q + 8 * g8;
-          if (pt0 >= P.n_pts) break;  // padding of the value channel's last tile
+          if (pt0 >= T.n_pts) break;  // padding of the value channel's last tile
           float xy[16];
           if constexpr (C == 4) {
 #pragma unroll
             for (int u = 0; u < 16; ++u) xy[u] = xy4[u];
           } else {
-            const float4* xp = reinterpret_cast<const float4*>(P.X + 2 * (size_t)pt0);
+            const float4* xp = reinterpret_cast<const float4*>(T.X + 2 * (size_t)pt0);
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
               const float4 q4 = xp[u];
@@ -898,15 +913,15 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
         r2[(pq * 3 + 2) * kW + j] = sy;
         named_barrier_sync(1, kEpiB * 32);
         if (pq == 0 && ok) {
-          float* o = P.part32 + (size_t)t * 3 * kW;
+          float* o = T.part32 + (size_t)tl * 3 * kW;
 #pragma unroll
           for (int c = 0; c < 3; ++c)
             o[c * kW + j] = (r2[c * kW + j] + r2[(3 + c) * kW + j]) + (r2[(6 + c) * kW + j] + r2[(9 + c) * kW + j]);
         }
       } else {
         // each point quarter (32 points) is one group
-        if (ok && pt_q < P.n_pts) {
-          float* o = P.part32 + (size_t)(pt_q / 32) * 3 * kW;
+        if (ok && pt_q < T.n_pts) {
+          float* o = T.part32 + (size_t)(pt_q / 32) * 3 * kW;
           o[j] = s0;
           o[kW + j] = sx;
           o[2 * kW + j] = sy;
@@ -918,10 +933,16 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
     // Two barriers: the store of tile it-1 has read the staging tile before anyone
     // rewrites it, and every row is written before thread 0 stores the tile. D2 is
     // released after the staging writes.
-    auto epi2 = [&](int it) {
-      const int t = (int)blockIdx.x + it * (int)gridDim.x;
+    auto epi2_c = [&](int it, int t, auto Cc) {
+      constexpr int C = decltype(Cc)::value;
+      constexpr int PT = kTR / C;
+      constexpr int NP = PT / 4;
+      [[maybe_unused]] const int p0 = pq * NP;
+      // chunk of channel ch of this thread's points: C = 4 -> one chunk (8 points) per
+      // channel, C = 1 -> chunks 4 pq .. 4 pq + 3 (cc = 0..3)
+      auto chunk = [&](int ch, int cc) -> int { return C == 4 ? 4 * ch + pq : 4 * pq + cc; };
       if constexpr (kFirst) {
-        epi2_first(it, t);
+        epi2_first(it, t, Cc);
       } else {
       uint32_t v[C == 4 ? 4 : 1][C == 4 ? 8 : 32];
       if (ok) ok = wait_warp_fast(S.bar(kBD2F), (uint32_t)(it & 1), abort_flag, P.status);
@@ -962,11 +983,26 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
       }
       }
     };
-
-    if (n_it > 0) epi1(0);
-    for (int it = 0; it < n_it; ++it) {
-      if (it + 1 < n_it) epi1(it + 1);
-      epi2(it);
+    // Epilogue order 1(0), then per it: 1(it+1), 2(it). This CTA's collocation tiles are
+    // its iterations 0 .. k4-1, its data tiles k4 .. n_it-1; each stretch runs in a loop
+    // of its own form (one loop body holding both forms would not fit the registers), with
+    // one iteration in between that ends the first form and starts the second.
+    const int k4 = n4 > (int)blockIdx.x ? (n4 - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    if (n_it > 0) {
+      if (k4 > 0) epi1_c(0, tile_of(0), C4{});
+      else epi1_c(0, tile_of(0), C1{});
+    }
+    for (int it = 0; it + 1 < k4; ++it) {
+      epi1_c(it + 1, tile_of(it + 1), C4{});
+      epi2_c(it, tile_of(it), C4{});
+    }
+    if (k4 > 0) {
+      if (k4 < n_it) epi1_c(k4, tile_of(k4), C1{});
+      epi2_c(k4 - 1, tile_of(k4 - 1), C4{});
+    }
+    for (int it = k4; it < n_it; ++it) {
+      if (it + 1 < n_it) epi1_c(it + 1, tile_of(it + 1), C1{});
+      epi2_c(it, tile_of(it), C1{});
     }
     if (e == 0 && lane == 0) bulk_wait_all<0>();
     // per-CTA partial sums: g_W (this warp's quadrant of rows, quarter of columns), g_b,
@@ -991,7 +1027,8 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
     if (top) {
       P.gwout_part[((size_t)blockIdx.x * 4 + pq) * kW + j] = ok ? gwo : 0.f;
       if (q == 0 && lane == 0) {
-        P.loss_part[blockIdx.x * 4 + pq] = ok ? (double)lsum - (double)lcomp : 0.0;
+        if (P.term[0].loss_part) P.term[0].loss_part[blockIdx.x * 4 + pq] = ok ? (double)lsum[0] - (double)lcomp[0] : 0.0;
+        if (P.term[1].loss_part) P.term[1].loss_part[blockIdx.x * 4 + pq] = ok ? (double)lsum[1] - (double)lcomp[1] : 0.0;
         P.gbout_part[blockIdx.x * 4 + pq] = ok ? gbo : 0.f;
       }
     }
@@ -1233,11 +1270,13 @@ __global__ void tc_sum_double_kernel(const double* __restrict__ part, int n, dou
   if (threadIdx.x == 0) *out += s * scale;
 }
 
+// *out += sum of part[0..n), one warp in the same fixed order as tc_sum_double_kernel
 __global__ void tc_sum_float_kernel(const float* __restrict__ part, int n, float* __restrict__ out) {
-  if (threadIdx.x != 0) return;
   float s = 0.f;
-  for (int i = 0; i < n; ++i) s += part[i];
-  *out += s;
+  for (int i = threadIdx.x; i < n; i += 32) s += part[i];
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+  if (threadIdx.x == 0) *out += s;
 }
 
 constexpr size_t kFwdSmem = 1024 + kStagesF * kTile + 2 * kTile + 8 * kFwdBars + 16 + 64;
@@ -1295,34 +1334,28 @@ cudaError_t tc_layer_fwd(const TcFwdParams& p, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <int C, bool kTop, bool kFirst>
+template <bool kTop, bool kFirst>
 cudaError_t launch_bwd(const TcBwdParams& p, int grid, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tc_bwd_kernel<C, kTop, kFirst>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kBwdSmem);
+    cudaError_t e =
+        cudaFuncSetAttribute(tc_bwd_kernel<kTop, kFirst>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdSmem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  tc_bwd_kernel<C, kTop, kFirst><<<grid, kThreadsB, kBwdSmem, st>>>(p);
+  tc_bwd_kernel<kTop, kFirst><<<grid, kThreadsB, kBwdSmem, st>>>(p);
   return cudaGetLastError();
 }
 
-template <int C>
-cudaError_t launch_bwd_c(const TcBwdParams& p, int grid, cudaStream_t st) {
-  if (p.top && p.first) return cudaErrorInvalidValue;  // depth 2: the first layer runs on its own
-  if (p.top) return launch_bwd<C, true, false>(p, grid, st);
-  if (p.first) return launch_bwd<C, false, true>(p, grid, st);
-  return launch_bwd<C, false, false>(p, grid, st);
-}
-
 cudaError_t tc_layer_bwd(const TcBwdParams& p, int* grid_used, cudaStream_t st) {
-  const int grid = p.n_tiles > 0 ? grid_for(p.n_tiles) : 0;
+  const int n = p.term[0].n_tiles + p.term[1].n_tiles;
+  const int grid = n > 0 ? grid_for(n) : 0;
   if (grid_used) *grid_used = grid;
   if (grid == 0) return cudaSuccess;
-  if (p.C == 4) return launch_bwd_c<4>(p, grid, st);
-  if (p.C == 1) return launch_bwd_c<1>(p, grid, st);
-  return cudaErrorInvalidValue;
+  if (p.top && p.first) return cudaErrorInvalidValue;  // one hidden layer: the first layer runs on its own
+  if (p.top) return launch_bwd<true, false>(p, grid, st);
+  if (p.first) return launch_bwd<false, true>(p, grid, st);
+  return launch_bwd<false, false>(p, grid, st);
 }
 
 cudaError_t tc_colsum(const float* part, int nblk, int stride, int n, float* out, int accumulate, cudaStream_t st) {

@@ -8,22 +8,39 @@ namespace mf {
 constexpr int kTcMaxLayers = 8;  // hidden layers a batched column sum handles
 
 // Forward of one hidden layer over all tiles: A_out = Taylor-mode tanh(W A_in^T + b).
+// The collocation points' tiles (four Taylor channels) come first, then the data
+// points' tiles (value channel); one launch covers both.
 struct TcFwdParams {
   const uint8_t* A_in;   // tiles of A_{l-1} (BF16, swizzled operand layout)
   uint8_t* A_out;        // tiles of A_l
   const void* wimg;      // W_l image, K-major 128-byte swizzle, rows = output features
   const float* bias;     // b_l [128]
-  int n_tiles;
-  int C;                 // channels per point: 1 (data points) or 4 (collocation points)
+  int n_tiles4;          // collocation tiles (the first n_tiles4)
+  int n_tiles;           // all tiles
   int* status;           // device status word (bounded waits)
 };
 
+// One loss term of a backward launch: [0] the collocation points (four channels, the
+// PDE residual), [1] the data points (value channel, u - y). Its tiles follow the other
+// term's in the tile buffers (collocation first).
+struct TcTerm {
+  int n_tiles;           // tiles of the term
+  int n_pts;             // its points (the data term's last tile may be padded)
+  int n_per_fn;          // points per function
+  const float* X;        // point coordinates [n_pts][2] (first layer's backward)
+  const float* Y;        // data term: targets [n_pts]
+  float gscale;          // top: 2 / (the term's points in the whole batch)
+  double* loss_part;     // top: [CTAs][4] sums of squared residuals
+  float* part32;         // first: [n_pts / 32][3][128] first-layer partial sums
+};
+
 // Backward of one hidden layer over all tiles (top = 1: the last hidden layer, with the
-// output layer and the loss folded in).
+// output layer and the loss folded in; first = 1: layer 1 below the top, which also runs
+// the first layer's backward in the epilogue, so that gA_0 is not written).
 struct TcBwdParams {
   const uint8_t* A_in;   // tiles of A_{l-1}
   const uint8_t* gA_in;  // tiles of gA_l (unused at the top)
-  uint8_t* gA_out;       // tiles of gA_{l-1}
+  uint8_t* gA_out;       // tiles of gA_{l-1} (unused with first = 1)
   const void* wimg;      // W_l image
   const void* wimgT;     // W_l^T image
   const float* bias;     // b_l
@@ -31,24 +48,14 @@ struct TcBwdParams {
   float* gb_part;        // [CTAs][4][128] per-CTA g_b (four point quarters)
   const float* wout;     // top: w_out [128]
   const float* bout;     // top: b_out (device scalar)
-  const float* Y;        // top, data points: targets per point
-  float gscale;          // top: 2 / (points in the loss term)
-  double* loss_part;     // top: [CTAs][4] sums of squared residuals
   float* gwout_part;     // top: [CTAs][4][128]
   float* gbout_part;     // top: [CTAs][4]
-  int n_tiles;
-  int n_pts;             // points of the pass (the value channel's last tile may be padded)
-  int C;
+  TcTerm term[2];
   int top;
-  // first = 1 (layer 1 below the top): the first layer's backward runs in the epilogue
-  // and gA_0 is not written; partial sums per 32 points go to part32 [n_pts / 32][3][128]
   int first;
-  const float* Bf;       // W1 g per function [F][128]
-  const float* W0;       // first-layer weights [128][130] (W1 | W2)
-  const float* b0;       // [128]
-  const float* X;        // point coordinates [n_pts][2]
-  int n;                 // points per function
-  float* part32;
+  const float* Bf;       // first: W1 g per function [F][128]
+  const float* W0;       // first: first-layer weights [128][130] (W1 | W2)
+  const float* b0;       // first: [128]
   int* status;
 };
 
