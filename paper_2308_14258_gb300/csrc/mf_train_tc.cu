@@ -111,6 +111,18 @@ __device__ __forceinline__ void setmaxnreg_inc() {
   asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(N));
 }
 
+// dst[i] = sum over the four quadrant rows of row[q * stride + i], i = 0..3, added in the
+// order q = 0, 1, 2, 3; 16-byte shared-memory loads (the values are broadcast to the warp)
+__device__ __forceinline__ void quad_sum4(const float* row, int stride, float (&dst)[4]) {
+  float4 a = *reinterpret_cast<const float4*>(row);
+#pragma unroll
+  for (int qq = 1; qq < 4; ++qq) {
+    const float4 x = *reinterpret_cast<const float4*>(row + qq * stride);
+    a.x += x.x; a.y += x.y; a.z += x.z; a.w += x.w;
+  }
+  dst[0] = a.x; dst[1] = a.y; dst[2] = a.z; dst[3] = a.w;
+}
+
 // BF16 value i (0..7) of a 16-byte chunk, as a float
 __device__ __forceinline__ float bf16_word(const uint4& u, int i) {
   const uint32_t w = (i >> 1) == 0 ? u.x : (i >> 1) == 1 ? u.y : (i >> 1) == 2 ? u.z : u.w;
@@ -680,10 +692,13 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
           named_barrier_sync(2 + pq, 128);
           // the tile's squared residuals are summed in FP32, the running total in FP64
           float lt = 0.f;
+          float dsum4[4];
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
-            const float d = rb[(pq * 4 + 0) * NP + i] + rb[(pq * 4 + 1) * NP + i] + rb[(pq * 4 + 2) * NP + i] +
-                            rb[(pq * 4 + 3) * NP + i];  // Delta u: collocation tiles are always full
+            // Delta u of point i (collocation tiles are always full): the four quadrants'
+            // sums, read 4 points at a time with 16-byte loads, added in quadrant order
+            if ((i & 3) == 0) quad_sum4(rb + (pq * 4) * NP + i, NP, dsum4);
+            const float d = dsum4[i & 3];
             const float g = T.gscale * d;
             gu[i] = g * wo;
             gwo = fmaf(g, la[i], gwo);
