@@ -562,10 +562,21 @@ mf_status run_chunk_fused(mf_trainer* t, int F, const float* G, const FusedTerm 
     TR_CUDA(mf::tc_first_fwd(t->Bf, t->w, t->w + t->off_b0, term[k].X, term[k].n, R[k], k == 0 ? 4 : 1,
                              static_cast<uint8_t*>(t->A[0]) + (k == 0 ? 0 : (size_t)nt[0] * tile), st),
             "train: first layer");
-  for (int l = 1; l < NH; ++l) {
-    mf::TcFwdParams fp{static_cast<const uint8_t*>(t->A[l - 1]), static_cast<uint8_t*>(t->A[l]), wimg(l),
-                       t->w + t->offb[l], nt[0], nt[0] + nt[1], t->status};
-    TR_CUDA(mf::tc_layer_fwd(fp, st), "train: fused forward");
+  // hidden layers 1..NH-1 forward, two per launch where two remain (layer l's output
+  // stays on chip as layer l+1's input, besides being stored for the backward pass)
+  for (int l = 1; l < NH;) {
+    if (l + 1 < NH) {
+      mf::TcFwd2Params fp{static_cast<const uint8_t*>(t->A[l - 1]), static_cast<uint8_t*>(t->A[l]),
+                          static_cast<uint8_t*>(t->A[l + 1]), wimg(l), wimg(l + 1), t->w + t->offb[l],
+                          t->w + t->offb[l + 1], nt[0], nt[0] + nt[1], t->status};
+      TR_CUDA(mf::tc_layer_fwd2(fp, st), "train: fused two-layer forward");
+      l += 2;
+    } else {
+      mf::TcFwdParams fp{static_cast<const uint8_t*>(t->A[l - 1]), static_cast<uint8_t*>(t->A[l]), wimg(l),
+                         t->w + t->offb[l], nt[0], nt[0] + nt[1], t->status};
+      TR_CUDA(mf::tc_layer_fwd(fp, st), "train: fused forward");
+      l += 1;
+    }
   }
   uint8_t* gbuf[2] = {static_cast<uint8_t*>(t->gZ), reinterpret_cast<uint8_t*>(t->gA)};
   int cur = 0;

@@ -375,6 +375,230 @@ __global__ void __launch_bounds__(kThreadsTc, 1) tc_fwd_kernel(const __grid_cons
   }
 }
 
+// ------------------------------------------------------------------ two-layer forward kernel
+
+// Forward of two consecutive hidden layers l and l+1 in one pass over the tiles. The
+// activations A_l of a tile are written by the first epilogue stage into a shared-memory
+// tile that is both stored to HBM (the backward pass needs A_l) and read directly as the
+// B operand of layer l+1's MMA, so A_l is never read back from HBM: a pair moves 3 tiles
+// per tile of input instead of the 4 of two single-layer launches.
+// Warps: 0 MMA issuer, 1 loads, 2-9 stage a (layer l: accumulator 1 -> tile X), 10-17
+// stage b (layer l+1: accumulator 2 -> staging tile Y). TMEM: accumulator 1 double-
+// buffered [0, 256), accumulator 2 [256, 384), W_l [384, 448), W_{l+1} [448, 512).
+// Shared memory: three input slots, two X tiles, two Y tiles (224 KB).
+// Barriers: 1..3 in_full[s]; 4..6 in_empty[s]; 7, 8 acc1_full[b]; 9, 10 acc1_empty[b]
+// (8 warps); 11, 12 x_full[b] (8 warps); 13, 14 x_empty[b] (MMA 2 done); 15 acc2_full;
+// 16 acc2_empty (8 warps); 17 drain.
+constexpr int kF2Stages = 3;
+constexpr int kThreadsF2 = 18 * 32;
+constexpr int kF2Bars = 18;
+enum {
+  kF2InF = 1, kF2InE = 4, kF2A1F = 7, kF2A1E = 9, kF2XF = 11, kF2XE = 13, kF2A2F = 15, kF2A2E = 16,
+  kF2Drain = 17
+};
+
+// Taylor-mode tanh of one accumulator tile's rows owned by this thread (feature j, point
+// half hh) into a swizzled shared-memory tile, 8 points (four channels) or 8 rows (value
+// channel) at a time; returns after the accumulator has been read (the caller releases it).
+__device__ __forceinline__ void fwd_epilogue_tile(uint32_t acc, bool c4, int hh, int j, float bj, uint32_t dst) {
+  if (c4) {
+#pragma unroll 1
+    for (int g = 0; g < 2; ++g) {
+      uint32_t v[4][8];
+#pragma unroll
+      for (int ch = 0; ch < 4; ++ch) tmem_ld8(acc + (uint32_t)(ch * 32 + 16 * hh + 8 * g), v[ch]);
+      tmem_wait_ld();
+      fwd_taylor8(v, bj, dst, j, 2 * hh + g);
+    }
+  } else {
+#pragma unroll 1
+    for (int c = 0; c < 8; ++c) {
+      uint32_t v[8];
+      tmem_ld8(acc + (uint32_t)(64 * hh + 8 * c), v);
+      tmem_wait_ld();
+      float o[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        float sd;
+        tanh_sech2(__uint_as_float(v[i]) + bj, o[i], sd);
+      }
+      st_shared_v4(dst + tile_chunk(j, 8 * hh + c), pack2(o[0], o[1]), pack2(o[2], o[3]), pack2(o[4], o[5]),
+                   pack2(o[6], o[7]));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreadsF2, 1) tc_fwd2_kernel(const __grid_constant__ TcFwd2Params P) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_addr(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* gen = smem_raw + (base - raw);
+  const uint32_t sIn = base;                              // kF2Stages input tiles
+  const uint32_t sX = sIn + kF2Stages * kTile;            // 2 tiles of A_l (MMA 2 operand, stored)
+  const uint32_t sY = sX + 2 * kTile;                     // 2 staging tiles of A_{l+1}
+  const uint32_t sBar = sY + 2 * kTile;
+  Smem S{sBar};
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(gen + (sBar - base) + 8 * kF2Bars);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(gen + (sBar - base) + 8 * kF2Bars + 8);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_it = P.n_tiles > (int)blockIdx.x ? (P.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kF2Stages; ++s) { mbar_init(S.bar(kF2InF + s), 1); mbar_init(S.bar(kF2InE + s), 1); }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(S.bar(kF2A1F + b), 1);
+      mbar_init(S.bar(kF2A1E + b), 8);
+      mbar_init(S.bar(kF2XF + b), 8);
+      mbar_init(S.bar(kF2XE + b), 1);
+    }
+    mbar_init(S.bar(kF2A2F), 1);
+    mbar_init(S.bar(kF2A2E), 8);
+    mbar_init(S.bar(kF2Drain), 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(smem_addr(tmem_holder), 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+  const uint32_t A1 = tmem, A2 = tmem + 256, W1t = tmem + 384, W2t = tmem + 448;
+  if (warp >= 2) {
+    const int stage_b = warp >= 10 ? 1 : 0;
+    const int hh = ((warp - 2) >> 2) & 1;
+    const uint8_t* img = static_cast<const uint8_t*>(stage_b ? P.wimg2 : P.wimg1);
+    const uint32_t wt = stage_b ? W2t : W1t;
+    weights_to_tmem(img, wt, warp & 3, lane, 2 * hh);
+    weights_to_tmem(img, wt, warp & 3, lane, 2 * hh + 1);
+    tmem_wait_st();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+
+  if (warp == 0) {
+    if (lane == 0) {
+      bool ok = true;
+      for (int it = 0; ok && it <= n_it; ++it) {
+        if (it < n_it) {  // MMA 1 of tile it: A_l^T = W_l A_{l-1}^T
+          const int s = it % kF2Stages, b = it & 1;
+          ok = wait_fast(S.bar(kF2InF + s), (uint32_t)((it / kF2Stages) & 1), abort_flag, P.status);
+          if (ok && it >= 2) ok = wait_fast(S.bar(kF2A1E + b), (uint32_t)(((it >> 1) - 1) & 1), abort_flag, P.status);
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t tin = sIn + (uint32_t)s * kTile;
+          const uint32_t acc = A1 + (uint32_t)(b * kTR);
+#pragma unroll
+          for (int ks = 0; ks < kW / 16; ++ks) {
+            if (ks == 0) mma_ts<0>(acc, W1t + (uint32_t)(8 * ks), desc_rows(tin, ks), kIdescRows);
+            else mma_ts<1>(acc, W1t + (uint32_t)(8 * ks), desc_rows(tin, ks), kIdescRows);
+          }
+          mma_commit(S.bar(kF2A1F + b));
+          mma_commit(S.bar(kF2InE + s));
+        }
+        if (it >= 1) {  // MMA 2 of tile it-1: A_{l+1}^T = W_{l+1} A_l^T, A_l from tile X
+          const int i2 = it - 1, b2 = i2 & 1;
+          ok = wait_fast(S.bar(kF2XF + b2), (uint32_t)((i2 >> 1) & 1), abort_flag, P.status);
+          if (ok && i2 >= 1) ok = wait_fast(S.bar(kF2A2E), (uint32_t)((i2 - 1) & 1), abort_flag, P.status);
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t tx = sX + (uint32_t)b2 * kTile;
+#pragma unroll
+          for (int ks = 0; ks < kW / 16; ++ks) {
+            if (ks == 0) mma_ts<0>(A2, W2t + (uint32_t)(8 * ks), desc_rows(tx, ks), kIdescRows);
+            else mma_ts<1>(A2, W2t + (uint32_t)(8 * ks), desc_rows(tx, ks), kIdescRows);
+          }
+          mma_commit(S.bar(kF2A2F));
+          mma_commit(S.bar(kF2XE + b2));
+        }
+      }
+      mma_commit(S.bar(kF2Drain));
+      wait_bounded(S.bar(kF2Drain), 0, abort_flag, P.status, false);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int it = 0; it < n_it; ++it) {
+        const int s = it % kF2Stages;
+        if (it >= kF2Stages &&
+            !wait_bounded(S.bar(kF2InE + s), (uint32_t)(((it / kF2Stages) - 1) & 1), abort_flag, P.status, true))
+          break;
+        const int t = (int)blockIdx.x + it * (int)gridDim.x;
+        mbar_arrive_expect_tx(S.bar(kF2InF + s), kTile);
+        bulk_g2s(sIn + (uint32_t)s * kTile, P.A_in + (size_t)t * kTile, kTile, S.bar(kF2InF + s));
+        issued = it + 1;
+      }
+      for (int it = (issued > kF2Stages ? issued - kF2Stages : 0); it < issued; ++it)
+        wait_bounded(S.bar(kF2InF + it % kF2Stages), (uint32_t)((it / kF2Stages) & 1), abort_flag, P.status, false);
+    }
+    __syncwarp();
+  } else {
+    const bool stage_b = warp >= 10;
+    const int e = warp - (stage_b ? 10 : 2);  // 0..7 within the stage
+    const int q = warp & 3, hh = e >> 2;
+    const int j = 32 * q + lane;
+    const float bj = (stage_b ? P.bias2 : P.bias1)[j];
+    const uint32_t lane_off = (uint32_t)(32 * q) << 16;
+    const int named = stage_b ? 2 : 1;
+    bool ok = true;
+    for (int it = 0; it < n_it; ++it) {
+      const int b = it & 1;
+      const int t = (int)blockIdx.x + it * (int)gridDim.x;
+      const bool c4 = t < P.n_tiles4;
+      uint32_t dst;
+      if (!stage_b) {
+        if (ok) ok = wait_warp_fast(S.bar(kF2A1F + b), (uint32_t)((it >> 1) & 1), abort_flag, P.status);
+        // MMA 2 of tile it-2 has finished reading the X tile this tile rewrites
+        if (ok && it >= 2) ok = wait_warp_fast(S.bar(kF2XE + b), (uint32_t)(((it >> 1) - 1) & 1), abort_flag, P.status);
+        dst = sX + (uint32_t)b * kTile;
+        if (ok) {
+          tc_fence_after();
+          fwd_epilogue_tile(A1 + (uint32_t)(b * kTR) + lane_off, c4, hh, j, bj, dst);
+          tc_fence_before();
+          fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) {
+            mbar_arrive(S.bar(kF2A1E + b));
+            mbar_arrive(S.bar(kF2XF + b));
+          }
+        }
+      } else {
+        if (ok) ok = wait_warp_fast(S.bar(kF2A2F), (uint32_t)(it & 1), abort_flag, P.status);
+        dst = sY + (uint32_t)b * kTile;
+        if (ok) {
+          tc_fence_after();
+          fwd_epilogue_tile(A2 + lane_off, c4, hh, j, bj, dst);
+          tc_fence_before();
+          fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(S.bar(kF2A2E));
+        }
+      }
+      // one barrier per tile and stage, reached by its 8 warps, aborted or not: before it,
+      // the stage's thread 0 waits until the store of tile it-1 has read its tile, which
+      // tile it+1 rewrites
+      if (e == 0 && lane == 0) bulk_wait_read<0>();
+      named_barrier_sync(named, 8 * 32);
+      if (e == 0 && lane == 0 && ok && !*abort_flag) {
+        bulk_s2g((stage_b ? P.A_out2 : P.A_out1) + (size_t)t * kTile, dst, kTile);
+        bulk_commit();
+      }
+    }
+    if (e == 0 && lane == 0) bulk_wait_all<0>();
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
 // ------------------------------------------------------------------ backward kernel
 
 // Backward kernel: 20 warps in five warpgroups. Warpgroup 0 holds the MMA issuer (warp
@@ -1296,6 +1520,8 @@ __global__ void tc_sum_float_kernel(const float* __restrict__ part, int n, float
 
 constexpr size_t kFwdSmem = 1024 + kStagesF * kTile + 2 * kTile + 8 * kFwdBars + 16 + 64;
 constexpr size_t kBwdSmem = 1024 + (kSlotsA + kSlotsG + 2) * kTile + 8 * kBwdBars + 16 + 64;
+constexpr size_t kFwd2Smem = 1024 + (kF2Stages + 4) * kTile + 8 * kF2Bars + 16 + 64;
+static_assert(kFwd2Smem <= 232448, "two-layer forward kernel shared memory");
 static_assert(kFwdSmem <= 232448, "forward kernel shared memory");
 static_assert(kBwdSmem <= 232448, "backward kernel shared memory");
 
@@ -1334,6 +1560,18 @@ cudaError_t tc_first_fwd(const float* Bf, const float* W0, const float* b0, cons
 cudaError_t tc_first_bwd(const float* Bf, const float* W0, const float* b0, const float* X, int n, int R, int C,
                          const void* gA0, float* part, cudaStream_t st) {
   tc_first_bwd_kernel<<<(R + 63) / 64, kW, 0, st>>>(Bf, W0, b0, X, n, R, C, static_cast<const uint8_t*>(gA0), part);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_layer_fwd2(const TcFwd2Params& p, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(tc_fwd2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwd2Smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (p.n_tiles <= 0) return cudaSuccess;
+  tc_fwd2_kernel<<<grid_for(p.n_tiles), kThreadsF2, kFwd2Smem, st>>>(p);
   return cudaGetLastError();
 }
 

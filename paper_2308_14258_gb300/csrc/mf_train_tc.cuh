@@ -20,6 +20,21 @@ struct TcFwdParams {
   int* status;           // device status word (bounded waits)
 };
 
+// Forward of two consecutive hidden layers l, l+1: A_out1 = A_l, A_out2 = A_{l+1}; A_l is
+// stored but not read back (layer l+1 reads it on chip).
+struct TcFwd2Params {
+  const uint8_t* A_in;   // tiles of A_{l-1}
+  uint8_t* A_out1;       // tiles of A_l
+  uint8_t* A_out2;       // tiles of A_{l+1}
+  const void* wimg1;     // W_l image
+  const void* wimg2;     // W_{l+1} image
+  const float* bias1;    // b_l
+  const float* bias2;    // b_{l+1}
+  int n_tiles4;
+  int n_tiles;
+  int* status;
+};
+
 // One loss term of a backward launch: [0] the collocation points (four channels, the
 // PDE residual), [1] the data points (value channel, u - y). Its tiles follow the other
 // term's in the tile buffers (collocation first).
@@ -70,6 +85,7 @@ cudaError_t tc_first_fwd(const float* Bf, const float* W0, const float* b0, cons
 cudaError_t tc_first_bwd(const float* Bf, const float* W0, const float* b0, const float* X, int n, int R, int C,
                          const void* gA0, float* part, cudaStream_t st);
 cudaError_t tc_layer_fwd(const TcFwdParams& p, cudaStream_t st);
+cudaError_t tc_layer_fwd2(const TcFwd2Params& p, cudaStream_t st);
 cudaError_t tc_layer_bwd(const TcBwdParams& p, int* grid_used, cudaStream_t st);
 cudaError_t tc_colsum(const float* part, int nblk, int stride, int n, float* out, int accumulate, cudaStream_t st);
 // out[off[l] + j] += sum over rows of layer l's nrows x ncols partials (at part + l

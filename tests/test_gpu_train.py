@@ -264,6 +264,7 @@ def test_full_size_workload(m):
     (5, 192, 128, 2, 6),    # chunks of 2 functions
     (1, 64, 64, 1, 6),      # one tile per CTA; the value channel's only tile half padded
     (3, 64, 192, 3, 3),     # two hidden layers: the first layer's backward in layer 1's kernel
+    (2, 64, 128, 2, 5),     # four hidden layers: a two-layer forward launch, then a single one
     (2, 128, 64, 2, 2),     # one hidden layer, top and first at once: separate first-layer kernel
 ])
 def test_fused_engine_matches_gemm_engine_and_oracle(m, F, Nc, Nb, mf, depth):
