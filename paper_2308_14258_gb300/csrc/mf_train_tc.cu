@@ -18,8 +18,13 @@
 // as a K-major operand with N = features and K = rows (g_W = g_Z^T A). An epilogue thread
 // owns one feature and so reads and writes its rows with 16-byte accesses.
 //
-// Forward kernel (hidden layers 1..NH-1): load tile A_{l-1}; MMA into TMEM; epilogue
-// applies the Taylor-mode tanh and writes tile A_l. Pre-activations are never stored.
+// A launch covers both loss terms of a chunk: the collocation points' tiles (four
+// channels) first, then the data points' tiles (value channel); the MMAs and copies do not
+// depend on the form, the epilogues take each tile's.
+// Forward kernels (hidden layers 1..NH-1): load tile A_{l-1}; MMA into TMEM; epilogue
+// applies the Taylor-mode tanh and writes tile A_l. The two-layer kernel then uses that
+// tile, still in shared memory, as the operand of layer l+1's MMA (besides storing it).
+// Pre-activations are never stored.
 // Backward kernel (hidden layer l, top = l == NH): load A_{l-1} and (below the top) the
 // incoming gradient tile gA_l; MMA 1 recomputes Z^T; epilogue 1 forms g_z for every
 // channel (the top layer first folds the output layer and the loss in); MMA 2 gives
@@ -37,7 +42,8 @@
 //
 // Roles per CTA (persistent, one CTA per SM, static tile schedule t = CTA + i x CTAs):
 // warp 0 lane 0 issues the MMAs, warp 1 lane 0 issues the bulk loads, and the epilogue
-// warps (warps 2-9 of the forward kernel, 4-19 of the backward kernel) each own the
+// warps (warps 2-9 of the forward kernel, 2-17 in two stages of the two-layer one, 4-19
+// of the backward kernel) each own the
 // feature quadrant q = w mod 4, the TMEM lanes warp w may read. Every wait is bounded
 // (mf_wait.cuh); after an abort the epilogue warps keep stepping through their loop
 // without work, so that every named barrier is reached by every warp, and the CTA drains
