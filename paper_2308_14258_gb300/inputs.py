@@ -33,6 +33,7 @@ TAG_BC = 2
 TAG_COLLOCATION = 3
 TAG_SIDES = 4
 TAG_TEST = 5
+TAG_FAMILY = 6
 
 POINTS_PER_UNIT = 32  # grid intervals per unit length (33 points per unit subdomain side)
 
@@ -293,6 +294,39 @@ def training_batch(n_functions: int = 1024, n_colloc: int = 1024, seed: int = 3)
     Xc = Stream(seed, TAG_COLLOCATION).uniform(n_functions * n_colloc * 2).reshape(n_functions, n_colloc, 2)
     Xb = np.broadcast_to(xb, (n_functions, 128, 2)).copy()
     return TrainBatch(G=G, Xc=Xc, Xb=Xb, Yb=G.copy())
+
+
+@dataclass
+class HarmonicFamily:
+    """Random harmonic functions on the unit square with data on all four sides:
+    u = e0 + e1 x + e2 y + e3 x y + sum over sides and k = 1..K of a_k times the
+    separable solution that is sin(k pi t) on that side and 0 on the other three,
+    e.g. sin(k pi x) sinh(k pi y) / sinh(k pi) for the top side."""
+    a: np.ndarray  # (F, 4, K): sides top, bottom, right, left
+    e: np.ndarray  # (F, 4): bilinear part
+
+    def __call__(self, x, y, scale: float = 1.0) -> np.ndarray:
+        """Values (F, P) at the points (x, y) (P each) of u(x / scale, y / scale)."""
+        x = np.asarray(x, dtype=np.float64).ravel() / scale
+        y = np.asarray(y, dtype=np.float64).ravel() / scale
+        K = self.a.shape[2]
+        kp = math.pi * np.arange(1, K + 1)[:, None]
+        sh = np.sinh(kp)
+        sx, sy = np.sin(kp * x), np.sin(kp * y)
+        top, bottom = sx * np.sinh(kp * y) / sh, sx * np.sinh(kp * (1.0 - y)) / sh
+        right, left = sy * np.sinh(kp * x) / sh, sy * np.sinh(kp * (1.0 - x)) / sh
+        out = self.e[:, :1] + self.e[:, 1:2] * x + self.e[:, 2:3] * y + self.e[:, 3:4] * (x * y)
+        for side, basis in enumerate((top, bottom, right, left)):
+            out = out + self.a[:, side, :] @ basis
+        return out
+
+
+def harmonic_family(n_functions: int, seed: int, n_modes: int = 6) -> HarmonicFamily:
+    """a ~ N(0, 1) / k (smoother functions weigh more), e ~ N(0, 1/4)."""
+    st = Stream(seed, TAG_FAMILY)
+    a = st.normal(n_functions * 4 * n_modes).reshape(n_functions, 4, n_modes) / np.arange(1, n_modes + 1)
+    e = 0.5 * st.normal(n_functions * 4).reshape(n_functions, 4)
+    return HarmonicFamily(a=a, e=e)
 
 
 WORKLOADS = {"tiny": tiny, "mid": mid, "large": large, "batched": batched}

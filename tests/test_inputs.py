@@ -91,3 +91,25 @@ def test_training_batch_shapes_and_harmonic_data():
     assert np.array_equal(tb.Yb, tb.G)
     # the 8-mode field vanishes on the bottom, left and right edges of the unit square
     assert np.abs(tb.G[:, :32]).max() < 1e-12 and np.abs(tb.G[:, 96:]).max() < 1e-12
+
+
+def test_harmonic_family_sides_and_harmonicity():
+    import math
+    f = I.harmonic_family(3, 5, n_modes=4)
+    t = np.linspace(0.0, 1.0, 17)
+    k = np.arange(1, 5)[:, None]
+    sk = np.sin(math.pi * k * t)
+    # each side carries its own sine series plus the bilinear part
+    np.testing.assert_allclose(f(t, 0 * t), f.e[:, :1] + f.e[:, 1:2] * t + f.a[:, 1, :] @ sk, atol=1e-12)
+    np.testing.assert_allclose(f(t, 0 * t + 1), f.e[:, :1] + f.e[:, 2:3] + (f.e[:, 1:2] + f.e[:, 3:4]) * t
+                               + f.a[:, 0, :] @ sk, atol=1e-12)
+    np.testing.assert_allclose(f(0 * t + 1, t), f.e[:, :1] + f.e[:, 1:2] + (f.e[:, 2:3] + f.e[:, 3:4]) * t
+                               + f.a[:, 2, :] @ sk, atol=1e-12)
+    np.testing.assert_allclose(f(0 * t, t), f.e[:, :1] + f.e[:, 2:3] * t + f.a[:, 3, :] @ sk, atol=1e-12)
+    # harmonic: the 5-point Laplacian is O(h^2) at interior points
+    h = 1e-3
+    x, y = np.array([0.3, 0.71]), np.array([0.45, 0.2])
+    lap = (f(x + h, y) + f(x - h, y) + f(x, y + h) + f(x, y - h) - 4 * f(x, y)) / h**2
+    assert np.abs(lap).max() < 1e-2
+    # scaling the domain keeps the function harmonic and maps the corners
+    np.testing.assert_allclose(f(np.array([4.0]), np.array([4.0]), scale=4.0), f(np.array([1.0]), np.array([1.0])))
