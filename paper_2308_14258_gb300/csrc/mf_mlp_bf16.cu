@@ -117,6 +117,10 @@ constexpr bool kGeluInlineEpi = false;
 
 // How the hand-off waits are compiled, per activation (measured): inline spins for tanh;
 // for GELU, whose longer epilogue the inline spins slow down, the two constants above.
+// The turn-token wait of the tanh epilogue sleeps 32 ns between polls (wait_nap_inl):
+// the turn passes three quarters into a phase, so a late wake-up costs nothing, and the
+// eight waiting warps stop taking issue slots from the eight working ones (measured
+// 0.846 against 0.852 ms per launch; a suspending try_wait gave 0.867).
 template <int ACT>
 struct HotWaits {
   static constexpr bool kIssue = ACT == kActTanh ? true : kGeluInlineIssue;
@@ -214,7 +218,9 @@ __device__ __forceinline__ void epilogue(const Bf16Params& P, int s, int q, int 
     const bool need = (s == 1) || (e > 0 ? slot_tile(P, k, 1) < P.n_tiles
                                          : (k > 0 && slot_tile(P, k - 1, 1) < P.n_tiles));
     if (!need) return true;
-    const bool r = hot_wait_warp<HotWaits<ACT>::kEpi>(tok_wait, tok_ph, abort_flag, P.status);
+    bool r;
+    if constexpr (ACT == kActTanh) r = __all_sync(0xffffffffu, wait_nap_inl(tok_wait, tok_ph, abort_flag, P.status));
+    else r = hot_wait_warp<HotWaits<ACT>::kEpi>(tok_wait, tok_ph, abort_flag, P.status);
     tok_ph ^= 1u;
     return r;
   };

@@ -90,6 +90,24 @@ __device__ __noinline__ bool wait_spin(uint32_t bar, uint32_t parity, volatile i
   return wait_spin_inl(bar, parity, abort_flag, status, limit_ns);
 }
 
+// Spinning bounded wait with a short sleep between polls, for waits that are not on the
+// critical path: the waiting warps then leave the issue slots to the warps that work.
+__device__ __forceinline__ bool wait_nap_inl(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status,
+                                             unsigned long long limit_ns = kWaitLimitNs) {
+  if (mbar_test(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  while (true) {
+    __nanosleep(32);
+    if (mbar_test(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (globaltimer() - t0 > limit_ns) {
+      *abort_flag = 1;
+      atomicExch(status, kDevErrTimeout);
+      return false;
+    }
+  }
+}
+
 // Warp-uniform form: every lane waits, and the warp continues only if all lanes saw
 // the phase complete (the .sync.aligned tcgen05 loads that follow need the whole warp).
 __device__ __forceinline__ bool wait_warp(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status) {
