@@ -75,3 +75,74 @@ def test_missing_library_fails_loudly(tmp_path):
             mosaicflow.load(str(tmp_path / "nope.so"))
     finally:
         mosaicflow._lib = saved
+
+
+@needs_nvcc
+def test_every_entry_point_validates_before_gpu_work(m):
+    """Each call the header documents with MF_ERR_INVALID_ARG rejects a bad argument
+    without touching the device (this machine has none, so a call that reached CUDA
+    would report MF_ERR_CUDA instead)."""
+    lib = m.load()
+    bad = m.MF_ERR_INVALID_ARG
+    h = C.c_void_p()
+    w = np.zeros(200000, dtype=np.float32)
+    # SDNet variants: activation, embedding channels and kernel size out of range
+    ex = m.SDNetDescEx
+    assert lib.mf_load_sdnet_ex(C.byref(ex(128, 6, 7, 0, 0)), w.ctypes.data, C.byref(h)) == bad
+    assert lib.mf_load_sdnet_ex(C.byref(ex(128, 6, 1, 17, 5)), w.ctypes.data, C.byref(h)) == bad
+    assert lib.mf_load_sdnet_ex(C.byref(ex(128, 6, 1, 8, 4)), w.ctypes.data, C.byref(h)) == bad
+    assert lib.mf_load_sdnet_ex(None, w.ctypes.data, C.byref(h)) == bad
+    assert lib.mf_load_sdnet(C.byref(m.SDNetDesc(64, 4)), None, C.byref(h)) == bad
+    # batches: count, descriptor and sizes
+    descs = (m.GridDesc * 2)(m.GridDesc(2, 2), m.GridDesc(0, 2))
+    bc = np.zeros(10000)
+    assert lib.mf_create_batch(0, descs, bc.ctypes.data, C.byref(h)) == bad
+    assert lib.mf_create_batch(2, None, bc.ctypes.data, C.byref(h)) == bad
+    assert lib.mf_create_batch(2, descs, bc.ctypes.data, C.byref(h)) == bad
+    nx, ny, off = C.c_int(), C.c_int(), C.c_longlong()
+    assert lib.mf_batch_info(None, 0, C.byref(nx), C.byref(ny), C.byref(off)) == bad
+    assert lib.mf_batch_upload(None, 0, None, 0, None) == bad
+    assert lib.mf_batch_download(None, 0, None, 0, None) == bad
+    assert lib.mf_batch_sweep(None, None, None, None, None) == bad
+    assert lib.mf_batch_residual(None, 0, None, None, None) == bad
+    # single grids
+    assert lib.mf_grid_dims(None, C.byref(nx), C.byref(ny)) == bad
+    assert lib.mf_grid_download(None, None, 0, None) == bad
+    assert lib.mf_create_grid(C.byref(m.GridDesc(2, 2)), None, C.byref(h)) == bad
+    # allocation-free sweep: null grid, size limits
+    d = C.c_double()
+    assert lib.mf_sweep_noalloc(None, 2, 2, None, 0, 1, C.byref(d), None) == bad
+    u = np.zeros(65 * 65, dtype=np.float32)
+    assert lib.mf_sweep_noalloc(u.ctypes.data, 0, 2, None, 0, 1, C.byref(d), None) == bad
+    assert lib.mf_sweep_noalloc(u.ctypes.data, 33, 2, None, 0, 1, C.byref(d), None) == bad
+    # failure-detection self-test: the limit must lie in (0, 1000] ms
+    n = C.c_int()
+    assert lib.mf_check_wait_timeout(0.0, C.byref(n)) == bad
+    assert lib.mf_check_wait_timeout(2000.0, C.byref(n)) == bad
+    # trainer: options, sizes and weights
+    td = m.TrainDesc
+
+    def desc(width=128, depth=6, prec=1, opt=1, F=4, P=128, engine=0):
+        return td(width, depth, prec, opt, F, P, 0.9, 0.999, 1e-6, 0.0, engine)
+
+    from paper_2308_14258_gb300 import inputs as I
+    tw = I.xavier_sdnet(I.SDNetShape(128, 6), 0)
+    assert lib.mf_create_trainer(None, tw.ctypes.data, C.byref(h)) == bad
+    assert lib.mf_create_trainer(C.byref(desc(width=96)), tw.ctypes.data, C.byref(h)) == bad
+    assert lib.mf_create_trainer(C.byref(desc(depth=9)), tw.ctypes.data, C.byref(h)) == bad
+    assert lib.mf_create_trainer(C.byref(desc(prec=5)), tw.ctypes.data, C.byref(h)) == bad
+    assert lib.mf_create_trainer(C.byref(desc(opt=3)), tw.ctypes.data, C.byref(h)) == bad
+    assert lib.mf_create_trainer(C.byref(desc(P=100)), tw.ctypes.data, C.byref(h)) == bad
+    assert lib.mf_create_trainer(C.byref(desc(F=0)), tw.ctypes.data, C.byref(h)) == bad
+    assert lib.mf_create_trainer(C.byref(desc(F=1 << 20, P=1 << 12)), tw.ctypes.data, C.byref(h)) == bad
+    assert lib.mf_create_trainer(C.byref(desc()), None, C.byref(h)) == bad
+    wn = tw.copy()
+    wn[5] = np.nan
+    assert lib.mf_create_trainer(C.byref(desc()), wn.ctypes.data, C.byref(h)) == bad
+    assert b"finite" in lib.mf_last_error() or b"weight" in lib.mf_last_error()
+    loss = (C.c_double * 3)()
+    assert lib.mf_train_grad(None, 1, 64, 64, None, None, None, None, loss, None) == bad
+    assert lib.mf_train_step(None, 1, 64, 64, None, None, None, None, 1e-3, loss, None) == bad
+    assert lib.mf_trainer_set_weights(None, None, 0, None) == bad
+    assert lib.mf_trainer_get_weights(None, None, 0, None) == bad
+    assert lib.mf_trainer_get_grads(None, None, 0, None) == bad
