@@ -277,3 +277,50 @@ def test_centre_line_option_validation(m):
     with pytest.raises(m.MFError) as e:
         g.sweep(net, 1, "A", "fp32", query="centre")
     assert e.value.status == m.MF_ERR_INVALID_ARG
+
+
+def _coordinate_only_weights(width, depth, ax, by, c):
+    """An SDNet that ignores its boundary input: N(x, y) = tanh^depth(ax x + by y) + c."""
+    w = np.zeros(I.SDNetShape(width, depth).n_params, dtype=np.float32)
+    w[128], w[129] = ax, by
+    o = width * 130 + width
+    for _ in range(depth - 1):
+        w[o] = 1.0
+        o += width * width + width
+    w[o] = 1.0
+    w[o + width] = c
+    return w
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-6), ("bf16", 1e-2)])
+@pytest.mark.parametrize("width", [64, 128])
+def test_coordinate_only_sdnet_sweep_closed_form(m, prec, tol, width):
+    """Independent of the oracle: after one multiplicative sweep with a network that
+    ignores the boundary, every interior grid point holds N at its local coordinates in
+    the last subdomain (colour order 0..3) whose open interior holds it; the boundary
+    rows are untouched."""
+    lx, ly, depth, ax, by, c = 2, 3, 3, 1.3, -0.7, 0.25
+    w = _coordinate_only_weights(width, depth, ax, by, c)
+    bc = problem(lx, ly, 7)
+    u0 = random_state(lx, ly, bc, 8)
+    g = m.Grid(lx, ly, bc)
+    g.upload(u0)
+    g.sweep(m.SDNet(w, width, depth), 1, "M", prec)
+    got = g.download()
+    ny, nx = u0.shape
+    ix = np.arange(nx)[None, :].repeat(ny, 0)
+    iy = np.arange(ny)[:, None].repeat(nx, 1)
+    want = np.full((ny, nx), np.nan)
+    best = np.full((ny, nx), -1)
+    for a in range(2 * lx - 1):
+        for b in range(2 * ly - 1):
+            col = (a % 2) + 2 * (b % 2)
+            inside = (16 * a < ix) & (ix < 16 * a + 32) & (16 * b < iy) & (iy < 16 * b + 32) & (col > best)
+            v = ax * (ix - 16 * a) / 32.0 + by * (iy - 16 * b) / 32.0
+            for _ in range(depth):
+                v = np.tanh(v)
+            want = np.where(inside, v + c, want)
+            best = np.where(inside, col, best)
+    assert np.abs(got[1:-1, 1:-1] - want[1:-1, 1:-1]).max() <= tol
+    for edge in (np.s_[0, :], np.s_[-1, :], np.s_[:, 0], np.s_[:, -1]):
+        assert np.array_equal(got[edge], u0[edge])

@@ -174,6 +174,59 @@ def test_mlp_toy_hand_computed():
     assert abs(outb[1, p] - 6.25) < 1e-14
 
 
+def coordinate_only_weights(width, depth, ax, by, c):
+    """Packed weights of an SDNet that ignores its boundary input: unit 0 of the first
+    layer sees ax x + by y, each hidden layer passes unit 0 on with weight 1, and the
+    output is unit 0 plus c, so N(x, y) = tanh^depth(ax x + by y) + c exactly."""
+    w = np.zeros(I.SDNetShape(width, depth).n_params)
+    w[0 * 130 + 128], w[0 * 130 + 129] = ax, by       # W0[0][x], W0[0][y]
+    o = width * 130 + width                            # past W0 and b0
+    for _ in range(depth - 1):
+        w[o] = 1.0                                     # W_l[0][0]
+        o += width * width + width
+    w[o] = 1.0                                         # w_out[0]
+    w[o + width] = c                                   # b_out
+    return w
+
+
+@pytest.mark.parametrize("lx,ly", [(2, 3), (3, 2)])
+def test_coordinate_only_sdnet_sweep_closed_form(lx, ly):
+    """One multiplicative sweep (colours 0..3 in turn, Section 4.1) with a network that
+    ignores the boundary: every interior grid point ends with N at its local coordinates
+    in the last subdomain, in colour order, whose open interior holds it. The expected
+    grid comes from the subdomain layout alone (origins 16a, 16b at half overlap, colour
+    (a mod 2) + 2 (b mod 2)), not from the oracle's sweep, and pins the coordinate
+    convention, the colour order and the scatter."""
+    width, depth, ax, by, c = 64, 3, 1.3, -0.7, 0.25
+    P = mf.unpack_sdnet(coordinate_only_weights(width, depth, ax, by, c), width, depth)
+    ny, nx = mf.grid_shape(lx, ly)
+    u0 = np.asarray(I.Stream(31, I.TAG_TEST).normal(ny * nx)).reshape(ny, nx)
+    u1 = mf.sweep_multiplicative(u0, lx, ly, mf.Solver(P))
+
+    def N(x, y):
+        v = ax * x + by * y
+        for _ in range(depth):
+            v = math.tanh(v)
+        return v + c
+
+    nsx, nsy = 2 * lx - 1, 2 * ly - 1
+    for iy in range(1, ny - 1):
+        for ix in range(1, nx - 1):
+            cover = [(a, b) for a in range(nsx) for b in range(nsy)
+                     if 16 * a < ix < 16 * a + 32 and 16 * b < iy < 16 * b + 32]
+            a, b = max(cover, key=lambda ab: (ab[0] % 2) + 2 * (ab[1] % 2))
+            want = N((ix - 16 * a) / 32.0, (iy - 16 * b) / 32.0)
+            assert abs(u1[iy, ix] - want) < 1e-14, (ix, iy)
+    assert np.array_equal(boundary_only(u1), boundary_only(u0))
+
+
+def test_mutation_colour_order_is_caught(monkeypatch):
+    orig = mf.subdomains_of_colour
+    monkeypatch.setattr(mf, "subdomains_of_colour", lambda lx, ly, c: orig(lx, ly, 3 - c))
+    with pytest.raises(AssertionError):
+        test_coordinate_only_sdnet_sweep_closed_form(2, 3)
+
+
 def test_concat_equals_split():
     w = I.xavier_sdnet(I.SDNetShape(128, 6), 9, bias_scale=0.3)
     P = mf.unpack_sdnet(w, 128, 6)
