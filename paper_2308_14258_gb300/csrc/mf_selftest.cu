@@ -17,8 +17,9 @@ void set_last_error(const std::string& msg);
 
 namespace {
 
-// 64 threads: warp 0 uses the spinning wait (which also stops on the CTA abort flag),
-// warp 1 the try_wait form that ignores the abort flag and runs to its own limit.
+// 64 threads: in warp 0, lanes 0-15 use the spinning wait and lanes 16-31 the spinning
+// wait that sleeps between polls (both also stop on the CTA abort flag); warp 1 uses the
+// try_wait form that ignores the abort flag and runs to its own limit.
 __global__ void wait_timeout_kernel(unsigned long long limit_ns, int* status, int* gave_up) {
   __shared__ __align__(8) unsigned long long bar_word;
   __shared__ int abort_word;
@@ -29,8 +30,10 @@ __global__ void wait_timeout_kernel(unsigned long long limit_ns, int* status, in
   }
   __syncthreads();
   volatile int* abort_flag = &abort_word;
-  const bool ok = threadIdx.x < 32 ? mf::wait_spin(bar, 0, abort_flag, status, limit_ns)
-                                   : mf::wait_bounded(bar, 0, abort_flag, status, false, limit_ns);
+  bool ok;
+  if (threadIdx.x < 16) ok = mf::wait_spin(bar, 0, abort_flag, status, limit_ns);
+  else if (threadIdx.x < 32) ok = mf::wait_nap_inl(bar, 0, abort_flag, status, limit_ns);
+  else ok = mf::wait_bounded(bar, 0, abort_flag, status, false, limit_ns);
   if (!ok) atomicAdd(gave_up, 1);
 }
 
