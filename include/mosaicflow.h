@@ -28,6 +28,10 @@
  *  - The library owns the device memory behind handles; the caller owns host
  *    buffers and streams. There is no CPU fallback: without a usable CUDA device
  *    every call that needs one returns MF_ERR_CUDA.
+ *  - Every handle is created under an mf_ctx, which names one CUDA device, and lives
+ *    on that device. A call on a handle makes the handle's device current while it
+ *    runs and restores the caller's current device before it returns. Streams passed
+ *    with a handle must belong to the handle's device.
  */
 #ifndef MOSAICFLOW_H
 #define MOSAICFLOW_H
@@ -55,6 +59,7 @@ typedef int mf_status;
 #define MF_QUERY_FULL 0   /* predict all 961 interior points of every subdomain */
 #define MF_QUERY_CENTRE 1 /* predict only the 61 centre-cross points (interfaces) */
 
+typedef struct mf_ctx mf_ctx;     /* one CUDA device and the library's set-up on it */
 typedef struct mf_sdnet mf_sdnet; /* device-resident SDNet weights (both precisions) */
 typedef struct mf_grid mf_grid;   /* device grid of one problem plus its sweep scratch */
 typedef struct mf_batch mf_batch; /* device grids of many independent problems */
@@ -92,6 +97,7 @@ typedef struct {
   double ms_reduce;    /* profile only: summed event time of snapshot copies and reductions */
   int sweeps_bf16;     /* of sweeps_done, sweeps run on the BF16 path */
   int graph_sweeps;    /* mf_batch_sweep: sweeps replayed from the captured graph */
+  mf_status status;    /* the call's own return value (MF_OK, MF_ERR_DIVERGED, ...) */
 } mf_sweep_result;
 
 #define MF_ACT_TANH 0 /* tanh activations (the default network) */
@@ -112,16 +118,37 @@ const char* mf_last_error(void);
 /* Library version as major*10000 + minor*100 + patch. */
 int mf_version(void);
 
-/* mf_load_sdnet -- copy an SDNet to the current device (Section 3.1-3.2).
+/* mf_ctx_create -- the execution context of the Laplace problems of Section 2.1 (Eq. 2)
+ * on one device: it binds the library to CUDA device `device` (0-based, as numbered by
+ * the CUDA runtime under CUDA_VISIBLE_DEVICES), initialises the CUDA context there,
+ * checks that the device can run this build (compute capability 10.3, the sm_103a
+ * code the library carries) and records its SM count. The paper has no such object;
+ * it runs one process per GPU and leaves the device implicit.
+ * Grids, batches, SDNets and trainers are created under a context and stay on its
+ * device. The context owns no device memory; destroying it does not free the handles
+ * created under it, which stay valid and are freed by their own calls. It is safe to
+ * create several contexts for one device. The caller's current device is unchanged.
+ * Errors: MF_ERR_INVALID_ARG (null `out`, device < 0 or not present), MF_ERR_UNSUPPORTED
+ * (a device of another compute capability), MF_ERR_CUDA (no CUDA device or driver).
+ * Synchronous. */
+mf_status mf_ctx_create(int device, mf_ctx** out);
+mf_status mf_ctx_destroy(mf_ctx* ctx);
+
+/* The device index of a context, and its SM count (either pointer may be NULL). */
+mf_status mf_ctx_device(const mf_ctx* ctx, int* device, int* sm_count);
+
+/* mf_load_sdnet -- copy an SDNet to the context's device (Section 3.1-3.2).
  * `weights` is a host array of FP32 values packed as
  *   W0[H][130], b0[H], { W_l[H][H], b_l[H] } for l = 1..depth-1, w_out[H], b_out
  * where columns 0..127 of W0 are the boundary block W1 and columns 128..129 the
  * coordinate block W2 of the input-split first layer (Eq. 7-8); rows are output
  * units. The array is read during the call and not retained. The handle keeps an
  * FP32 copy and a BF16 (round-to-nearest-even) copy laid out for the tensor cores.
+ * Both copies are kept, so one handle serves every precision of mf_sweep; the
+ * precision is chosen per sweep, not at load time.
  * Errors: MF_ERR_INVALID_ARG for a null pointer or unsupported width/depth,
  * MF_ERR_OUT_OF_MEMORY / MF_ERR_CUDA from the device. Synchronous. */
-mf_status mf_load_sdnet(const mf_sdnet_desc* desc, const float* weights, mf_sdnet** out);
+mf_status mf_load_sdnet(mf_ctx* ctx, const mf_sdnet_desc* desc, const float* weights, mf_sdnet** out);
 
 /* mf_load_sdnet_ex -- mf_load_sdnet for the SDNet variants of Section 3.1: GELU
  * activations and/or a boundary embedding by 1-D convolutions, the boundary taken as a
@@ -136,17 +163,17 @@ mf_status mf_load_sdnet(const mf_sdnet_desc* desc, const float* weights, mf_sdne
  * MF_ACT_GELU is x Phi(x): exact (erf) on the FP32 path; on the BF16 path its tanh form
  * 0.5 x (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3))) (Hendrycks and Gimpel), whose error is
  * far below the BF16 rounding. Errors and synchronisation as mf_load_sdnet. */
-mf_status mf_load_sdnet_ex(const mf_sdnet_desc_ex* desc, const float* weights, mf_sdnet** out);
+mf_status mf_load_sdnet_ex(mf_ctx* ctx, const mf_sdnet_desc_ex* desc, const float* weights, mf_sdnet** out);
 mf_status mf_free_sdnet(mf_sdnet* net);
 
 /* mf_create_grid -- allocate the global grid of one Laplace problem (Eq. 2) on the
- * current device and set it up: boundary from `bc_ccw`, interior zero.
+ * context's device and set it up: boundary from `bc_ccw`, interior zero.
  * `bc_ccw` is a host array of 2(nx-1) + 2(ny-1) FP64 Dirichlet values in
  * counter-clockwise order from (0,0): bottom ix = 0..nx-2, right iy = 0..ny-2,
  * top ix = nx-1..1, left iy = ny-1..1. Values are rounded to FP32. Synchronous.
  * Errors: MF_ERR_INVALID_ARG (null pointer, lx or ly outside 1..128),
  * MF_ERR_OUT_OF_MEMORY, MF_ERR_CUDA. */
-mf_status mf_create_grid(const mf_grid_desc* desc, const double* bc_ccw, mf_grid** out);
+mf_status mf_create_grid(mf_ctx* ctx, const mf_grid_desc* desc, const double* bc_ccw, mf_grid** out);
 mf_status mf_destroy_grid(mf_grid* grid);
 
 /* Grid dimensions (points): *nx = 32 lx + 1, *ny = 32 ly + 1. */
@@ -201,7 +228,7 @@ mf_status mf_residual(const mf_grid* grid, double* max_abs, double* rms, void* s
  * Dirichlet lists (as in mf_create_grid) one after another. Sweeps over a batch treat
  * the atomic subdomains of one colour of all problems as one batch (Section 4.1
  * applied across problems). Synchronous. Errors as mf_create_grid. */
-mf_status mf_create_batch(int n, const mf_grid_desc* descs, const double* bc_all, mf_batch** out);
+mf_status mf_create_batch(mf_ctx* ctx, int n, const mf_grid_desc* descs, const double* bc_all, mf_batch** out);
 mf_status mf_destroy_batch(mf_batch* batch);
 
 /* Grid dimensions of one problem and its offset (in floats) inside the batch buffer. */
@@ -230,10 +257,11 @@ mf_status mf_batch_residual(const mf_batch* batch, int problem, double* max_abs,
  * cannot afford the device synchronisation a cudaMalloc/cudaFree implies. The paper
  * has no counterpart; this is an interface convenience of this library.
  * `u` is the caller's device grid (ny x nx FP32, row-major, boundary included), read
- * and updated in place; `net` was loaded earlier with mf_load_sdnet on the current
- * device; `precision` is MF_PREC_FP32 or MF_PREC_BF16. If `delta` is not NULL it
- * receives delta of the last sweep (-1 when n_sweeps is 0). The call synchronises
- * `stream` before returning.
+ * and updated in place; `net` was loaded earlier with mf_load_sdnet under a context of
+ * the current device (the call does not switch devices; another device returns
+ * MF_ERR_INVALID_ARG); `precision` is MF_PREC_FP32 or MF_PREC_BF16. If `delta` is not
+ * NULL it receives delta of the last sweep (-1 when n_sweeps is 0). The call is
+ * synchronous: it waits for its work on `stream` to finish, then returns.
  * Memory: nothing is allocated. All scratch lives in one fixed array of about 4.7 MB
  * that every GPU using this library holds until the process exits; grids are limited
  * to 1 <= lx, ly <= 32 (larger sizes return MF_ERR_INVALID_ARG). The first call on a
@@ -278,7 +306,7 @@ typedef struct {
   int engine;        /* MF_TRAIN_ENGINE_AUTO or MF_TRAIN_ENGINE_GEMM (same results to rounding) */
 } mf_train_desc;
 
-/* mf_create_trainer -- device state for training one SDNet on the current device.
+/* mf_create_trainer -- device state for training one SDNet on the context's device.
  * `weights`: host FP32 parameters in the mf_load_sdnet packing, copied during the call.
  * Device memory grows with max_functions * max_points * width * depth (about 20 GB at
  * 1024 x 1024 x 128 x 6 in BF16 with the GEMM engine, 8 GB with the fused engine): a
@@ -289,7 +317,7 @@ typedef struct {
  * Errors: MF_ERR_INVALID_ARG (null pointer, unsupported option, non-finite weight,
  * 4 * max_functions * max_points above 2^31 - 1), MF_ERR_OUT_OF_MEMORY, MF_ERR_CUDA.
  * Synchronous. */
-mf_status mf_create_trainer(const mf_train_desc* desc, const float* weights, mf_trainer** out);
+mf_status mf_create_trainer(mf_ctx* ctx, const mf_train_desc* desc, const float* weights, mf_trainer** out);
 mf_status mf_destroy_trainer(mf_trainer* trainer);
 
 /* Replace the weights from a host (src_on_device = 0) or device (1) FP32 array in the

@@ -54,6 +54,11 @@ mf_status cuda_fail(cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, what); \
   } while (0)
 
+// Make the handle's device current for the rest of the enclosing call.
+#define MF_ON_DEVICE(dev, what)                  \
+  mf::DeviceGuard guard_((dev));                 \
+  if (guard_.err != cudaSuccess) return cuda_fail(guard_.err, what)
+
 uint16_t bf16_rne(float f) {
   uint32_t u;
   std::memcpy(&u, &f, 4);
@@ -141,15 +146,50 @@ extern "C" {
 
 const char* mf_last_error(void) { return g_err.c_str(); }
 
-int mf_version(void) { return 100; }
+int mf_version(void) { return 200; }
 
-mf_status mf_load_sdnet(const mf_sdnet_desc* desc, const float* w, mf_sdnet** out) {
-  if (!desc) return fail(MF_ERR_INVALID_ARG, "mf_load_sdnet: null argument");
-  const mf_sdnet_desc_ex ex{desc->width, desc->depth, MF_ACT_TANH, 0, 0};
-  return mf_load_sdnet_ex(&ex, w, out);
+mf_status mf_ctx_create(int device, mf_ctx** out) {
+  if (!out) return fail(MF_ERR_INVALID_ARG, "mf_ctx_create: null argument");
+  *out = nullptr;
+  if (device < 0 || device >= mf::kMaxDevices) return fail(MF_ERR_INVALID_ARG, "mf_ctx_create: bad device index");
+  int count = 0;
+  MF_CUDA(cudaGetDeviceCount(&count), "mf_ctx_create: cudaGetDeviceCount");
+  if (device >= count) return fail(MF_ERR_INVALID_ARG, "mf_ctx_create: no such device");
+  MF_ON_DEVICE(device, "mf_ctx_create: cudaSetDevice");
+  MF_CUDA(cudaFree(nullptr), "mf_ctx_create: context initialisation");
+  int major = 0, minor = 0, sms = 0;
+  MF_CUDA(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device), "mf_ctx_create: attribute");
+  MF_CUDA(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device), "mf_ctx_create: attribute");
+  MF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device), "mf_ctx_create: attribute");
+  if (major != 10 || minor != 3)
+    return fail(MF_ERR_UNSUPPORTED, "mf_ctx_create: the library carries sm_103a code only; device has compute "
+                                    "capability " + std::to_string(major) + "." + std::to_string(minor));
+  mf_ctx* c = new mf_ctx();
+  c->device = device;
+  c->sms = sms;
+  *out = c;
+  return MF_OK;
 }
 
-mf_status mf_load_sdnet_ex(const mf_sdnet_desc_ex* desc, const float* w, mf_sdnet** out) {
+mf_status mf_ctx_destroy(mf_ctx* ctx) {
+  delete ctx;
+  return MF_OK;
+}
+
+mf_status mf_ctx_device(const mf_ctx* ctx, int* device, int* sm_count) {
+  if (!ctx) return fail(MF_ERR_INVALID_ARG, "mf_ctx_device: null context");
+  if (device) *device = ctx->device;
+  if (sm_count) *sm_count = ctx->sms;
+  return MF_OK;
+}
+
+mf_status mf_load_sdnet(mf_ctx* ctx, const mf_sdnet_desc* desc, const float* w, mf_sdnet** out) {
+  if (!desc) return fail(MF_ERR_INVALID_ARG, "mf_load_sdnet: null argument");
+  const mf_sdnet_desc_ex ex{desc->width, desc->depth, MF_ACT_TANH, 0, 0};
+  return mf_load_sdnet_ex(ctx, &ex, w, out);
+}
+
+mf_status mf_load_sdnet_ex(mf_ctx* ctx, const mf_sdnet_desc_ex* desc, const float* w, mf_sdnet** out) {
   if (!desc || !w || !out) return fail(MF_ERR_INVALID_ARG, "mf_load_sdnet: null argument");
   *out = nullptr;
   const int H = desc->width, D = desc->depth;
@@ -194,8 +234,10 @@ mf_status mf_load_sdnet_ex(const mf_sdnet_desc_ex* desc, const float* w, mf_sdne
   const float* wout = p;  p += H;
   const float bout = *p;
 
+  if (!ctx) return fail(MF_ERR_INVALID_ARG, "mf_load_sdnet: null context");
+  MF_ON_DEVICE(ctx->device, "mf_load_sdnet: cudaSetDevice");
   mf_sdnet* net = new mf_sdnet();
-  cudaGetDevice(&net->device);
+  net->device = ctx->device;
   // one allocation: W1t | W2 | b0 | WhT | bh | wout | BF16 images | conv (each 256-byte aligned)
   auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t sz_W1t = up(W1t.size() * 4), sz_W2 = up(W2.size() * 4), sz_b0 = up((size_t)H * 4),
@@ -255,7 +297,7 @@ mf_status mf_load_sdnet_ex(const mf_sdnet_desc_ex* desc, const float* w, mf_sdne
 
 mf_status mf_free_sdnet(mf_sdnet* net) {
   if (!net) return MF_OK;
-  cudaSetDevice(net->device);
+  mf::DeviceGuard guard(net->device);
   cudaFree(net->dmem);
   delete net;
   return MF_OK;
@@ -263,7 +305,7 @@ mf_status mf_free_sdnet(mf_sdnet* net) {
 
 mf_status mf_destroy_grid(mf_grid* g) {
   if (!g) return MF_OK;
-  cudaSetDevice(g->device);
+  mf::DeviceGuard guard(g->device);
   cudaFree(g->u);
   cudaFree(g->prev);
   cudaFree(g->B);
@@ -277,13 +319,15 @@ mf_status mf_destroy_grid(mf_grid* g) {
   return MF_OK;
 }
 
-mf_status mf_create_grid(const mf_grid_desc* desc, const double* bc, mf_grid** out) {
+mf_status mf_create_grid(mf_ctx* ctx, const mf_grid_desc* desc, const double* bc, mf_grid** out) {
   if (!desc || !bc || !out) return fail(MF_ERR_INVALID_ARG, "mf_create_grid: null argument");
   *out = nullptr;
   if (desc->lx < 1 || desc->lx > 128 || desc->ly < 1 || desc->ly > 128)
     return fail(MF_ERR_INVALID_ARG, "mf_create_grid: lx and ly must be in 1..128");
+  if (!ctx) return fail(MF_ERR_INVALID_ARG, "mf_create_grid: null context");
+  MF_ON_DEVICE(ctx->device, "mf_create_grid: cudaSetDevice");
   mf_grid* g = new mf_grid();
-  MF_CUDA(cudaGetDevice(&g->device), "mf_create_grid: cudaGetDevice");
+  g->device = ctx->device;
   g->lx = desc->lx;
   g->ly = desc->ly;
   g->nx = mf::kPts * g->lx + 1;
@@ -325,7 +369,7 @@ mf_status mf_grid_dims(const mf_grid* g, int* nx, int* ny) {
 
 mf_status mf_grid_upload(mf_grid* g, const float* src, int on_device, void* stream) {
   if (!g || !src) return fail(MF_ERR_INVALID_ARG, "mf_grid_upload: null argument");
-  MF_CUDA(cudaSetDevice(g->device), "mf_grid_upload: cudaSetDevice");
+  MF_ON_DEVICE(g->device, "mf_grid_upload: cudaSetDevice");
   MF_CUDA(cudaMemcpyAsync(g->u, src, (size_t)g->nx * g->ny * sizeof(float),
                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, as_stream(stream)),
           "mf_grid_upload: cudaMemcpyAsync");
@@ -334,15 +378,19 @@ mf_status mf_grid_upload(mf_grid* g, const float* src, int on_device, void* stre
 
 mf_status mf_grid_download(const mf_grid* g, float* dst, int on_device, void* stream) {
   if (!g || !dst) return fail(MF_ERR_INVALID_ARG, "mf_grid_download: null argument");
-  MF_CUDA(cudaSetDevice(g->device), "mf_grid_download: cudaSetDevice");
+  MF_ON_DEVICE(g->device, "mf_grid_download: cudaSetDevice");
   MF_CUDA(cudaMemcpyAsync(dst, g->u, (size_t)g->nx * g->ny * sizeof(float),
                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, as_stream(stream)),
           "mf_grid_download: cudaMemcpyAsync");
   return MF_OK;
 }
 
-mf_status mf_sweep(mf_grid* g, const mf_sdnet* net, const mf_sweep_opts* o, mf_sweep_result* res,
-                   void* stream) {
+}  // extern "C"
+
+namespace {
+
+mf_status sweep_impl(mf_grid* g, const mf_sdnet* net, const mf_sweep_opts* o, mf_sweep_result* res,
+                     void* stream) {
   if (!g || !net || !o) return fail(MF_ERR_INVALID_ARG, "mf_sweep: null argument");
   if (o->n_sweeps < 0) return fail(MF_ERR_INVALID_ARG, "mf_sweep: n_sweeps < 0");
   if (o->schedule != MF_SCHEDULE_MULTIPLICATIVE && o->schedule != MF_SCHEDULE_ADDITIVE)
@@ -361,8 +409,8 @@ mf_status mf_sweep(mf_grid* g, const mf_sdnet* net, const mf_sweep_opts* o, mf_s
   if (o->precision != MF_PREC_FP32 && !mf::bf16_supported(net->d))
     return fail(MF_ERR_UNSUPPORTED, "mf_sweep: BF16 path needs 1..5 hidden layers");
   if (net->device != g->device) return fail(MF_ERR_INVALID_ARG, "mf_sweep: grid and SDNet on different devices");
-  if (res) *res = mf_sweep_result{0, -1.0, 0, 0, 0.0, 0.0, 0.0, 0};
-  MF_CUDA(cudaSetDevice(g->device), "mf_sweep: cudaSetDevice");
+  if (res) *res = mf_sweep_result{0, -1.0, 0, 0, 0.0, 0.0, 0.0, 0, 0, MF_OK};
+  MF_ON_DEVICE(g->device, "mf_sweep: cudaSetDevice");
   cudaStream_t st = as_stream(stream);
   const int mask = o->colours == 0 ? 15 : o->colours;
   const bool additive = o->schedule == MF_SCHEDULE_ADDITIVE;
@@ -447,6 +495,17 @@ mf_status mf_sweep(mf_grid* g, const mf_sdnet* net, const mf_sweep_opts* o, mf_s
   return MF_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+mf_status mf_sweep(mf_grid* g, const mf_sdnet* net, const mf_sweep_opts* o, mf_sweep_result* res,
+                   void* stream) {
+  const mf_status st = sweep_impl(g, net, o, res, stream);
+  if (res) res->status = st;
+  return st;
+}
+
 mf_status mf_synchronize(void* stream) {
   MF_CUDA(cudaStreamSynchronize(as_stream(stream)), "mf_synchronize");
   return MF_OK;
@@ -454,7 +513,7 @@ mf_status mf_synchronize(void* stream) {
 
 mf_status mf_residual(const mf_grid* g, double* max_abs, double* rms, void* stream) {
   if (!g) return fail(MF_ERR_INVALID_ARG, "mf_residual: null grid");
-  MF_CUDA(cudaSetDevice(g->device), "mf_residual: cudaSetDevice");
+  MF_ON_DEVICE(g->device, "mf_residual: cudaSetDevice");
   cudaStream_t st = as_stream(stream);
   MF_CUDA(mf::launch_reduce(g->u, nullptr, g->nx, g->ny, g->partial, g->out + 8, st), "mf_residual: reduce");
   MF_CUDA(cudaMemcpyAsync(g->h_out + 8, g->out + 8, 5 * sizeof(double), cudaMemcpyDeviceToHost, st),

@@ -64,6 +64,9 @@ mf_status cuda_fail(cudaError_t e, const char* what) {
     cudaError_t e_ = (call);                           \
     if (e_ != cudaSuccess) return cuda_fail(e_, what); \
   } while (0)
+#define BT_ON_DEVICE(dev, what)   \
+  mf::DeviceGuard guard_((dev));  \
+  if (guard_.err != cudaSuccess) return cuda_fail(guard_.err, what)
 
 mf::ColourGeom batch_geom(const mf_batch* b, int c, int query) {
   mf::ColourGeom g{};
@@ -101,7 +104,7 @@ extern "C" {
 
 mf_status mf_destroy_batch(mf_batch* b) {
   if (!b) return MF_OK;
-  cudaSetDevice(b->device);
+  mf::DeviceGuard guard(b->device);
   drop_graph(b);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   cudaFree(b->u);
@@ -117,14 +120,16 @@ mf_status mf_destroy_batch(mf_batch* b) {
   return MF_OK;
 }
 
-mf_status mf_create_batch(int n, const mf_grid_desc* descs, const double* bc_all, mf_batch** out) {
+mf_status mf_create_batch(mf_ctx* ctx, int n, const mf_grid_desc* descs, const double* bc_all, mf_batch** out) {
   if (!descs || !bc_all || !out || n < 1) return fail(MF_ERR_INVALID_ARG, "mf_create_batch: null argument or n < 1");
   *out = nullptr;
   for (int q = 0; q < n; ++q)
     if (descs[q].lx < 1 || descs[q].lx > 128 || descs[q].ly < 1 || descs[q].ly > 128)
       return fail(MF_ERR_INVALID_ARG, "mf_create_batch: lx and ly must be in 1..128");
+  if (!ctx) return fail(MF_ERR_INVALID_ARG, "mf_create_batch: null context");
+  BT_ON_DEVICE(ctx->device, "mf_create_batch: cudaSetDevice");
   mf_batch* b = new mf_batch();
-  cudaGetDevice(&b->device);
+  b->device = ctx->device;
   b->n = n;
   size_t off = 0, nbc = 0;
   std::vector<size_t> bc_off(n);
@@ -197,7 +202,7 @@ mf_status mf_batch_info(const mf_batch* b, int problem, int* nx, int* ny, long l
 
 mf_status mf_batch_upload(mf_batch* b, int problem, const float* src, int on_device, void* stream) {
   if (!b || !src || problem < 0 || problem >= b->n) return fail(MF_ERR_INVALID_ARG, "mf_batch_upload: bad argument");
-  BT_CUDA(cudaSetDevice(b->device), "mf_batch_upload: cudaSetDevice");
+  BT_ON_DEVICE(b->device, "mf_batch_upload: cudaSetDevice");
   BT_CUDA(cudaMemcpyAsync(b->u + b->offset[problem], src, (size_t)b->nx[problem] * b->ny[problem] * sizeof(float),
                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                           reinterpret_cast<cudaStream_t>(stream)),
@@ -207,7 +212,7 @@ mf_status mf_batch_upload(mf_batch* b, int problem, const float* src, int on_dev
 
 mf_status mf_batch_download(const mf_batch* b, int problem, float* dst, int on_device, void* stream) {
   if (!b || !dst || problem < 0 || problem >= b->n) return fail(MF_ERR_INVALID_ARG, "mf_batch_download: bad argument");
-  BT_CUDA(cudaSetDevice(b->device), "mf_batch_download: cudaSetDevice");
+  BT_ON_DEVICE(b->device, "mf_batch_download: cudaSetDevice");
   BT_CUDA(cudaMemcpyAsync(dst, b->u + b->offset[problem], (size_t)b->nx[problem] * b->ny[problem] * sizeof(float),
                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                           reinterpret_cast<cudaStream_t>(stream)),
@@ -217,7 +222,7 @@ mf_status mf_batch_download(const mf_batch* b, int problem, float* dst, int on_d
 
 mf_status mf_batch_residual(const mf_batch* b, int problem, double* max_abs, double* rms, void* stream) {
   if (!b || problem < 0 || problem >= b->n) return fail(MF_ERR_INVALID_ARG, "mf_batch_residual: bad argument");
-  BT_CUDA(cudaSetDevice(b->device), "mf_batch_residual: cudaSetDevice");
+  BT_ON_DEVICE(b->device, "mf_batch_residual: cudaSetDevice");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int nx = b->nx[problem], ny = b->ny[problem];
   BT_CUDA(mf::launch_reduce(b->u + b->offset[problem], nullptr, nx, ny, b->partial, b->out + 8, st),
@@ -230,8 +235,12 @@ mf_status mf_batch_residual(const mf_batch* b, int problem, double* max_abs, dou
   return MF_OK;
 }
 
-mf_status mf_batch_sweep(mf_batch* b, const mf_sdnet* net, const mf_sweep_opts* o, mf_sweep_result* res,
-                         void* stream) {
+}  // extern "C"
+
+namespace {
+
+mf_status batch_sweep_impl(mf_batch* b, const mf_sdnet* net, const mf_sweep_opts* o, mf_sweep_result* res,
+                           void* stream) {
   if (!b || !net || !o) return fail(MF_ERR_INVALID_ARG, "mf_batch_sweep: null argument");
   if (o->n_sweeps < 0) return fail(MF_ERR_INVALID_ARG, "mf_batch_sweep: n_sweeps < 0");
   if (o->schedule != MF_SCHEDULE_MULTIPLICATIVE)
@@ -248,8 +257,8 @@ mf_status mf_batch_sweep(mf_batch* b, const mf_sdnet* net, const mf_sweep_opts* 
   if (net_device != b->device) return fail(MF_ERR_INVALID_ARG, "mf_batch_sweep: batch and SDNet on different devices");
   if (o->precision == MF_PREC_BF16 && !mf::bf16_supported(*d))
     return fail(MF_ERR_UNSUPPORTED, "mf_batch_sweep: BF16 path needs 1..5 hidden layers");
-  if (res) *res = mf_sweep_result{0, -1.0, 0, 0, 0.0, 0.0, 0.0, 0};
-  BT_CUDA(cudaSetDevice(b->device), "mf_batch_sweep: cudaSetDevice");
+  if (res) *res = mf_sweep_result{0, -1.0, 0, 0, 0.0, 0.0, 0.0, 0, 0, MF_OK};
+  BT_ON_DEVICE(b->device, "mf_batch_sweep: cudaSetDevice");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   BT_CUDA(cudaMemsetAsync(b->status, 0, sizeof(int), st), "mf_batch_sweep: reset status");
 
@@ -320,6 +329,17 @@ mf_status mf_batch_sweep(mf_batch* b, const mf_sdnet* net, const mf_sweep_opts* 
   }
   if (checked && !std::isfinite(b->h_out[4])) return fail(MF_ERR_DIVERGED, "mf_batch_sweep: delta is not finite");
   return MF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mf_status mf_batch_sweep(mf_batch* b, const mf_sdnet* net, const mf_sweep_opts* o, mf_sweep_result* res,
+                         void* stream) {
+  const mf_status st = batch_sweep_impl(b, net, o, res, stream);
+  if (res) res->status = st;
+  return st;
 }
 
 }  // extern "C"

@@ -137,14 +137,12 @@ embed_boundary_kernel(const float* __restrict__ u, ColourGeom g, const float* __
 template <int H, int ACT>
 cudaError_t launch_embed(const float* u, const ColourGeom& g, const DevNet& net, float* B, cudaStream_t st) {
   const size_t smem = (size_t)kEmbedSubs * embed_floats_per_sub(net.embed_c) * sizeof(float);
-  static bool attr_set = false;
-  if (!attr_set) {
+  static PerDevice pd;
+  cudaError_t e = per_device(pd, [](int, int*, size_t*) {
     const int max_smem = kEmbedSubs * embed_floats_per_sub(kMaxEmbedC) * (int)sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(embed_boundary_kernel<H, ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         max_smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+    return cudaFuncSetAttribute(embed_boundary_kernel<H, ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  });
+  if (e != cudaSuccess) return e;
   const int blocks = (g.n_c + kEmbedSubs - 1) / kEmbedSubs;
   embed_boundary_kernel<H, ACT><<<blocks, kEmbedThreads, smem, st>>>(u, g, net.cw1, net.cb1, net.cw2, net.cb2,
                                                                       net.embed_c, net.embed_k, net.W1t, net.b0, B);

@@ -4,7 +4,86 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
+// An execution context (the ABI's mf_ctx): one CUDA device and what the library knows
+// about it. Handles created under it copy the device index and keep no pointer to it.
+struct mf_ctx {
+  int device = 0;
+  int sms = 0;
+};
+
 namespace mf {
+
+// ---- devices ----------------------------------------------------------------------
+// Handles record the device they were created on; every call that works on a handle
+// makes that device current for its duration and gives the caller's selection back.
+constexpr int kMaxDevices = 64;
+
+struct DeviceGuard {
+  int prev = -1;
+  cudaError_t err = cudaSuccess;
+  explicit DeviceGuard(int device) {
+    err = cudaGetDevice(&prev);
+    if (err != cudaSuccess) {
+      prev = -1;
+      return;
+    }
+    if (prev != device) err = cudaSetDevice(device);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+  DeviceGuard(const DeviceGuard&) = delete;
+  DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
+
+// One-time launch set-up per device. A cudaFuncSetAttribute call, an occupancy query
+// and the SM count all belong to the device that is current when they run, so each
+// launcher keeps one record per device, filled under a lock the first time that
+// device launches it.
+struct PerDevice {
+  std::mutex lock;
+  bool ready[kMaxDevices] = {};
+  int ival[kMaxDevices] = {};
+  size_t zval[kMaxDevices] = {};
+};
+
+inline cudaError_t current_device(int* dev) {
+  const cudaError_t e = cudaGetDevice(dev);
+  if (e != cudaSuccess) return e;
+  return (*dev < 0 || *dev >= kMaxDevices) ? cudaErrorInvalidDevice : cudaSuccess;
+}
+
+// Runs init(device, ival, zval) once per device for the record `pd`; returns its
+// error, and the stored values through ival/zval.
+template <class F>
+cudaError_t per_device(PerDevice& pd, F&& init, int* ival = nullptr, size_t* zval = nullptr) {
+  int dev = 0;
+  cudaError_t e = current_device(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> g(pd.lock);
+  if (!pd.ready[dev]) {
+    int iv = 0;
+    size_t zv = 0;
+    e = init(dev, &iv, &zv);
+    if (e != cudaSuccess) return e;
+    pd.ival[dev] = iv;
+    pd.zval[dev] = zv;
+    pd.ready[dev] = true;
+  }
+  if (ival) *ival = pd.ival[dev];
+  if (zval) *zval = pd.zval[dev];
+  return cudaSuccess;
+}
+
+// SM count of the current device (cached per device).
+inline cudaError_t device_sms(int* sms) {
+  static PerDevice pd;
+  return per_device(pd, [](int dev, int* iv, size_t*) {
+    return cudaDeviceGetAttribute(iv, cudaDevAttrMultiProcessorCount, dev);
+  }, sms);
+}
 
 // Geometry of the unit subdomain: 32 intervals per side, lattice spacing 16 points.
 constexpr int kPts = 32;        // intervals per unit length

@@ -395,33 +395,37 @@ __global__ void __launch_bounds__(kThreadsBf16, 1) mlp_bf16_kernel(const __grid_
 template <int H, int NH, int ACT>
 cudaError_t launch_t(const Bf16Params& p, cudaStream_t st) {
   using C = Bf16Cfg<H, NH>;
-  static int grid_cap = 0;
-  static size_t smem_bytes = 0;
-  if (grid_cap == 0) {
+  // per device: the dynamic shared memory to request and the grid cap (resident CTAs)
+  static PerDevice pd;
+  int grid_cap = 0;
+  size_t smem_bytes = 0;
+  cudaError_t e0 = per_device(pd, [](int dev, int* cap, size_t* smem) {
     cudaError_t e = cudaFuncSetAttribute(mlp_bf16_kernel<H, NH, ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)C::kSmem);
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int sms = 0, per_sm = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_bf16_kernel<H, NH, ACT>, kThreadsBf16, C::kSmem);
     if (e != cudaSuccess) return e;
     // every resident CTA must be able to hold its tensor memory at once (512 columns):
     // if shared memory alone would admit more CTAs per SM, request more of it
     const int tmem_cap = 512 / (int)C::kTmemCols;
-    smem_bytes = C::kSmem;
+    *smem = C::kSmem;
     if (per_sm > tmem_cap) {
       int smem_sm = 0;
       cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-      smem_bytes = (size_t)smem_sm / (size_t)(tmem_cap + 1) + 1024;
-      e = cudaFuncSetAttribute(mlp_bf16_kernel<H, NH, ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+      *smem = (size_t)smem_sm / (size_t)(tmem_cap + 1) + 1024;
+      e = cudaFuncSetAttribute(mlp_bf16_kernel<H, NH, ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
       if (e != cudaSuccess) return e;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_bf16_kernel<H, NH, ACT>, kThreadsBf16, smem_bytes);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_bf16_kernel<H, NH, ACT>, kThreadsBf16, *smem);
       if (e != cudaSuccess) return e;
     }
     if (per_sm > tmem_cap || per_sm < 1) return cudaErrorInvalidConfiguration;
-    grid_cap = sms * per_sm;
-  }
+    *cap = sms * per_sm;
+    return cudaSuccess;
+  }, &grid_cap, &smem_bytes);
+  if (e0 != cudaSuccess) return e0;
   int grid = (p.n_tiles + kSlots - 1) / kSlots;
   if (grid > grid_cap) grid = grid_cap;
   if (grid < 1) return cudaSuccess;

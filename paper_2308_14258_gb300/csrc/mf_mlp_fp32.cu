@@ -158,13 +158,11 @@ cudaError_t launch_h(const float* B, const ColourGeom& g, const DevNet& net, flo
   const int n_rows = g.n_c * g.rows_per_sub;
   const int tiles = (n_rows + kTR - 1) / kTR;
   const size_t smem = Fp32Cfg<H>::kSmem;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(mlp_fp32_kernel<H, ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static PerDevice pd;
+  cudaError_t e = per_device(pd, [smem](int, int*, size_t*) {
+    return cudaFuncSetAttribute(mlp_fp32_kernel<H, ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (e != cudaSuccess) return e;
   mlp_fp32_kernel<H, ACT><<<tiles, kThreads, smem, st>>>(B, g, n_rows, net.W2, net.WhT, net.bh, net.wout, net.bout,
                                                      net.n_hidden, u, additive);
   return cudaGetLastError();

@@ -417,6 +417,9 @@ mf_status tblas(cublasStatus_t s, const char* what) {
     cudaError_t e_ = (call);                         \
     if (e_ != cudaSuccess) return tcuda(e_, what);   \
   } while (0)
+#define TR_ON_DEVICE(dev, what)   \
+  mf::DeviceGuard guard_((dev));  \
+  if (guard_.err != cudaSuccess) return tcuda(guard_.err, what)
 #define TR_BLAS(call, what)                                     \
   do {                                                          \
     cublasStatus_t s_ = (call);                                 \
@@ -726,7 +729,7 @@ extern "C" {
 
 mf_status mf_destroy_trainer(mf_trainer* t) {
   if (!t) return MF_OK;
-  cudaSetDevice(t->device);
+  mf::DeviceGuard guard(t->device);
   if (t->cublas) cublasDestroy(t->cublas);
   for (void* p : t->A) cudaFree(p);
   for (float* p : t->Z) cudaFree(p);
@@ -741,7 +744,7 @@ mf_status mf_destroy_trainer(mf_trainer* t) {
   return MF_OK;
 }
 
-mf_status mf_create_trainer(const mf_train_desc* d, const float* weights, mf_trainer** out) {
+mf_status mf_create_trainer(mf_ctx* ctx, const mf_train_desc* d, const float* weights, mf_trainer** out) {
   if (!d || !weights || !out) return tfail(MF_ERR_INVALID_ARG, "mf_create_trainer: null argument");
   *out = nullptr;
   if (d->width != 64 && d->width != 128) return tfail(MF_ERR_INVALID_ARG, "mf_create_trainer: width must be 64 or 128");
@@ -756,8 +759,15 @@ mf_status mf_create_trainer(const mf_train_desc* d, const float* weights, mf_tra
     return tfail(MF_ERR_INVALID_ARG, "mf_create_trainer: unknown optimizer");
   if (d->engine != MF_TRAIN_ENGINE_AUTO && d->engine != MF_TRAIN_ENGINE_GEMM)
     return tfail(MF_ERR_INVALID_ARG, "mf_create_trainer: unknown engine");
+  {
+    const size_t h = (size_t)d->width, n_params = h * (kNB + 2) + h + (size_t)(d->depth - 1) * (h * h + h) + h + 1;
+    for (size_t i = 0; i < n_params; ++i)
+      if (!std::isfinite(weights[i])) return tfail(MF_ERR_INVALID_ARG, "mf_create_trainer: non-finite weight");
+  }
+  if (!ctx) return tfail(MF_ERR_INVALID_ARG, "mf_create_trainer: null context");
+  TR_ON_DEVICE(ctx->device, "mf_create_trainer: cudaSetDevice");
   mf_trainer* t = new mf_trainer();
-  cudaGetDevice(&t->device);
+  t->device = ctx->device;
   t->H = d->width;
   t->D = d->depth;
   t->NH = d->depth - 1;
@@ -782,11 +792,6 @@ mf_status mf_create_trainer(const mf_train_desc* d, const float* weights, mf_tra
   t->off_wout = t->off_b0 + H + (size_t)t->NH * (HH + H);
   t->off_bout = t->off_wout + H;
   t->n_params = t->off_bout + 1;
-  for (size_t i = 0; i < t->n_params; ++i)
-    if (!std::isfinite(weights[i])) {
-      delete t;
-      return tfail(MF_ERR_INVALID_ARG, "mf_create_trainer: non-finite weight");
-    }
   const size_t es = esize(t), C4 = 4 * t->Rmax * H;
   // fused engine: a tile buffer holds a chunk's collocation tiles (4 channels, 32 points
   // each) followed by its data tiles (128 points each, the last one padded)
@@ -875,7 +880,7 @@ mf_status mf_create_trainer(const mf_train_desc* d, const float* weights, mf_tra
 
 mf_status mf_trainer_set_weights(mf_trainer* t, const float* src, int on_device, void* stream) {
   if (!t || !src) return tfail(MF_ERR_INVALID_ARG, "mf_trainer_set_weights: null argument");
-  TR_CUDA(cudaSetDevice(t->device), "mf_trainer_set_weights");
+  TR_ON_DEVICE(t->device, "mf_trainer_set_weights");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   TR_CUDA(cudaMemcpyAsync(t->w, src, t->n_params * 4, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st),
           "mf_trainer_set_weights");
@@ -884,6 +889,7 @@ mf_status mf_trainer_set_weights(mf_trainer* t, const float* src, int on_device,
 
 mf_status mf_trainer_get_weights(const mf_trainer* t, float* dst, int on_device, void* stream) {
   if (!t || !dst) return tfail(MF_ERR_INVALID_ARG, "mf_trainer_get_weights: null argument");
+  TR_ON_DEVICE(t->device, "mf_trainer_get_weights");
   TR_CUDA(cudaMemcpyAsync(dst, t->w, t->n_params * 4, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                           reinterpret_cast<cudaStream_t>(stream)),
           "mf_trainer_get_weights");
@@ -892,6 +898,7 @@ mf_status mf_trainer_get_weights(const mf_trainer* t, float* dst, int on_device,
 
 mf_status mf_trainer_get_grads(const mf_trainer* t, float* dst, int on_device, void* stream) {
   if (!t || !dst) return tfail(MF_ERR_INVALID_ARG, "mf_trainer_get_grads: null argument");
+  TR_ON_DEVICE(t->device, "mf_trainer_get_grads");
   TR_CUDA(cudaMemcpyAsync(dst, t->g, t->n_params * 4, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                           reinterpret_cast<cudaStream_t>(stream)),
           "mf_trainer_get_grads");
@@ -903,7 +910,7 @@ mf_status mf_train_grad(mf_trainer* t, int F, int Nc, int Nb, const float* G, co
   if (!t) return tfail(MF_ERR_INVALID_ARG, "mf_train_grad: null trainer");
   mf_status s = validate_batch(t, F, Nc, Nb, G, Xc, Xb, Yb);
   if (s != MF_OK) return s;
-  TR_CUDA(cudaSetDevice(t->device), "mf_train_grad");
+  TR_ON_DEVICE(t->device, "mf_train_grad");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   TR_BLAS(cublasSetStream(t->cublas, st), "mf_train_grad: cublasSetStream");
   TR_CUDA(cudaMemsetAsync(t->g, 0, t->n_params * 4, st), "mf_train_grad: zero grads");
@@ -934,9 +941,10 @@ mf_status mf_train_grad(mf_trainer* t, int F, int Nc, int Nb, const float* G, co
 
 mf_status mf_train_step(mf_trainer* t, int F, int Nc, int Nb, const float* G, const float* Xc, const float* Xb,
                         const float* Yb, float lr, double* loss3, void* stream) {
+  if (!std::isfinite(lr)) return tfail(MF_ERR_INVALID_ARG, "mf_train_step: lr must be finite");
   mf_status s = mf_train_grad(t, F, Nc, Nb, G, Xc, Xb, Yb, loss3, stream);
   if (s != MF_OK) return s;
-  if (!std::isfinite(lr)) return tfail(MF_ERR_INVALID_ARG, "mf_train_step: lr must be finite");
+  TR_ON_DEVICE(t->device, "mf_train_step");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (t->optimizer == MF_OPT_SGD) {
     sgd_kernel<<<256, 256, 0, st>>>(t->w, t->g, lr, t->n_params);

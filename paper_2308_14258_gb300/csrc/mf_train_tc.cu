@@ -1532,12 +1532,8 @@ static_assert(kFwdSmem <= 232448, "forward kernel shared memory");
 static_assert(kBwdSmem <= 232448, "backward kernel shared memory");
 
 int grid_for(int n_tiles) {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  }
+  int sms = 0;
+  if (device_sms(&sms) != cudaSuccess || sms < 1) sms = 1;
   return n_tiles < sms ? n_tiles : sms;
 }
 
@@ -1570,24 +1566,22 @@ cudaError_t tc_first_bwd(const float* Bf, const float* W0, const float* b0, cons
 }
 
 cudaError_t tc_layer_fwd2(const TcFwd2Params& p, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tc_fwd2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwd2Smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static PerDevice pd;
+  cudaError_t e = per_device(pd, [](int, int*, size_t*) {
+    return cudaFuncSetAttribute(tc_fwd2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwd2Smem);
+  });
+  if (e != cudaSuccess) return e;
   if (p.n_tiles <= 0) return cudaSuccess;
   tc_fwd2_kernel<<<grid_for(p.n_tiles), kThreadsF2, kFwd2Smem, st>>>(p);
   return cudaGetLastError();
 }
 
 cudaError_t tc_layer_fwd(const TcFwdParams& p, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tc_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static PerDevice pd;
+  cudaError_t e = per_device(pd, [](int, int*, size_t*) {
+    return cudaFuncSetAttribute(tc_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
+  });
+  if (e != cudaSuccess) return e;
   if (p.n_tiles <= 0) return cudaSuccess;
   tc_fwd_kernel<<<grid_for(p.n_tiles), kThreadsTc, kFwdSmem, st>>>(p);
   return cudaGetLastError();
@@ -1595,13 +1589,12 @@ cudaError_t tc_layer_fwd(const TcFwdParams& p, cudaStream_t st) {
 
 template <bool kTop, bool kFirst>
 cudaError_t launch_bwd(const TcBwdParams& p, int grid, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e =
-        cudaFuncSetAttribute(tc_bwd_kernel<kTop, kFirst>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdSmem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static PerDevice pd;
+  cudaError_t e = per_device(pd, [](int, int*, size_t*) {
+    return cudaFuncSetAttribute(tc_bwd_kernel<kTop, kFirst>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kBwdSmem);
+  });
+  if (e != cudaSuccess) return e;
   tc_bwd_kernel<kTop, kFirst><<<grid, kThreadsB, kBwdSmem, st>>>(p);
   return cudaGetLastError();
 }

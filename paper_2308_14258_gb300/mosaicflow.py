@@ -32,7 +32,7 @@ ENGINE = {"auto": 0, "gemm": 1}
 ACTIVATION = {"tanh": 0, "gelu": 1}
 
 # Every exported symbol the header declares (checked by the CPU test suite).
-EXPORTS = ["mf_last_error", "mf_version", "mf_load_sdnet", "mf_load_sdnet_ex", "mf_free_sdnet", "mf_create_grid",
+EXPORTS = ["mf_last_error", "mf_version", "mf_ctx_create", "mf_ctx_destroy", "mf_ctx_device", "mf_load_sdnet", "mf_load_sdnet_ex", "mf_free_sdnet", "mf_create_grid",
            "mf_destroy_grid", "mf_grid_dims", "mf_grid_upload", "mf_grid_download", "mf_sweep",
            "mf_residual", "mf_synchronize", "mf_sweep_noalloc", "mf_create_batch", "mf_destroy_batch",
            "mf_batch_info", "mf_batch_upload", "mf_batch_download", "mf_batch_sweep", "mf_batch_residual",
@@ -68,7 +68,8 @@ class SweepOpts(C.Structure):
 class SweepResult(C.Structure):
     _fields_ = [("sweeps_done", C.c_int), ("delta", C.c_double), ("kernel_launches", C.c_int),
                 ("mlp_launches", C.c_int), ("ms_gather", C.c_double), ("ms_mlp", C.c_double),
-                ("ms_reduce", C.c_double), ("sweeps_bf16", C.c_int), ("graph_sweeps", C.c_int)]
+                ("ms_reduce", C.c_double), ("sweeps_bf16", C.c_int), ("graph_sweeps", C.c_int),
+                ("status", C.c_int)]
 
 
 class TrainDesc(C.Structure):
@@ -96,10 +97,13 @@ def load(path: str | None = None) -> C.CDLL:
     vp, i = C.c_void_p, C.c_int
     lib.mf_last_error.restype = C.c_char_p
     lib.mf_version.restype = i
-    lib.mf_load_sdnet.argtypes = [C.POINTER(SDNetDesc), vp, C.POINTER(vp)]
-    lib.mf_load_sdnet_ex.argtypes = [C.POINTER(SDNetDescEx), vp, C.POINTER(vp)]
+    lib.mf_ctx_create.argtypes = [i, C.POINTER(vp)]
+    lib.mf_ctx_destroy.argtypes = [vp]
+    lib.mf_ctx_device.argtypes = [vp, C.POINTER(i), C.POINTER(i)]
+    lib.mf_load_sdnet.argtypes = [vp, C.POINTER(SDNetDesc), vp, C.POINTER(vp)]
+    lib.mf_load_sdnet_ex.argtypes = [vp, C.POINTER(SDNetDescEx), vp, C.POINTER(vp)]
     lib.mf_free_sdnet.argtypes = [vp]
-    lib.mf_create_grid.argtypes = [C.POINTER(GridDesc), vp, C.POINTER(vp)]
+    lib.mf_create_grid.argtypes = [vp, C.POINTER(GridDesc), vp, C.POINTER(vp)]
     lib.mf_destroy_grid.argtypes = [vp]
     lib.mf_grid_dims.argtypes = [vp, C.POINTER(i), C.POINTER(i)]
     lib.mf_grid_upload.argtypes = [vp, vp, i, vp]
@@ -108,7 +112,7 @@ def load(path: str | None = None) -> C.CDLL:
     lib.mf_residual.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
     lib.mf_synchronize.argtypes = [vp]
     lib.mf_sweep_noalloc.argtypes = [vp, i, i, vp, i, i, C.POINTER(C.c_double), vp]
-    lib.mf_create_batch.argtypes = [i, vp, vp, C.POINTER(vp)]
+    lib.mf_create_batch.argtypes = [vp, i, vp, vp, C.POINTER(vp)]
     lib.mf_destroy_batch.argtypes = [vp]
     lib.mf_batch_info.argtypes = [vp, i, C.POINTER(i), C.POINTER(i), C.POINTER(C.c_longlong)]
     lib.mf_batch_upload.argtypes = [vp, i, vp, i, vp]
@@ -116,7 +120,7 @@ def load(path: str | None = None) -> C.CDLL:
     lib.mf_batch_sweep.argtypes = [vp, vp, C.POINTER(SweepOpts), C.POINTER(SweepResult), vp]
     lib.mf_batch_residual.argtypes = [vp, i, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
     lib.mf_check_wait_timeout.argtypes = [C.c_double, C.POINTER(i)]
-    lib.mf_create_trainer.argtypes = [C.POINTER(TrainDesc), vp, C.POINTER(vp)]
+    lib.mf_create_trainer.argtypes = [vp, C.POINTER(TrainDesc), vp, C.POINTER(vp)]
     lib.mf_destroy_trainer.argtypes = [vp]
     lib.mf_trainer_set_weights.argtypes = [vp, vp, i, vp]
     lib.mf_trainer_get_weights.argtypes = [vp, vp, i, vp]
@@ -155,20 +159,60 @@ def _buffer(arr):
     return arr.data_ptr(), 1 if arr.is_cuda else 0, arr.numel() * 4
 
 
+class Context:
+    """mf_ctx_create / mf_ctx_destroy: the library bound to one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self._h = C.c_void_p()
+        _check(load().mf_ctx_create(int(device), C.byref(self._h)))
+        dev, sms = C.c_int(), C.c_int()
+        _check(load().mf_ctx_device(self._h, C.byref(dev), C.byref(sms)))
+        self.device, self.sm_count = dev.value, sms.value
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.mf_ctx_destroy(self._h)
+            self._h = None
+
+
+_CONTEXTS: dict = {}
+
+
+def default_context(device: int | None = None) -> Context:
+    """The context of `device` (default: torch's current CUDA device, else 0), created
+    on first use and kept for the process."""
+    if device is None:
+        device = 0
+        try:
+            import torch
+            if torch.cuda.is_available():
+                device = torch.cuda.current_device()
+        except ImportError:
+            pass
+    if device not in _CONTEXTS:
+        _CONTEXTS[device] = Context(device)
+    return _CONTEXTS[device]
+
+
+def _ctx(ctx):
+    return (ctx if ctx is not None else default_context())._h
+
+
 class SDNet:
     """mf_load_sdnet / mf_load_sdnet_ex / mf_free_sdnet. activation "tanh" or "gelu";
     embed_channels > 0 adds the conv1d boundary embedding (kernel size embed_kernel)."""
 
     def __init__(self, weights: np.ndarray, width: int, depth: int, activation: str = "tanh",
-                 embed_channels: int = 0, embed_kernel: int = 0):
+                 embed_channels: int = 0, embed_kernel: int = 0, ctx: Context | None = None):
         w = np.ascontiguousarray(weights, dtype=np.float32)
         self.width, self.depth = width, depth
         self._h = C.c_void_p()
         if activation == "tanh" and embed_channels == 0:
-            _check(load().mf_load_sdnet(C.byref(SDNetDesc(width, depth)), w.ctypes.data, C.byref(self._h)))
+            _check(load().mf_load_sdnet(_ctx(ctx), C.byref(SDNetDesc(width, depth)), w.ctypes.data,
+                                        C.byref(self._h)))
         else:
             d = SDNetDescEx(width, depth, ACTIVATION[activation], embed_channels, embed_kernel)
-            _check(load().mf_load_sdnet_ex(C.byref(d), w.ctypes.data, C.byref(self._h)))
+            _check(load().mf_load_sdnet_ex(_ctx(ctx), C.byref(d), w.ctypes.data, C.byref(self._h)))
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:
@@ -187,19 +231,20 @@ class SweepOutcome:
     ms_reduce: float = 0.0
     sweeps_bf16: int = 0
     graph_sweeps: int = 0
+    status: int = 0
 
 
 class Grid:
     """mf_create_grid / mf_grid_* / mf_sweep / mf_residual for one problem."""
 
-    def __init__(self, lx: int, ly: int, bc_ccw: np.ndarray):
+    def __init__(self, lx: int, ly: int, bc_ccw: np.ndarray, ctx: Context | None = None):
         bc = np.ascontiguousarray(bc_ccw, dtype=np.float64)
         self.lx, self.ly = lx, ly
         self.nx, self.ny = 32 * lx + 1, 32 * ly + 1
         if bc.size != 2 * (self.nx - 1) + 2 * (self.ny - 1):
             raise ValueError("bc_ccw has the wrong length")
         self._h = C.c_void_p()
-        _check(load().mf_create_grid(C.byref(GridDesc(lx, ly)), bc.ctypes.data, C.byref(self._h)))
+        _check(load().mf_create_grid(_ctx(ctx), C.byref(GridDesc(lx, ly)), bc.ctypes.data, C.byref(self._h)))
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:
@@ -235,7 +280,8 @@ class Grid:
         res = SweepResult()
         _check(load().mf_sweep(self._h, net._h, C.byref(opts), C.byref(res), _stream_ptr(stream)))
         return SweepOutcome(res.sweeps_done, res.delta, res.kernel_launches, res.mlp_launches,
-                            res.ms_gather, res.ms_mlp, res.ms_reduce, res.sweeps_bf16, res.graph_sweeps)
+                            res.ms_gather, res.ms_mlp, res.ms_reduce, res.sweeps_bf16, res.graph_sweeps,
+                            res.status)
 
     def assemble(self, net: SDNet, precision: str = "fp32", stream=None) -> SweepOutcome:
         """Algorithm 2's final step after centre-line sweeps: every subdomain predicts all
@@ -252,13 +298,13 @@ class Grid:
 class Batch:
     """mf_create_batch / mf_batch_*: many independent problems swept together."""
 
-    def __init__(self, sizes, bcs):
+    def __init__(self, sizes, bcs, ctx: Context | None = None):
         self.n = len(sizes)
         descs = (GridDesc * self.n)(*[GridDesc(int(lx), int(ly)) for lx, ly in sizes])
         bc = np.ascontiguousarray(np.concatenate([np.asarray(b, dtype=np.float64) for b in bcs]))
         self.sizes = [(int(lx), int(ly)) for lx, ly in sizes]
         self._h = C.c_void_p()
-        _check(load().mf_create_batch(self.n, descs, bc.ctypes.data, C.byref(self._h)))
+        _check(load().mf_create_batch(_ctx(ctx), self.n, descs, bc.ctypes.data, C.byref(self._h)))
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:
@@ -293,7 +339,8 @@ class Batch:
         res = SweepResult()
         _check(load().mf_batch_sweep(self._h, net._h, C.byref(opts), C.byref(res), _stream_ptr(stream)))
         return SweepOutcome(res.sweeps_done, res.delta, res.kernel_launches, res.mlp_launches,
-                            res.ms_gather, res.ms_mlp, res.ms_reduce, res.sweeps_bf16, res.graph_sweeps)
+                            res.ms_gather, res.ms_mlp, res.ms_reduce, res.sweeps_bf16, res.graph_sweeps,
+                            res.status)
 
     def residual(self, q, stream=None):
         mx, rms = C.c_double(), C.c_double()
@@ -335,13 +382,13 @@ class Trainer:
     def __init__(self, weights: np.ndarray, width: int, depth: int, precision: str = "bf16",
                  optimizer: str = "lamb", max_functions: int = 1024, max_points: int = 1024,
                  beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-6, weight_decay: float = 0.0,
-                 engine: str = "auto"):
+                 engine: str = "auto", ctx: Context | None = None):
         w = np.ascontiguousarray(weights, dtype=np.float32)
         self.width, self.depth, self.n_params = width, depth, w.size
         d = TrainDesc(width, depth, PREC[precision], OPTIMIZER[optimizer], max_functions, max_points,
                       beta1, beta2, eps, weight_decay, ENGINE[engine])
         self._h = C.c_void_p()
-        _check(load().mf_create_trainer(C.byref(d), w.ctypes.data, C.byref(self._h)))
+        _check(load().mf_create_trainer(_ctx(ctx), C.byref(d), w.ctypes.data, C.byref(self._h)))
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:

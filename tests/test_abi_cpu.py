@@ -36,7 +36,7 @@ def test_exports_every_declared_symbol(m):
     assert sorted(m.EXPORTS) == decl
     for name in decl:
         assert getattr(lib, name) is not None
-    assert lib.mf_version() == 100
+    assert lib.mf_version() == 200
 
 
 @needs_nvcc
@@ -44,13 +44,13 @@ def test_validation_before_gpu_work(m):
     lib = m.load()
     h = C.c_void_p()
     w = np.zeros(100, dtype=np.float32)
-    assert lib.mf_load_sdnet(None, w.ctypes.data, C.byref(h)) == m.MF_ERR_INVALID_ARG
-    assert lib.mf_load_sdnet(C.byref(m.SDNetDesc(96, 4)), w.ctypes.data, C.byref(h)) == m.MF_ERR_INVALID_ARG
+    assert lib.mf_load_sdnet(None, None, w.ctypes.data, C.byref(h)) == m.MF_ERR_INVALID_ARG
+    assert lib.mf_load_sdnet(None, C.byref(m.SDNetDesc(96, 4)), w.ctypes.data, C.byref(h)) == m.MF_ERR_INVALID_ARG
     assert b"width" in lib.mf_last_error()
-    assert lib.mf_load_sdnet(C.byref(m.SDNetDesc(64, 9)), w.ctypes.data, C.byref(h)) == m.MF_ERR_INVALID_ARG
+    assert lib.mf_load_sdnet(None, C.byref(m.SDNetDesc(64, 9)), w.ctypes.data, C.byref(h)) == m.MF_ERR_INVALID_ARG
     bc = np.zeros(1000)
-    assert lib.mf_create_grid(C.byref(m.GridDesc(0, 2)), bc.ctypes.data, C.byref(h)) == m.MF_ERR_INVALID_ARG
-    assert lib.mf_create_grid(C.byref(m.GridDesc(2, 200)), bc.ctypes.data, C.byref(h)) == m.MF_ERR_INVALID_ARG
+    assert lib.mf_create_grid(None, C.byref(m.GridDesc(0, 2)), bc.ctypes.data, C.byref(h)) == m.MF_ERR_INVALID_ARG
+    assert lib.mf_create_grid(None, C.byref(m.GridDesc(2, 200)), bc.ctypes.data, C.byref(h)) == m.MF_ERR_INVALID_ARG
     assert lib.mf_sweep(None, None, None, None, None) == m.MF_ERR_INVALID_ARG
     assert lib.mf_residual(None, None, None, None) == m.MF_ERR_INVALID_ARG
     assert lib.mf_grid_upload(None, None, 0, None) == m.MF_ERR_INVALID_ARG
@@ -88,17 +88,17 @@ def test_every_entry_point_validates_before_gpu_work(m):
     w = np.zeros(200000, dtype=np.float32)
     # SDNet variants: activation, embedding channels and kernel size out of range
     ex = m.SDNetDescEx
-    assert lib.mf_load_sdnet_ex(C.byref(ex(128, 6, 7, 0, 0)), w.ctypes.data, C.byref(h)) == bad
-    assert lib.mf_load_sdnet_ex(C.byref(ex(128, 6, 1, 17, 5)), w.ctypes.data, C.byref(h)) == bad
-    assert lib.mf_load_sdnet_ex(C.byref(ex(128, 6, 1, 8, 4)), w.ctypes.data, C.byref(h)) == bad
-    assert lib.mf_load_sdnet_ex(None, w.ctypes.data, C.byref(h)) == bad
-    assert lib.mf_load_sdnet(C.byref(m.SDNetDesc(64, 4)), None, C.byref(h)) == bad
+    assert lib.mf_load_sdnet_ex(None, C.byref(ex(128, 6, 7, 0, 0)), w.ctypes.data, C.byref(h)) == bad
+    assert lib.mf_load_sdnet_ex(None, C.byref(ex(128, 6, 1, 17, 5)), w.ctypes.data, C.byref(h)) == bad
+    assert lib.mf_load_sdnet_ex(None, C.byref(ex(128, 6, 1, 8, 4)), w.ctypes.data, C.byref(h)) == bad
+    assert lib.mf_load_sdnet_ex(None, None, w.ctypes.data, C.byref(h)) == bad
+    assert lib.mf_load_sdnet(None, C.byref(m.SDNetDesc(64, 4)), None, C.byref(h)) == bad
     # batches: count, descriptor and sizes
     descs = (m.GridDesc * 2)(m.GridDesc(2, 2), m.GridDesc(0, 2))
     bc = np.zeros(10000)
-    assert lib.mf_create_batch(0, descs, bc.ctypes.data, C.byref(h)) == bad
-    assert lib.mf_create_batch(2, None, bc.ctypes.data, C.byref(h)) == bad
-    assert lib.mf_create_batch(2, descs, bc.ctypes.data, C.byref(h)) == bad
+    assert lib.mf_create_batch(None, 0, descs, bc.ctypes.data, C.byref(h)) == bad
+    assert lib.mf_create_batch(None, 2, None, bc.ctypes.data, C.byref(h)) == bad
+    assert lib.mf_create_batch(None, 2, descs, bc.ctypes.data, C.byref(h)) == bad
     nx, ny, off = C.c_int(), C.c_int(), C.c_longlong()
     assert lib.mf_batch_info(None, 0, C.byref(nx), C.byref(ny), C.byref(off)) == bad
     assert lib.mf_batch_upload(None, 0, None, 0, None) == bad
@@ -108,7 +108,7 @@ def test_every_entry_point_validates_before_gpu_work(m):
     # single grids
     assert lib.mf_grid_dims(None, C.byref(nx), C.byref(ny)) == bad
     assert lib.mf_grid_download(None, None, 0, None) == bad
-    assert lib.mf_create_grid(C.byref(m.GridDesc(2, 2)), None, C.byref(h)) == bad
+    assert lib.mf_create_grid(None, C.byref(m.GridDesc(2, 2)), None, C.byref(h)) == bad
     # allocation-free sweep: null grid, size limits
     d = C.c_double()
     assert lib.mf_sweep_noalloc(None, 2, 2, None, 0, 1, C.byref(d), None) == bad
@@ -127,18 +127,18 @@ def test_every_entry_point_validates_before_gpu_work(m):
 
     from paper_2308_14258_gb300 import inputs as I
     tw = I.xavier_sdnet(I.SDNetShape(128, 6), 0)
-    assert lib.mf_create_trainer(None, tw.ctypes.data, C.byref(h)) == bad
-    assert lib.mf_create_trainer(C.byref(desc(width=96)), tw.ctypes.data, C.byref(h)) == bad
-    assert lib.mf_create_trainer(C.byref(desc(depth=9)), tw.ctypes.data, C.byref(h)) == bad
-    assert lib.mf_create_trainer(C.byref(desc(prec=5)), tw.ctypes.data, C.byref(h)) == bad
-    assert lib.mf_create_trainer(C.byref(desc(opt=3)), tw.ctypes.data, C.byref(h)) == bad
-    assert lib.mf_create_trainer(C.byref(desc(P=100)), tw.ctypes.data, C.byref(h)) == bad
-    assert lib.mf_create_trainer(C.byref(desc(F=0)), tw.ctypes.data, C.byref(h)) == bad
-    assert lib.mf_create_trainer(C.byref(desc(F=1 << 20, P=1 << 12)), tw.ctypes.data, C.byref(h)) == bad
-    assert lib.mf_create_trainer(C.byref(desc()), None, C.byref(h)) == bad
+    assert lib.mf_create_trainer(None, None, tw.ctypes.data, C.byref(h)) == bad
+    assert lib.mf_create_trainer(None, C.byref(desc(width=96)), tw.ctypes.data, C.byref(h)) == bad
+    assert lib.mf_create_trainer(None, C.byref(desc(depth=9)), tw.ctypes.data, C.byref(h)) == bad
+    assert lib.mf_create_trainer(None, C.byref(desc(prec=5)), tw.ctypes.data, C.byref(h)) == bad
+    assert lib.mf_create_trainer(None, C.byref(desc(opt=3)), tw.ctypes.data, C.byref(h)) == bad
+    assert lib.mf_create_trainer(None, C.byref(desc(P=100)), tw.ctypes.data, C.byref(h)) == bad
+    assert lib.mf_create_trainer(None, C.byref(desc(F=0)), tw.ctypes.data, C.byref(h)) == bad
+    assert lib.mf_create_trainer(None, C.byref(desc(F=1 << 20, P=1 << 12)), tw.ctypes.data, C.byref(h)) == bad
+    assert lib.mf_create_trainer(None, C.byref(desc()), None, C.byref(h)) == bad
     wn = tw.copy()
     wn[5] = np.nan
-    assert lib.mf_create_trainer(C.byref(desc()), wn.ctypes.data, C.byref(h)) == bad
+    assert lib.mf_create_trainer(None, C.byref(desc()), wn.ctypes.data, C.byref(h)) == bad
     assert b"finite" in lib.mf_last_error() or b"weight" in lib.mf_last_error()
     loss = (C.c_double * 3)()
     assert lib.mf_train_grad(None, 1, 64, 64, None, None, None, None, loss, None) == bad
@@ -146,3 +146,44 @@ def test_every_entry_point_validates_before_gpu_work(m):
     assert lib.mf_trainer_set_weights(None, None, 0, None) == bad
     assert lib.mf_trainer_get_weights(None, None, 0, None) == bad
     assert lib.mf_trainer_get_grads(None, None, 0, None) == bad
+
+
+@needs_nvcc
+def test_context_calls_validate_and_report_no_device(m):
+    """mf_ctx_create rejects a bad index or a null result pointer before touching CUDA;
+    on this machine (no GPU) a valid request reports MF_ERR_CUDA. The creating calls
+    check their descriptors before they look at the context, and a null context is
+    rejected by name."""
+    import torch
+    lib = m.load()
+    bad = m.MF_ERR_INVALID_ARG
+    c = C.c_void_p()
+    assert lib.mf_ctx_create(-1, C.byref(c)) == bad
+    assert lib.mf_ctx_create(0, None) == bad
+    assert lib.mf_ctx_create(10**6, C.byref(c)) == bad
+    assert lib.mf_ctx_device(None, None, None) == bad
+    assert lib.mf_ctx_destroy(None) == m.MF_OK
+    if not torch.cuda.is_available():
+        assert lib.mf_ctx_create(0, C.byref(c)) == m.MF_ERR_CUDA
+        assert not c.value
+    h = C.c_void_p()
+    w = np.zeros(200000, dtype=np.float32)
+    assert lib.mf_load_sdnet(None, C.byref(m.SDNetDesc(96, 4)), w.ctypes.data, C.byref(h)) == bad
+    assert b"width" in lib.mf_last_error()
+    assert lib.mf_load_sdnet(None, C.byref(m.SDNetDesc(64, 4)), w.ctypes.data, C.byref(h)) == bad
+    assert b"context" in lib.mf_last_error()
+    bc = np.zeros(1000)
+    assert lib.mf_create_grid(None, C.byref(m.GridDesc(2, 2)), bc.ctypes.data, C.byref(h)) == bad
+    assert b"context" in lib.mf_last_error()
+    descs = (m.GridDesc * 1)(m.GridDesc(2, 2))
+    assert lib.mf_create_batch(None, 1, descs, bc.ctypes.data, C.byref(h)) == bad
+    assert b"context" in lib.mf_last_error()
+    from paper_2308_14258_gb300 import inputs as I
+    tw = I.xavier_sdnet(I.SDNetShape(128, 6), 0)
+    td = m.TrainDesc(128, 6, 1, 1, 4, 128, 0.9, 0.999, 1e-6, 0.0, 0)
+    assert lib.mf_create_trainer(None, C.byref(td), tw.ctypes.data, C.byref(h)) == bad
+    assert b"context" in lib.mf_last_error()
+    wn = tw.copy()
+    wn[7] = np.inf
+    assert lib.mf_create_trainer(None, C.byref(td), wn.ctypes.data, C.byref(h)) == bad
+    assert b"finite" in lib.mf_last_error()

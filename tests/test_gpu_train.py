@@ -192,6 +192,30 @@ def test_autograd_function(m):
     assert e2 <= 1e-4
 
 
+def test_autograd_function_fused_engine(m):
+    """pinn_loss on the fused tensor-core engine (BF16, width 128, depth 6: the
+    default engine for the training workload's network) against the FP64 oracle."""
+    import torch
+    width, depth = 128, 6
+    w = I.xavier_sdnet(I.SDNetShape(width, depth), 4, bias_scale=0.1)
+    Gn, Xcn, Xbn, Ybn = batch(4, 256, 128, 6)
+    G, Xc, Xb, Yb = to_dev(Gn, Xcn, Xbn, Ybn)
+    tr = m.Trainer(w, width, depth, "bf16", "sgd", max_functions=4, max_points=256)
+    wt = torch.from_numpy(w).cuda().requires_grad_(True)
+    loss = m.pinn_loss(wt, tr, G, Xc, Xb, Yb)
+    (2.0 * loss).backward()
+    (lt, _, _), gref = oracle(w, width, depth, Gn, Xcn, Xbn, Ybn)
+    assert abs(float(loss.detach()) - lt) <= TOL["bf16"] * lt
+    e2, _ = grad_errors(wt.grad.cpu().numpy() / 2.0, gref)
+    assert e2 <= TOL["bf16"]
+    # a second evaluation at moved weights goes through the same engine
+    with torch.no_grad():
+        w2 = wt - 1e-2 * wt.grad
+    loss2 = m.pinn_loss(w2.requires_grad_(True), tr, G, Xc, Xb, Yb)
+    (lt2, _, _), _ = oracle(w2.detach().cpu().numpy(), width, depth, Gn, Xcn, Xbn, Ybn)
+    assert abs(float(loss2.detach()) - lt2) <= TOL["bf16"] * lt2
+
+
 def test_invalid_arguments(m):
     import torch
     w = I.xavier_sdnet(I.SDNetShape(64, 3), 1)

@@ -154,4 +154,4 @@ def test_invalid_variant_options(m):
     d = m.SDNetDescEx(64, 3, 2, 0, 0)     # unknown activation code
     import ctypes as C
     h = C.c_void_p()
-    assert m.load().mf_load_sdnet_ex(C.byref(d), w.ctypes.data, C.byref(h)) == m.MF_ERR_INVALID_ARG
+    assert m.load().mf_load_sdnet_ex(m.default_context()._h, C.byref(d), w.ctypes.data, C.byref(h)) == m.MF_ERR_INVALID_ARG
