@@ -301,12 +301,20 @@ def train_tile_traffic(F, Nc, Nb, NH):
 
 
 def measure_converged(m, I, torch, np, net, p, weights, stream, rank, with_oracle):
-    """Algorithm 2's loop to convergence on the benchmark grid from the zero interior:
-    FP32 sweeps alone to delta < 1e-6; MF_PREC_MIXED (BF16 sweeps until delta < 1e-2,
-    then FP32 refinement sweeps to delta < 1e-6); BF16 sweeps alone (to delta < 1e-6 or
-    60 sweeps). Reports sweeps, device time and the converged fields' differences."""
+    """Algorithm 2's loop to convergence on the benchmark grid from the zero interior.
+
+    * fp32: FP32 sweeps alone until delta < 1e-5;
+    * mixed: MF_PREC_MIXED, BF16 sweeps until delta < 1e-2 or until a BF16 sweep stops
+      reducing delta (its rounding floor, about 1.2e-2 on this grid), then FP32 sweeps
+      until delta < 1e-5;
+    * bf16: BF16 sweeps alone (40, well past their plateau).
+    The stop value 1e-5 lies above the FP32 rounding floor of delta on this grid
+    (about 1.5e-6). Each field is compared with the FP32 fixed point (FP32 sweeps
+    continued to 250 in all, where delta sits at its floor), as max |u - u_ref| /
+    max |u_ref|; the target is 1e-3."""
     res, fields = {}, {}
-    runs = (("fp32", "fp32", 200, 1e-6, 0.0), ("mixed", "mixed", 200, 1e-6, 1e-2), ("bf16", "bf16", 60, 1e-6, 0.0))
+    runs = (("fp32", "fp32", 400, 1e-5, 0.0), ("mixed", "mixed", 400, 1e-5, 1e-2), ("bf16", "bf16", 40, 0.0, 0.0))
+    ref_grid = None
     for name, prec, n, eps, eps_c in runs:
         g = m.Grid(p.lx, p.ly, p.bc)
         torch.cuda.synchronize()
@@ -320,14 +328,22 @@ def measure_converged(m, I, torch, np, net, p, weights, stream, rank, with_oracl
         res[name] = {"sweeps": o.sweeps_done, "sweeps_bf16": o.sweeps_bf16,
                      "sweeps_fp32": o.sweeps_done - o.sweeps_bf16, "delta": o.delta,
                      "ms": e0.elapsed_time(e1)}
-        del g
-    ref = fields["fp32"]
+        if name == "fp32":
+            ref_grid = g
+        else:
+            del g
+    # the FP32 fixed point: continue the FP32 run until delta has reached its floor
+    o = ref_grid.sweep(net, 250 - res["fp32"]["sweeps"], "M", "fp32", check_every=10, stream=stream)
+    ref = ref_grid.download(stream=stream).astype(np.float64)
+    del ref_grid
     scale = float(np.abs(ref).max())
-    for name in ("mixed", "bf16"):
-        res[name]["max_rel_diff_vs_fp32"] = float(np.abs(fields[name] - ref).max() / scale)
+    res["reference"] = {"what": "FP32 sweeps continued to 250 from the zero interior", "delta": o.delta}
+    for name in ("fp32", "mixed", "bf16"):
+        res[name]["max_rel_err_vs_fp32_fixed_point"] = float(np.abs(fields[name] - ref).max() / scale)
     res["speedup_mixed_over_fp32"] = res["fp32"]["ms"] / res["mixed"]["ms"]
     res["workload"] = "large_L64 grid from the zero interior, SDNet 6x128 (seed 2), multiplicative schedule"
-    res["stop"] = "delta < 1e-6 (Algorithm 2); MIXED switches to FP32 at delta < 1e-2"
+    res["stop"] = ("delta < 1e-5 (Algorithm 2); MIXED switches from BF16 to FP32 at delta < 1e-2 or when a BF16 "
+                   "sweep no longer reduces delta")
     if with_oracle and rank == 0:
         # fixed-point residual of the MIXED field under the FP64 oracle's map: at a
         # multiplicative fixed point, each last-colour subdomain's prediction from the
@@ -393,7 +409,7 @@ def measure_train(args, m, I, torch, np, stream, rank):
                          "hbm_frac_of_step": traffic / (t / kt) / (peaks.get("hbm_gbs") * 1e9)}
     del tr
     torch.cuda.empty_cache()
-    # FP32 mode on the same batch (cuBLAS FP32 GEMMs), fewer steps
+    # FP32 mode on the same batch (the GEMM engine's FP32 layer GEMMs), fewer steps
     tr = m.Trainer(I.xavier_sdnet(I.SDNetShape(H, NH + 1), 4), H, NH + 1, "fp32", "lamb",
                    max_functions=F, max_points=Nc)
     tr.step(*tdev, 1e-3, stream=stream)
@@ -405,7 +421,7 @@ def measure_train(args, m, I, torch, np, stream, rank):
     e1.synchronize()
     t32 = e0.elapsed_time(e1) / 1e3
     train["fp32"] = {"value": k32t / t32, "unit": "train steps/s", "ms_per_step": 1e3 * t32 / k32t,
-                     "engine": "cuBLAS FP32 layer GEMMs"}
+                     "engine": "GEMM engine: FP32 SIMT layer GEMMs + elementwise kernels"}
     del tr
     torch.cuda.empty_cache()
     tr = m.Trainer(I.xavier_sdnet(I.SDNetShape(H, NH + 1), 4), H, NH + 1, "bf16", "lamb",
@@ -418,7 +434,7 @@ def measure_train(args, m, I, torch, np, stream, rank):
     e1.synchronize()
     tg = e0.elapsed_time(e1) / 1e3
     train["bf16_gemm_engine"] = {"value": k32t / tg, "unit": "train steps/s", "ms_per_step": 1e3 * tg / k32t,
-                                 "engine": "cuBLAS BF16 layer GEMMs + elementwise kernels"}
+                                 "engine": "GEMM engine: BF16 operands, FP32 SIMT layer GEMMs + elementwise kernels"}
     del tr, tdev
     torch.cuda.empty_cache()
     # BF16 gradient against the FP64 oracle on 4 sampled functions (full Nc)

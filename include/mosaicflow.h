@@ -51,7 +51,7 @@ typedef int mf_status;
 
 #define MF_PREC_FP32 0  /* FP32 weights and activations, SIMT FMA, accurate tanh */
 #define MF_PREC_BF16 1  /* BF16 weights/activations on tcgen05 tensor cores, FP32 accumulate */
-#define MF_PREC_MIXED 2 /* BF16 sweeps until delta < eps_coarse, then FP32 refinement sweeps */
+#define MF_PREC_MIXED 2 /* BF16 sweeps until delta < eps_coarse or stalls, then FP32 refinement */
 
 #define MF_SCHEDULE_MULTIPLICATIVE 0 /* colours 0..3 in turn, each reads the latest grid */
 #define MF_SCHEDULE_ADDITIVE 1       /* all colours read the old grid; overlaps averaged */
@@ -201,8 +201,9 @@ mf_status mf_grid_download(const mf_grid* grid, float* dst, int dst_on_device, v
  * synchronises `stream` after each checked sweep and stops once delta < eps. The call
  * always synchronises `stream` before returning to fill `result` (which may be NULL).
  * MF_PREC_MIXED is iterative refinement of the converged field: BF16 sweeps (checked
- * every sweep) until delta < eps_coarse, then FP32 sweeps until delta < eps, both
- * within the n_sweeps budget.
+ * every sweep) until delta < eps_coarse or until a BF16 sweep fails to reduce delta
+ * (delta_k >= delta_{k-1}: the BF16 iteration has reached the floor its rounding
+ * allows), then FP32 sweeps until delta < eps, all within the n_sweeps budget.
  * MF_QUERY_CENTRE is the interface-only iteration of Algorithm 2: a subdomain's only
  * interior points that other subdomains read are its centre lines (x or y on the
  * 1/2 lattice), so each sweep predicts just those 61 points and leaves the others as
@@ -291,7 +292,7 @@ mf_status mf_check_wait_timeout(double limit_ms, int* waits_gave_up);
 #define MF_OPT_LAMB 1 /* LAMB (You et al., ICLR 2020): Adam moments, trust ratio ||w||/||r|| per tensor */
 
 #define MF_TRAIN_ENGINE_AUTO 0 /* fused tensor-core layer kernels for BF16 at width 128, else GEMM */
-#define MF_TRAIN_ENGINE_GEMM 1 /* layer GEMMs through cuBLAS, elementwise steps in own kernels */
+#define MF_TRAIN_ENGINE_GEMM 1 /* layer GEMMs and elementwise steps as separate kernels (any width/precision) */
 
 typedef struct mf_trainer mf_trainer; /* device weights, optimiser state and training scratch */
 
@@ -313,7 +314,8 @@ typedef struct {
  * chunk of functions is processed at a time, so max_functions bounds memory without
  * bounding the batch. The fused engine (BF16, width 128) runs each layer as one
  * tensor-core kernel that recomputes pre-activations in the backward pass instead of
- * storing them; the GEMM engine stores them and calls cuBLAS for the layer GEMMs.
+ * storing them; the GEMM engine stores them and runs each layer GEMM as a separate
+ * FP32-accumulating kernel.
  * Errors: MF_ERR_INVALID_ARG (null pointer, unsupported option, non-finite weight,
  * 4 * max_functions * max_points above 2^31 - 1), MF_ERR_OUT_OF_MEMORY, MF_ERR_CUDA.
  * Synchronous. */

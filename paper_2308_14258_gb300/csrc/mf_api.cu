@@ -424,6 +424,7 @@ mf_status sweep_impl(mf_grid* g, const mf_sdnet* net, const mf_sweep_opts* o, mf
   bool checked = false;
   const bool mixed = o->precision == MF_PREC_MIXED;
   bool coarse = mixed;  // mixed precision: still in the BF16 phase
+  double d_prev = INFINITY;  // delta of the previous BF16 sweep
   for (int k = 0; k < o->n_sweeps; ++k) {
     const bool check = coarse || ((k + 1) % o->check_every == 0) || (k + 1 == o->n_sweeps);
     const bool bf16 = mixed ? coarse : (o->precision == MF_PREC_BF16);
@@ -468,7 +469,10 @@ mf_status sweep_impl(mf_grid* g, const mf_sdnet* net, const mf_sweep_opts* o, mf
         if (res) { res->sweeps_done = done; res->delta = d; res->sweeps_bf16 = done_bf16; }
         if (!std::isfinite(d)) return fail(MF_ERR_DIVERGED, "mf_sweep: delta is not finite");
         if (coarse) {
-          if (d < o->eps_coarse) coarse = false;  // switch to FP32 refinement
+          // switch to FP32 refinement once delta is small enough, or once a BF16 sweep
+          // no longer reduces it (the BF16 iteration has reached its rounding floor)
+          if (d < o->eps_coarse || d >= d_prev) coarse = false;
+          d_prev = d;
         } else if (d < o->eps) {
           break;
         }

@@ -26,11 +26,11 @@
 // Two engines run these formulas. The fused engine (BF16, width 128; mf_train_tc.cu)
 // keeps each layer's GEMM and its Taylor-mode epilogue in one tensor-core kernel and
 // moves only BF16 activation and gradient tiles through HBM. The GEMM engine (FP32 or
-// BF16, any width) runs the layer GEMMs (stacked channels x H times H x H, and the
-// H x H weight gradients) as plain cuBLAS GEMMs with FP32 accumulation and every other
-// step in the kernels below. Reductions use fixed-order block partials in both, so
-// results do not depend on timing.
-#include <cublas_v2.h>
+// BF16, any width) runs the layer products (stacked channels x H times H x H, and the
+// H x H weight gradients) as separate FP32-accumulating kernels (mf_train_gemm.cu) and
+// every other step in the kernels below. The first layer's boundary term and its
+// gradient are the small products of mf_train_gemm.cu in both engines. Reductions use
+// fixed-order block partials throughout, so results do not depend on timing.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -42,6 +42,7 @@
 
 #include "../../include/mosaicflow.h"
 #include "mf_internal.cuh"
+#include "mf_train_gemm.cuh"
 #include "mf_train_tc.cuh"
 
 namespace mf {
@@ -386,7 +387,8 @@ struct mf_trainer {
   double* h_loss = nullptr;        // pinned [3]
   unsigned long long* ranges = nullptr;  // LAMB tensor ranges
   int n_groups = 0;
-  cublasHandle_t cublas = nullptr;
+  float* wpart = nullptr;          // GEMM engine: per-block H x H weight-gradient partials
+  int wblocks = 0;                 // their count
   // fused engine
   bool fused = false;
   void* timg = nullptr;            // [NH] x (W image, W^T image), BF16 swizzled
@@ -409,9 +411,6 @@ mf_status tcuda(cudaError_t e, const char* what) {
   return tfail(e == cudaErrorMemoryAllocation ? MF_ERR_OUT_OF_MEMORY : MF_ERR_CUDA,
                std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
 }
-mf_status tblas(cublasStatus_t s, const char* what) {
-  return tfail(MF_ERR_CUDA, std::string(what) + ": cuBLAS status " + std::to_string((int)s));
-}
 #define TR_CUDA(call, what)                          \
   do {                                               \
     cudaError_t e_ = (call);                         \
@@ -420,46 +419,31 @@ mf_status tblas(cublasStatus_t s, const char* what) {
 #define TR_ON_DEVICE(dev, what)   \
   mf::DeviceGuard guard_((dev));  \
   if (guard_.err != cudaSuccess) return tcuda(guard_.err, what)
-#define TR_BLAS(call, what)                                     \
-  do {                                                          \
-    cublasStatus_t s_ = (call);                                 \
-    if (s_ != CUBLAS_STATUS_SUCCESS) return tblas(s_, what);    \
-  } while (0)
 
 size_t esize(const mf_trainer* t) { return t->precision == MF_PREC_BF16 ? 2 : 4; }
-cudaDataType_t etype(const mf_trainer* t) { return t->precision == MF_PREC_BF16 ? CUDA_R_16BF : CUDA_R_32F; }
+int bf16(const mf_trainer* t) { return t->precision == MF_PREC_BF16 ? 1 : 0; }
 
-// Row-major GEMMs through column-major cuBLAS (see the file comment for the products).
-// Z[rows][H] = X[rows][H] * W^T   (W row-major [out][in])
-cublasStatus_t gemm_fwd(mf_trainer* t, const void* W, const void* X, float* Zo, long rows) {
-  const float one = 1.f, zero = 0.f;
-  return cublasGemmEx(t->cublas, CUBLAS_OP_T, CUBLAS_OP_N, t->H, (int)rows, t->H, &one, W, etype(t), t->H, X,
-                      etype(t), t->H, &zero, Zo, CUDA_R_32F, t->H, CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
+// Row-major layer products of the GEMM engine (see the file comment):
+// Z[rows][H] = X[rows][H] W^T   (W row-major [out][in])
+cudaError_t gemm_fwd(mf_trainer* t, const void* W, const void* X, float* Zo, long rows, cudaStream_t st) {
+  return mf::train_row_gemm(bf16(t), t->H, X, W, 1, rows, Zo, st);
 }
-// gX[rows][H] = gZ[rows][H] * W
-cublasStatus_t gemm_bwd_data(mf_trainer* t, const void* W, const void* gZ, float* gX, long rows) {
-  const float one = 1.f, zero = 0.f;
-  return cublasGemmEx(t->cublas, CUBLAS_OP_N, CUBLAS_OP_N, t->H, (int)rows, t->H, &one, W, etype(t), t->H, gZ,
-                      etype(t), t->H, &zero, gX, CUDA_R_32F, t->H, CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
+// gX[rows][H] = gZ[rows][H] W
+cudaError_t gemm_bwd_data(mf_trainer* t, const void* W, const void* gZ, float* gX, long rows, cudaStream_t st) {
+  return mf::train_row_gemm(bf16(t), t->H, gZ, W, 0, rows, gX, st);
 }
-// gW[out][in] += gZ^T X  over all rows
-cublasStatus_t gemm_bwd_weight(mf_trainer* t, const void* X, const void* gZ, float* gW, long rows) {
-  const float one = 1.f;
-  return cublasGemmEx(t->cublas, CUBLAS_OP_N, CUBLAS_OP_T, t->H, t->H, (int)rows, &one, X, etype(t), t->H, gZ,
-                      etype(t), t->H, &one, gW, CUDA_R_32F, t->H, CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
+// gW[out][in] += gZ^T X over all rows
+cudaError_t gemm_bwd_weight(mf_trainer* t, const void* X, const void* gZ, float* gW, long rows, cudaStream_t st) {
+  return mf::train_weight_grad(bf16(t), t->H, gZ, X, rows, t->wpart, t->wblocks, gW, st);
 }
 
 // First layer, boundary block, FP32: Bf[f][j] = sum_k W0[j][k] G[f][k] (k < 128).
-cublasStatus_t gemm_boundary(mf_trainer* t, const float* G, int F) {
-  const float one = 1.f, zero = 0.f;
-  return cublasSgemm(t->cublas, CUBLAS_OP_T, CUBLAS_OP_N, t->H, F, kNB, &one, t->w, kNB + 2, G, kNB, &zero, t->Bf,
-                     t->H);
+cudaError_t gemm_boundary(mf_trainer* t, const float* G, int F, cudaStream_t st) {
+  return mf::train_boundary_fwd(t->w, G, F, t->H, t->Bf, st);
 }
 // First layer, boundary-block gradient, FP32: gW0[j][k] += sum_f S[f][j] G[f][k].
-cublasStatus_t gemm_boundary_grad(mf_trainer* t, const float* G, int F) {
-  const float one = 1.f;
-  return cublasSgemm(t->cublas, CUBLAS_OP_N, CUBLAS_OP_T, kNB, t->H, F, &one, G, kNB, t->S, t->H, &one, t->g,
-                     kNB + 2);
+cudaError_t gemm_boundary_grad(mf_trainer* t, const float* G, int F, cudaStream_t st) {
+  return mf::train_boundary_grad(t->S, G, F, t->H, t->g, st);
 }
 
 // One forward + backward pass over F functions with n points each (C = 1: data points,
@@ -475,7 +459,7 @@ mf_status run_pass(mf_trainer* t, int C, int F, int n, const float* G, const flo
   const int ncol = (H + 31) / 32;
   T* wq = static_cast<T*>(t->wq);
   // forward
-  TR_BLAS(gemm_boundary(t, G, F), "train: boundary GEMM");
+  TR_CUDA(gemm_boundary(t, G, F, st), "train: boundary GEMM");
   if (C == 4)
     first_fwd_kernel<T, 4><<<nblk, H, 0, st>>>(t->Bf, t->w, t->w + t->off_b0, X, n, R, H, static_cast<T*>(t->A[0]),
                                                t->a[0]);
@@ -484,7 +468,7 @@ mf_status run_pass(mf_trainer* t, int C, int F, int n, const float* G, const flo
                                                t->a[0]);
   TR_CUDA(cudaGetLastError(), "train: first layer");
   for (int l = 1; l <= NH; ++l) {
-    TR_BLAS(gemm_fwd(t, wq + (size_t)(l - 1) * H * H, t->A[l - 1], t->Z[l], (long)C * R), "train: forward GEMM");
+    TR_CUDA(gemm_fwd(t, wq + (size_t)(l - 1) * H * H, t->A[l - 1], t->Z[l], (long)C * R, st), "train: forward GEMM");
     const float* bl = t->w + t->offb[l];
     if (C == 4)
       act_fwd_kernel<T, 4><<<nblk, H, 0, st>>>(t->Z[l], bl, R, H, static_cast<T*>(t->A[l]), t->a[l]);
@@ -514,8 +498,8 @@ mf_status run_pass(mf_trainer* t, int C, int F, int n, const float* G, const flo
       act_bwd_kernel<T, 1><<<nblk, H, 0, st>>>(t->gA, t->Z[l], t->a[l], R, H, static_cast<T*>(t->gZ), t->part);
     TR_CUDA(cudaGetLastError(), "train: activation backward");
     colsum_kernel<<<ncol, 1024, 0, st>>>(t->part, nblk, H, H, t->g + t->offb[l], 1);
-    TR_BLAS(gemm_bwd_weight(t, t->A[l - 1], t->gZ, t->g + t->offW[l], (long)C * R), "train: weight GEMM");
-    TR_BLAS(gemm_bwd_data(t, wq + (size_t)(l - 1) * H * H, t->gZ, t->gA, (long)C * R), "train: data GEMM");
+    TR_CUDA(gemm_bwd_weight(t, t->A[l - 1], t->gZ, t->g + t->offW[l], (long)C * R, st), "train: weight GEMM");
+    TR_CUDA(gemm_bwd_data(t, wq + (size_t)(l - 1) * H * H, t->gZ, t->gA, (long)C * R, st), "train: data GEMM");
   }
   // first layer: W2 columns and b0 from all rows, W1 through per-function sums
   if (C == 4)
@@ -527,7 +511,7 @@ mf_status run_pass(mf_trainer* t, int C, int F, int n, const float* G, const flo
   add_w2_b0_kernel<<<1, H, 0, st>>>(t->sums, H, t->g, t->g + t->off_b0);
   per_function_sum_kernel<<<F, H, 0, st>>>(t->part, n / kRB, H, t->S, 0);
   TR_CUDA(cudaGetLastError(), "train: first layer gradients");
-  TR_BLAS(gemm_boundary_grad(t, G, F), "train: boundary gradient GEMM");
+  TR_CUDA(gemm_boundary_grad(t, G, F, st), "train: boundary gradient GEMM");
   return MF_OK;
 }
 
@@ -560,7 +544,7 @@ mf_status run_chunk_fused(mf_trainer* t, int F, const float* G, const FusedTerm 
   // per-32-point first-layer partial sums of each term, one after the other
   float* part32[2] = {t->part, t->part + (size_t)(R[0] / 32) * 3 * H};
   int grid_used = 0;
-  TR_BLAS(gemm_boundary(t, G, F), "train: boundary GEMM");
+  TR_CUDA(gemm_boundary(t, G, F, st), "train: boundary GEMM");
   for (int k = 0; k < 2; ++k)
     TR_CUDA(mf::tc_first_fwd(t->Bf, t->w, t->w + t->off_b0, term[k].X, term[k].n, R[k], k == 0 ? 4 : 1,
                              static_cast<uint8_t*>(t->A[0]) + (k == 0 ? 0 : (size_t)nt[0] * tile), st),
@@ -657,7 +641,7 @@ mf_status run_chunk_fused(mf_trainer* t, int F, const float* G, const FusedTerm 
     per_function_sum_kernel<<<F, H, 0, st>>>(part, term[k].n / group, H, t->S, k);
   }
   TR_CUDA(cudaGetLastError(), "train: first layer gradients");
-  TR_BLAS(gemm_boundary_grad(t, G, F), "train: boundary gradient GEMM");
+  TR_CUDA(gemm_boundary_grad(t, G, F, st), "train: boundary gradient GEMM");
   return MF_OK;
 }
 
@@ -730,7 +714,7 @@ extern "C" {
 mf_status mf_destroy_trainer(mf_trainer* t) {
   if (!t) return MF_OK;
   mf::DeviceGuard guard(t->device);
-  if (t->cublas) cublasDestroy(t->cublas);
+  cudaFree(t->wpart);
   for (void* p : t->A) cudaFree(p);
   for (float* p : t->Z) cudaFree(p);
   for (float* p : t->a) cudaFree(p);
@@ -838,6 +822,10 @@ mf_status mf_create_trainer(mf_ctx* ctx, const mf_train_desc* d, const float* we
   alloc((void**)&t->part, std::max(nblk_max * 3 * H * 4 + nblk_max * 4, (2 * t->Rmax / 32 + 2) * 3 * H * 4));
   alloc((void**)&t->sums, 3 * H * 4);
   alloc((void**)&t->lpart, nblk_max * 8);
+  if (!t->fused) {
+    t->wblocks = mf::train_wgrad_blocks();
+    alloc((void**)&t->wpart, (size_t)t->wblocks * HH * 4);
+  }
   alloc((void**)&t->loss, 4 * 8);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&t->h_loss, 4 * 8);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&t->h_status, sizeof(int));
@@ -863,11 +851,6 @@ mf_status mf_create_trainer(mf_ctx* ctx, const mf_train_desc* d, const float* we
     mf_destroy_trainer(t);
     return tcuda(e, "mf_create_trainer");
   }
-  if (cublasCreate(&t->cublas) != CUBLAS_STATUS_SUCCESS) {
-    mf_destroy_trainer(t);
-    return tfail(MF_ERR_CUDA, "mf_create_trainer: cublasCreate failed");
-  }
-  cublasSetMathMode(t->cublas, CUBLAS_DEFAULT_MATH);  // FP32 mode stays FP32 (no TF32)
   mf_status s = refresh_gemm_weights(t, nullptr);
   if (s == MF_OK && cudaDeviceSynchronize() != cudaSuccess) s = tcuda(cudaGetLastError(), "mf_create_trainer");
   if (s != MF_OK) {
@@ -912,7 +895,6 @@ mf_status mf_train_grad(mf_trainer* t, int F, int Nc, int Nb, const float* G, co
   if (s != MF_OK) return s;
   TR_ON_DEVICE(t->device, "mf_train_grad");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  TR_BLAS(cublasSetStream(t->cublas, st), "mf_train_grad: cublasSetStream");
   TR_CUDA(cudaMemsetAsync(t->g, 0, t->n_params * 4, st), "mf_train_grad: zero grads");
   TR_CUDA(cudaMemsetAsync(t->loss, 0, 3 * sizeof(double), st), "mf_train_grad: zero loss");
   TR_CUDA(cudaMemsetAsync(t->status, 0, sizeof(int), st), "mf_train_grad: reset status");

@@ -1,7 +1,7 @@
 """ctypes binding of libmosaicflow.so: the mf_* calls with Python argument marshalling.
 
-Every step of the sweep runs in the library's sm_103a kernels, and every step of the
-training step in its kernels plus the cuBLAS layer GEMMs it calls; this module only
+Every step of the sweep and of the training step runs in the library's own sm_103a
+kernels (no other CUDA library is linked); this module only
 converts arguments (NumPy arrays, torch tensors, streams) to the C ABI and raises
 MFError on a non-zero status. There is no CPU fallback: if the library is missing or cannot be
 loaded, loading raises.
