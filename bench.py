@@ -562,6 +562,34 @@ def main():
                    "unit": UNIT, "evals_per_sweep": b_evals, **res}
         del bt
 
+    # launch modes of a sweep (per colour, graph replay, one whole-sweep cooperative
+    # launch, autotuned) on the large grid and on a batch of 256 small problems (L = 2)
+    modes = None
+    if args.L == 64 and not args.no_batched:
+        def per_sweep(fn, k):
+            fn()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(k):
+                fn()
+            e1.record(stream)
+            e1.synchronize()
+            return e0.elapsed_time(e1) / k
+        modes = {"unit": "ms per sweep", "large_L64": {}, "small_256xL2": {}}
+        for mode in ("per_colour", "sweep"):
+            modes["large_L64"][mode] = per_sweep(
+                lambda: grid.sweep(net, 1, "M", "bf16", stream=stream, launch_mode=mode), 10)
+        sizes = [(2, 2)] * 256
+        sb = m.Batch(sizes, [I.bc_values(2, 2, I.mode_field(I.mode_coeffs(1000 + q), 2, 2)) for q in range(256)])
+        for mode in ("per_colour", "graph", "sweep", "auto"):
+            r = sb.sweep(net, 2, "bf16", launch_mode=mode, stream=stream)
+            modes["small_256xL2"][mode] = per_sweep(
+                lambda: sb.sweep(net, 20, "bf16", launch_mode=mode, check_every=20, stream=stream), 3) / 20
+            if mode == "auto":
+                modes["small_256xL2"]["auto_choice"] = {"launch_mode": r.launch_mode, "gather_block": r.gather_block}
+        del sb
+
     # the paper's SDNet variant (Section 3.1): conv1d boundary embedding (8 channels,
     # kernel 5) + GELU, 6 x 128, on the same grid
     variant = None
@@ -657,6 +685,7 @@ def main():
         "train": train,
         "variant_conv1d_gelu": variant,
         "converged": converged,
+        "launch_modes": modes,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
         "gpu_launches": launches,
         "roofline": {"kernel": "mlp_bf16_kernel<128,5,tanh>", "bound": "tensor", "achieved": achieved,

@@ -59,6 +59,16 @@ typedef int mf_status;
 #define MF_QUERY_FULL 0   /* predict all 961 interior points of every subdomain */
 #define MF_QUERY_CENTRE 1 /* predict only the 61 centre-cross points (interfaces) */
 
+/* How a multiplicative sweep is launched (mf_sweep_opts.launch_mode). */
+#define MF_LAUNCH_PER_COLOUR 0 /* per colour one boundary-gather launch and one SDNet launch */
+#define MF_LAUNCH_GRAPH 1      /* mf_batch_sweep: the same launches, unchecked sweeps replayed from a CUDA graph */
+#define MF_LAUNCH_SWEEP 2      /* one cooperative launch per sweep: gather, SDNet and scatter of every colour,
+                                  colours separated by device-wide barriers (BF16 sweeps; SDNets without a
+                                  boundary embedding) */
+#define MF_LAUNCH_AUTO 3       /* mf_batch_sweep: time the launch modes and gather block sizes on a copy of
+                                  the batch at the first call for this SDNet, precision and query; keep the
+                                  fastest */
+
 typedef struct mf_ctx mf_ctx;     /* one CUDA device and the library's set-up on it */
 typedef struct mf_sdnet mf_sdnet; /* device-resident SDNet weights (both precisions) */
 typedef struct mf_grid mf_grid;   /* device grid of one problem plus its sweep scratch */
@@ -84,7 +94,7 @@ typedef struct {
   int profile;     /* nonzero: time each phase with CUDA events recorded on `stream` */
   double eps_coarse; /* MF_PREC_MIXED: switch from BF16 to FP32 once delta < eps_coarse (> 0) */
   int query;         /* MF_QUERY_FULL, or MF_QUERY_CENTRE (multiplicative schedule only) */
-  int graph;         /* mf_batch_sweep: replay unchecked sweeps from a captured CUDA graph */
+  int launch_mode;   /* MF_LAUNCH_*; mf_sweep takes MF_LAUNCH_PER_COLOUR or MF_LAUNCH_SWEEP */
 } mf_sweep_opts;
 
 typedef struct {
@@ -98,6 +108,8 @@ typedef struct {
   int sweeps_bf16;     /* of sweeps_done, sweeps run on the BF16 path */
   int graph_sweeps;    /* mf_batch_sweep: sweeps replayed from the captured graph */
   mf_status status;    /* the call's own return value (MF_OK, MF_ERR_DIVERGED, ...) */
+  int launch_mode;     /* the MF_LAUNCH_* mode that ran (the autotuner's choice under MF_LAUNCH_AUTO) */
+  int gather_block;    /* subdomains per block of the boundary-gather launches (4, 8 or 16) */
 } mf_sweep_result;
 
 #define MF_ACT_TANH 0 /* tanh activations (the default network) */
@@ -204,6 +216,10 @@ mf_status mf_grid_download(const mf_grid* grid, float* dst, int dst_on_device, v
  * every sweep) until delta < eps_coarse or until a BF16 sweep fails to reduce delta
  * (delta_k >= delta_{k-1}: the BF16 iteration has reached the floor its rounding
  * allows), then FP32 sweeps until delta < eps, all within the n_sweeps budget.
+ * Launch modes: MF_LAUNCH_PER_COLOUR, or MF_LAUNCH_SWEEP (one cooperative launch per
+ * BF16 sweep of all colours; the multiplicative schedule with all colours, SDNets
+ * without a boundary embedding, else MF_ERR_UNSUPPORTED; FP32 sweeps of MF_PREC_MIXED
+ * keep the per-colour launches); other modes return MF_ERR_INVALID_ARG.
  * MF_QUERY_CENTRE is the interface-only iteration of Algorithm 2: a subdomain's only
  * interior points that other subdomains read are its centre lines (x or y on the
  * 1/2 lattice), so each sweep predicts just those 61 points and leaves the others as
@@ -240,12 +256,21 @@ mf_status mf_batch_upload(mf_batch* batch, int problem, const float* src, int sr
 mf_status mf_batch_download(const mf_batch* batch, int problem, float* dst, int dst_on_device, void* stream);
 
 /* mf_batch_sweep -- multiplicative sweeps (all four colours) of every problem of the
- * batch at once: per colour one gather launch and one SDNet launch cover all problems.
- * Options as mf_sweep (precision MF_PREC_FP32 or MF_PREC_BF16; MF_QUERY_FULL or
- * MF_QUERY_CENTRE; colours must be 0). delta is taken over all problems' grid points
- * together. With opts->graph set, sweeps after the first are replayed from a CUDA graph
- * of one sweep (re-captured when the SDNet, precision or query changes). Synchronises
- * `stream` before returning. Errors as mf_sweep. */
+ * batch at once (Section 4.1's batching of atomic subdomains, applied across problems):
+ * each colour of all problems is one batch. Options as mf_sweep (precision MF_PREC_FP32
+ * or MF_PREC_BF16; MF_QUERY_FULL or MF_QUERY_CENTRE; colours must be 0). delta is taken
+ * over all problems' grid points together. Launch modes (opts->launch_mode):
+ *  - MF_LAUNCH_PER_COLOUR: per colour one gather launch and one SDNet launch;
+ *  - MF_LAUNCH_GRAPH: sweeps after the first are replayed from a CUDA graph of one
+ *    sweep (re-captured when the SDNet, precision or query changes);
+ *  - MF_LAUNCH_SWEEP: one cooperative launch per sweep (BF16 only, else
+ *    MF_ERR_UNSUPPORTED);
+ *  - MF_LAUNCH_AUTO: at the first call for an SDNet, precision and query, every
+ *    applicable mode and gather block size (4, 8, 16 subdomains) is timed over a few
+ *    sweeps of a scratch copy of the grids (the batch's own grids are not touched) and
+ *    the fastest is kept for later calls with the same SDNet, precision and query.
+ * result->launch_mode and result->gather_block report what ran. Synchronises `stream`
+ * before returning. Errors as mf_sweep. */
 mf_status mf_batch_sweep(mf_batch* batch, const mf_sdnet* net, const mf_sweep_opts* opts,
                          mf_sweep_result* result, void* stream);
 

@@ -29,6 +29,7 @@ struct mf_grid {
   double* partial = nullptr;
   double* out = nullptr;    // 16 doubles: [0..4] sweep reduction + delta, [8..12] residual
   int* status = nullptr;    // kernel status word
+  unsigned int* sync = nullptr;  // barrier counter of the whole-sweep launch
   double* h_out = nullptr;  // pinned host mirror of out (16 doubles)
   int* h_status = nullptr;  // pinned host mirror of status
   std::vector<cudaEvent_t> events;  // profiling events, grown on demand
@@ -312,6 +313,7 @@ mf_status mf_destroy_grid(mf_grid* g) {
   cudaFree(g->partial);
   cudaFree(g->out);
   cudaFree(g->status);
+  cudaFree(g->sync);
   cudaFreeHost(g->h_out);
   cudaFreeHost(g->h_status);
   for (cudaEvent_t ev : g->events) cudaEventDestroy(ev);
@@ -343,6 +345,7 @@ mf_status mf_create_grid(mf_ctx* ctx, const mf_grid_desc* desc, const double* bc
   if (e == cudaSuccess) e = cudaMalloc(&g->partial, mf::kReduceBlocks * 4 * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&g->out, 16 * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&g->status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&g->sync, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMallocHost(&g->h_out, 16 * sizeof(double));
   if (e == cudaSuccess) e = cudaMallocHost(&g->h_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&dbc, nbc * sizeof(double));
@@ -408,8 +411,15 @@ mf_status sweep_impl(mf_grid* g, const mf_sdnet* net, const mf_sweep_opts* o, mf
   if (!std::isfinite(o->eps)) return fail(MF_ERR_INVALID_ARG, "mf_sweep: eps must be finite");
   if (o->precision != MF_PREC_FP32 && !mf::bf16_supported(net->d))
     return fail(MF_ERR_UNSUPPORTED, "mf_sweep: BF16 path needs 1..5 hidden layers");
+  if (o->launch_mode != MF_LAUNCH_PER_COLOUR && o->launch_mode != MF_LAUNCH_SWEEP)
+    return fail(MF_ERR_INVALID_ARG, "mf_sweep: launch_mode must be MF_LAUNCH_PER_COLOUR or MF_LAUNCH_SWEEP");
+  const bool sweep_launch = o->launch_mode == MF_LAUNCH_SWEEP;
+  if (sweep_launch && (o->schedule != MF_SCHEDULE_MULTIPLICATIVE || (o->colours != 0 && o->colours != 15) ||
+                       o->precision == MF_PREC_FP32 || !mf::bf16_sweep_supported(net->d)))
+    return fail(MF_ERR_UNSUPPORTED, "mf_sweep: MF_LAUNCH_SWEEP runs BF16 multiplicative sweeps of all colours "
+                                    "with an SDNet without a boundary embedding");
   if (net->device != g->device) return fail(MF_ERR_INVALID_ARG, "mf_sweep: grid and SDNet on different devices");
-  if (res) *res = mf_sweep_result{0, -1.0, 0, 0, 0.0, 0.0, 0.0, 0, 0, MF_OK};
+  if (res) *res = mf_sweep_result{0, -1.0, 0, 0, 0.0, 0.0, 0.0, 0, 0, MF_OK, o->launch_mode, 16};
   MF_ON_DEVICE(g->device, "mf_sweep: cudaSetDevice");
   cudaStream_t st = as_stream(stream);
   const int mask = o->colours == 0 ? 15 : o->colours;
@@ -435,7 +445,26 @@ mf_status sweep_impl(mf_grid* g, const mf_sdnet* net, const mf_sweep_opts* o, mf
       ++launches;
     }
     MF_CUDA(pt.mark(kPhaseReduce), "mf_sweep: event");
-    for (int c = 0; c < 4; ++c) {
+    if (bf16 && sweep_launch) {
+      // the whole sweep in one cooperative launch (gathers included)
+      mf::ColourGeom gc[4];
+      int n_col = 0;
+      for (int c = 0; c < 4; ++c) {
+        mf::ColourGeom cg = colour_geom(g, c);
+        if (cg.n_c == 0) continue;
+        if (o->query == MF_QUERY_CENTRE) {
+          cg.centre = 1;
+          cg.rows_per_sub = mf::kNcross;
+        }
+        gc[n_col++] = cg;
+      }
+      MF_CUDA(mf::launch_mlp_bf16_sweep(gc, n_col, net->d, g->u, g->B, g->sync, g->status, st),
+              "mf_sweep: whole-sweep launch");
+      MF_CUDA(pt.mark(kPhaseMlp), "mf_sweep: event");
+      launches += 1;
+      mlp_launches += 1;
+    }
+    for (int c = 0; c < 4 && !(bf16 && sweep_launch); ++c) {
       if (!((mask >> c) & 1)) continue;
       mf::ColourGeom cg = colour_geom(g, c);
       if (cg.n_c == 0) continue;

@@ -6,13 +6,18 @@
 // SDNet launch per colour serve the whole batch, however uneven the problems are: the
 // kernels flatten (subdomain, point) rows across problems exactly as they do within one
 // problem (Section 4.1 batches a problem's atomic subdomains; here the batch also spans
-// problems). Sweeps without a convergence check replay a CUDA graph captured from the
-// first such sweep, so a long run costs one graph launch per sweep.
+// problems). A sweep is launched in one of three ways: per colour one gather launch and
+// one SDNet launch; the same launches replayed from a CUDA graph (sweeps without a
+// convergence check); or one cooperative launch per sweep that gathers, evaluates and
+// scatters every colour with device-wide barriers between them (BF16). An autotuner
+// times these modes and the gather block size on a scratch copy of the batch and keeps
+// the fastest per SDNet, precision and query.
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/mosaicflow.h"
@@ -39,12 +44,19 @@ struct mf_batch {
   int* status = nullptr;
   double* h_out = nullptr;
   int* h_status = nullptr;
+  unsigned int* sync = nullptr;  // barrier counter of the whole-sweep launch
   // captured sweep
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
   const mf_sdnet* g_net = nullptr;
-  int g_prec = -1, g_query = -1;
+  int g_prec = -1, g_query = -1, g_gather = -1;
   bool warmed = false;
+  // autotuner choices: (SDNet, precision, query) -> (launch mode, gather block)
+  struct Choice {
+    const mf_sdnet* net;
+    int prec, query, mode, gather;
+  };
+  std::vector<Choice> tuned;
 };
 
 namespace {
@@ -77,25 +89,126 @@ mf::ColourGeom batch_geom(const mf_batch* b, int c, int query) {
   return g;
 }
 
-// One sweep's launches (gather + SDNet for colours 0..3) on stream st.
-cudaError_t enqueue_sweep(mf_batch* b, const mf::DevNet& net, int prec, int query, cudaStream_t st) {
+// One sweep's launches (gather + SDNet for colours 0..3) over the grids at `u` (the
+// batch's own, or a scratch copy of the same layout) on stream st.
+cudaError_t enqueue_sweep(mf_batch* b, const mf::DevNet& net, int prec, int query, int gather, float* u,
+                          cudaStream_t st) {
   for (int c = 0; c < 4; ++c) {
     const mf::ColourGeom g = batch_geom(b, c, query);
     if (g.n_c == 0) continue;
-    cudaError_t e = mf::launch_gather_boundary(b->u, g, net, b->B, st);
+    cudaError_t e = mf::launch_gather_boundary(u, g, net, b->B, st, gather);
     if (e != cudaSuccess) return e;
-    e = prec == MF_PREC_BF16 ? mf::launch_mlp_bf16(b->B, g, net, b->u, 0, b->status, st)
-                             : mf::launch_mlp_fp32(b->B, g, net, b->u, 0, st);
+    e = prec == MF_PREC_BF16 ? mf::launch_mlp_bf16(b->B, g, net, u, 0, b->status, st)
+                             : mf::launch_mlp_fp32(b->B, g, net, u, 0, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+// One sweep as a single cooperative launch (BF16).
+cudaError_t enqueue_sweep_whole(mf_batch* b, const mf::DevNet& net, int query, float* u, cudaStream_t st) {
+  mf::ColourGeom gc[4];
+  int n_col = 0;
+  for (int c = 0; c < 4; ++c) {
+    const mf::ColourGeom g = batch_geom(b, c, query);
+    if (g.n_c > 0) gc[n_col++] = g;
+  }
+  return mf::launch_mlp_bf16_sweep(gc, n_col, net, u, b->B, b->sync, b->status, st);
 }
 
 void drop_graph(mf_batch* b) {
   if (b->graph) cudaGraphExecDestroy(b->graph);
   b->graph = nullptr;
   b->g_net = nullptr;
-  b->g_prec = b->g_query = -1;
+  b->g_prec = b->g_query = b->g_gather = -1;
+}
+
+// Capture one sweep's per-colour launches over the grids at `u` into an executable graph.
+cudaError_t capture_sweep(mf_batch* b, const mf::DevNet& net, int prec, int query, int gather, float* u,
+                          cudaGraphExec_t* out) {
+  if (!b->cap_stream) {
+    cudaError_t e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+  }
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  const cudaError_t e1 = enqueue_sweep(b, net, prec, query, gather, u, b->cap_stream);
+  const cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &graph);
+  if (e1 != cudaSuccess || e2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return e1 != cudaSuccess ? e1 : e2;
+  }
+  e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  return e;
+}
+
+// The autotuner: time every applicable (mode, gather block) on a scratch copy of the
+// grids (the `prev` buffer, which every checked sweep overwrites anyway) and return the
+// fastest. Each candidate runs one untimed sweep, then kTimed timed sweeps.
+cudaError_t autotune(mf_batch* b, const mf::DevNet& net, int prec, int query, cudaStream_t st, int* mode,
+                     int* gather) {
+  constexpr int kTimed = 3;
+  float* scratch = b->prev;
+  cudaError_t e = cudaMemcpyAsync(scratch, b->u, b->total * sizeof(float), cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return e;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess) return e;
+  if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return e;
+  }
+  std::vector<std::tuple<int, int>> cand;
+  for (int gs : {4, 8, 16}) cand.emplace_back(MF_LAUNCH_PER_COLOUR, gs);
+  if (prec == MF_PREC_BF16 && mf::bf16_sweep_supported(net)) cand.emplace_back(MF_LAUNCH_SWEEP, 16);
+  float best = 3.4e38f;
+  int best_mode = MF_LAUNCH_PER_COLOUR, best_gather = 16;
+  for (const auto& c : cand) {
+    const int md = std::get<0>(c), gs = std::get<1>(c);
+    auto one = [&]() {
+      return md == MF_LAUNCH_SWEEP ? enqueue_sweep_whole(b, net, query, scratch, st)
+                                   : enqueue_sweep(b, net, prec, query, gs, scratch, st);
+    };
+    if ((e = one()) != cudaSuccess) break;
+    if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
+    for (int k = 0; k < kTimed && e == cudaSuccess; ++k) e = one();
+    if (e != cudaSuccess || (e = cudaEventRecord(e1, st)) != cudaSuccess) break;
+    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+    float ms = 0.f;
+    if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) break;
+    if (ms < best) {
+      best = ms;
+      best_mode = md;
+      best_gather = gs;
+    }
+  }
+  // the graph of the best per-colour configuration, replayed
+  if (e == cudaSuccess) {
+    int gs = best_mode == MF_LAUNCH_PER_COLOUR ? best_gather : 16;
+    cudaGraphExec_t ge = nullptr;
+    e = capture_sweep(b, net, prec, query, gs, scratch, &ge);
+    if (e == cudaSuccess) {
+      e = cudaGraphLaunch(ge, st);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+      for (int k = 0; k < kTimed && e == cudaSuccess; ++k) e = cudaGraphLaunch(ge, st);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && ms < best) {
+        best = ms;
+        best_mode = MF_LAUNCH_GRAPH;
+        best_gather = gs;
+      }
+      cudaGraphExecDestroy(ge);
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *mode = best_mode;
+  *gather = best_gather;
+  return e;
 }
 
 }  // namespace
@@ -114,6 +227,7 @@ mf_status mf_destroy_batch(mf_batch* b) {
   cudaFree(b->partial);
   cudaFree(b->out);
   cudaFree(b->status);
+  cudaFree(b->sync);
   cudaFreeHost(b->h_out);
   cudaFreeHost(b->h_status);
   delete b;
@@ -175,6 +289,7 @@ mf_status mf_create_batch(mf_ctx* ctx, int n, const mf_grid_desc* descs, const d
   if (e == cudaSuccess) e = cudaMalloc(&b->partial, mf::kReduceBlocks * 4 * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&b->out, 16 * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&b->status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&b->sync, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemset(b->status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost(&b->h_out, 16 * sizeof(double));
   if (e == cudaSuccess) e = cudaMallocHost(&b->h_status, sizeof(int));
@@ -257,31 +372,41 @@ mf_status batch_sweep_impl(mf_batch* b, const mf_sdnet* net, const mf_sweep_opts
   if (net_device != b->device) return fail(MF_ERR_INVALID_ARG, "mf_batch_sweep: batch and SDNet on different devices");
   if (o->precision == MF_PREC_BF16 && !mf::bf16_supported(*d))
     return fail(MF_ERR_UNSUPPORTED, "mf_batch_sweep: BF16 path needs 1..5 hidden layers");
-  if (res) *res = mf_sweep_result{0, -1.0, 0, 0, 0.0, 0.0, 0.0, 0, 0, MF_OK};
+  if (o->launch_mode < MF_LAUNCH_PER_COLOUR || o->launch_mode > MF_LAUNCH_AUTO)
+    return fail(MF_ERR_INVALID_ARG, "mf_batch_sweep: unknown launch_mode");
+  if (o->launch_mode == MF_LAUNCH_SWEEP && (o->precision != MF_PREC_BF16 || !mf::bf16_sweep_supported(*d)))
+    return fail(MF_ERR_UNSUPPORTED, "mf_batch_sweep: MF_LAUNCH_SWEEP runs BF16 sweeps with an SDNet without a "
+                                    "boundary embedding");
   BT_ON_DEVICE(b->device, "mf_batch_sweep: cudaSetDevice");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   BT_CUDA(cudaMemsetAsync(b->status, 0, sizeof(int), st), "mf_batch_sweep: reset status");
 
-  // graph of one unchecked sweep, captured once the kernels have run uncaptured
-  const bool use_graph = o->graph != 0;
-  if (use_graph && b->warmed && (b->g_net != net || b->g_prec != o->precision || b->g_query != o->query || !b->graph)) {
-    drop_graph(b);
-    if (!b->cap_stream) BT_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking), "mf_batch_sweep: stream");
-    cudaGraph_t graph = nullptr;
-    BT_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal), "mf_batch_sweep: begin capture");
-    const cudaError_t e1 = enqueue_sweep(b, *d, o->precision, o->query, b->cap_stream);
-    const cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &graph);
-    if (e1 != cudaSuccess) {
-      if (graph) cudaGraphDestroy(graph);
-      return cuda_fail(e1, "mf_batch_sweep: capture");
+  int mode = o->launch_mode, gather = 16;
+  if (mode == MF_LAUNCH_AUTO) {
+    bool found = false;
+    for (const auto& c : b->tuned)
+      if (c.net == net && c.prec == o->precision && c.query == o->query) {
+        mode = c.mode;
+        gather = c.gather;
+        found = true;
+      }
+    if (!found) {
+      BT_CUDA(autotune(b, *d, o->precision, o->query, st, &mode, &gather), "mf_batch_sweep: autotune");
+      b->tuned.push_back(mf_batch::Choice{net, o->precision, o->query, mode, gather});
     }
-    BT_CUDA(e2, "mf_batch_sweep: end capture");
-    const cudaError_t e3 = cudaGraphInstantiate(&b->graph, graph, 0);
-    cudaGraphDestroy(graph);
-    BT_CUDA(e3, "mf_batch_sweep: instantiate");
+  }
+  if (res) *res = mf_sweep_result{0, -1.0, 0, 0, 0.0, 0.0, 0.0, 0, 0, MF_OK, mode, gather};
+
+  // graph of one unchecked sweep, captured once the kernels have run uncaptured
+  const bool use_graph = mode == MF_LAUNCH_GRAPH;
+  if (use_graph && b->warmed &&
+      (b->g_net != net || b->g_prec != o->precision || b->g_query != o->query || b->g_gather != gather || !b->graph)) {
+    drop_graph(b);
+    BT_CUDA(capture_sweep(b, *d, o->precision, o->query, gather, b->u, &b->graph), "mf_batch_sweep: capture");
     b->g_net = net;
     b->g_prec = o->precision;
     b->g_query = o->query;
+    b->g_gather = gather;
   }
 
   int done = 0, launches = 0, graph_sweeps = 0;
@@ -294,11 +419,15 @@ mf_status batch_sweep_impl(mf_batch* b, const mf_sdnet* net, const mf_sweep_opts
     if (use_graph && b->graph) {
       BT_CUDA(cudaGraphLaunch(b->graph, st), "mf_batch_sweep: graph launch");
       ++graph_sweeps;
+      launches += 8;
+    } else if (mode == MF_LAUNCH_SWEEP) {
+      BT_CUDA(enqueue_sweep_whole(b, *d, o->query, b->u, st), "mf_batch_sweep: whole-sweep launch");
+      launches += 1;
     } else {
-      BT_CUDA(enqueue_sweep(b, *d, o->precision, o->query, st), "mf_batch_sweep: sweep");
+      BT_CUDA(enqueue_sweep(b, *d, o->precision, o->query, gather, b->u, st), "mf_batch_sweep: sweep");
       b->warmed = true;
+      launches += 8;
     }
-    launches += 8;
     done = k + 1;
     if (check) {
       BT_CUDA(mf::launch_reduce(b->u, b->prev, (int)kRow, (int)(b->total / kRow), b->partial, b->out, st, false),
@@ -323,7 +452,7 @@ mf_status batch_sweep_impl(mf_batch* b, const mf_sdnet* net, const mf_sweep_opts
     res->sweeps_done = done;
     res->delta = checked ? b->h_out[4] : -1.0;
     res->kernel_launches = launches;
-    res->mlp_launches = 4 * done;
+    res->mlp_launches = mode == MF_LAUNCH_SWEEP ? done : 4 * done;
     res->sweeps_bf16 = o->precision == MF_PREC_BF16 ? done : 0;
     res->graph_sweeps = graph_sweeps;
   }

@@ -14,9 +14,11 @@ namespace mf {
 namespace {
 
 constexpr int kGatherThreads = 256;
-constexpr int kSubPerBlock = 16;  // subdomains per block (one warp gathers two)
 
-template <int H>
+// kSubPerBlock subdomains per block (4, 8 or 16; the default 16 has each warp gather
+// two): fewer per block spread a small colour over more SMs, more per block share each
+// weight load among more subdomains.
+template <int H, int kSubPerBlock>
 __global__ void __launch_bounds__(kGatherThreads)
 gather_boundary_kernel(const float* __restrict__ u, ColourGeom g, const float* __restrict__ W1t,
                        const float* __restrict__ b0, float* __restrict__ B) {
@@ -44,7 +46,7 @@ gather_boundary_kernel(const float* __restrict__ u, ColourGeom g, const float* _
   // B[s][j] = sum_k W1[j][k] g_s[k] + b0[j]; W1t is k-major so the weight reads of a
   // warp are one contiguous row segment.
   constexpr int kGroups = kGatherThreads / H;
-  constexpr int kPer = kSubPerBlock / kGroups;
+  constexpr int kPer = kSubPerBlock / kGroups > 0 ? kSubPerBlock / kGroups : 1;
   const int j = threadIdx.x % H, grp = threadIdx.x / H;
   float acc[kPer];
 #pragma unroll
@@ -53,13 +55,16 @@ gather_boundary_kernel(const float* __restrict__ u, ColourGeom g, const float* _
   for (int k = 0; k < kNbdry; ++k) {
     const float w = __ldg(W1t + k * H + j);
 #pragma unroll
-    for (int i = 0; i < kPer; ++i) acc[i] = fmaf(w, gs[grp + i * kGroups][k], acc[i]);
+    for (int i = 0; i < kPer; ++i) {
+      const int sl = grp + i * kGroups;
+      if (sl < kSubPerBlock) acc[i] = fmaf(w, gs[sl][k], acc[i]);
+    }
   }
   const float bj = __ldg(b0 + j);
 #pragma unroll
   for (int i = 0; i < kPer; ++i) {
-    const int s = s0 + grp + i * kGroups;
-    if (s < g.n_c) B[(size_t)s * H + j] = acc[i] + bj;
+    const int sl = grp + i * kGroups, s = s0 + sl;
+    if (sl < kSubPerBlock && s < g.n_c) B[(size_t)s * H + j] = acc[i] + bj;
   }
 }
 
@@ -179,20 +184,29 @@ __global__ void zero_interior_kernel(float* __restrict__ u, int nx, int ny) {
 
 }  // namespace
 
+template <int H>
+cudaError_t launch_gather_h(const float* u, const ColourGeom& g, const DevNet& net, float* B, int subs,
+                            cudaStream_t st) {
+  const int blocks = (g.n_c + subs - 1) / subs;
+  switch (subs) {
+    case 4: gather_boundary_kernel<H, 4><<<blocks, kGatherThreads, 0, st>>>(u, g, net.W1t, net.b0, B); break;
+    case 8: gather_boundary_kernel<H, 8><<<blocks, kGatherThreads, 0, st>>>(u, g, net.W1t, net.b0, B); break;
+    case 16: gather_boundary_kernel<H, 16><<<blocks, kGatherThreads, 0, st>>>(u, g, net.W1t, net.b0, B); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gather_boundary(const float* u, const ColourGeom& g, const DevNet& net, float* B,
-                                   cudaStream_t st) {
+                                   cudaStream_t st, int subs_per_block) {
   if (g.n_c <= 0) return cudaSuccess;
   if (net.embed_c > 0) {
     if (net.width == 128)
       return net.act == kActGelu ? launch_embed<128, kActGelu>(u, g, net, B, st) : launch_embed<128, kActTanh>(u, g, net, B, st);
     return net.act == kActGelu ? launch_embed<64, kActGelu>(u, g, net, B, st) : launch_embed<64, kActTanh>(u, g, net, B, st);
   }
-  const int blocks = (g.n_c + kSubPerBlock - 1) / kSubPerBlock;
-  if (net.width == 128)
-    gather_boundary_kernel<128><<<blocks, kGatherThreads, 0, st>>>(u, g, net.W1t, net.b0, B);
-  else
-    gather_boundary_kernel<64><<<blocks, kGatherThreads, 0, st>>>(u, g, net.W1t, net.b0, B);
-  return cudaGetLastError();
+  return net.width == 128 ? launch_gather_h<128>(u, g, net, B, subs_per_block, st)
+                          : launch_gather_h<64>(u, g, net, B, subs_per_block, st);
 }
 
 cudaError_t launch_init_grid(float* u, int nx, int ny, const double* bc, cudaStream_t st) {

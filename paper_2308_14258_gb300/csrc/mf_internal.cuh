@@ -176,8 +176,9 @@ struct DevNet {
 // K1: gather the boundary of every subdomain of the colour from `u` and form the
 // per-subdomain first-layer term B[s][:] = W1 z_s + b0 (Eq. 8, left operand), with z_s
 // the boundary g_s itself or, for the embedding variant, its conv1d embedding.
+// subs_per_block: subdomains per block of the plain gather (4, 8 or 16).
 cudaError_t launch_gather_boundary(const float* u, const ColourGeom& g, const DevNet& net,
-                                   float* B, cudaStream_t st);
+                                   float* B, cudaStream_t st, int subs_per_block = 16);
 
 // K3f: FP32 SDNet on every interior point of every subdomain of the colour, fused with
 // the scatter into `u` (store, or weighted add for the additive schedule).
@@ -188,6 +189,16 @@ cudaError_t launch_mlp_fp32(const float* B, const ColourGeom& g, const DevNet& n
 cudaError_t launch_mlp_bf16(const float* B, const ColourGeom& g, const DevNet& net,
                             float* u, int additive, int* dev_status, cudaStream_t st);
 bool bf16_supported(const DevNet& net);
+
+// K3 over a whole multiplicative sweep in one cooperative launch: for each of the n_col
+// colour passes gc[0..n_col-1] in order, the boundary gather and B = W1 g + b0 (into B,
+// which must hold the largest pass's n_c x H floats), then the SDNet with the scatter
+// into `u`, with device-wide barriers between the steps (`sync`: one word of device
+// memory, zeroed by the call before the launch). The multiplicative schedule only; not
+// for SDNets with a boundary embedding.
+cudaError_t launch_mlp_bf16_sweep(const ColourGeom* gc, int n_col, const DevNet& net, float* u, float* B,
+                                  unsigned int* sync, int* dev_status, cudaStream_t st);
+bool bf16_sweep_supported(const DevNet& net);
 
 // K5: FP64 reductions over the grid. partial must hold kReduceBlocks * 4 doubles and
 // out 5 doubles: {sum (u-prev)^2, sum prev^2, max |r|, sum r^2, delta}.

@@ -48,6 +48,15 @@ struct Bf16Params {
   float bias[kMaxHidden][128];  // hidden-layer biases
   float wout[128];
   float w2[128][2];             // coordinate block of the first layer
+  // whole-sweep launch (multi-colour kernel only): colour passes in order, each with its
+  // own geometry; the kernel forms B itself (boundary gather + W1 g + b0) before each
+  // pass, and passes are separated by device-wide barriers on `sync`
+  int n_col;
+  ColourGeom gc[4];
+  int n_rows_c[4], n_tiles_c[4];
+  const float* W1t;      // [128][H] boundary block of the first layer, k-major
+  const float* b0;       // [H]
+  unsigned int* sync;    // barrier counter, zero at launch
 };
 
 // Activation of two FP32 pre-activations, packed as BF16x2. tanh: the hardware tanh on
@@ -138,14 +147,13 @@ __device__ __forceinline__ bool hot_wait_warp(uint32_t bar, uint32_t parity, vol
 }
 
 template <int H, int NH, int ACT>
-__device__ __forceinline__ void mma_issuer(const Bf16Params& P, int s, uint32_t tmem, uint32_t sA, uint32_t sW,
-                                           uint32_t bar_act0, uint32_t bar_act1, uint32_t bar_acc,
-                                           volatile int* abort_flag) {
+__device__ __forceinline__ bool mma_issuer(const Bf16Params& P, int n_tiles, int s, uint32_t tmem, uint32_t sA,
+                                           uint32_t sW, uint32_t bar_act0, uint32_t bar_act1, uint32_t bar_acc,
+                                           volatile int* abort_flag, uint32_t& ph0, uint32_t& ph1) {
   using C = Bf16Cfg<H, NH>;
   const uint32_t acc0 = tmem + (uint32_t)(s * 2 * H);
-  uint32_t ph0 = 0u, ph1 = 0u;
   bool ok = true;
-  for (int k = 0; ok && slot_tile(P, k, s) < P.n_tiles; ++k) {
+  for (int k = 0; ok && slot_tile(P, k, s) < n_tiles; ++k) {
     // rebuilt every tile (an opaque copy of the base) so the compiler does not hoist all
     // NH x H/16 descriptors out of the loop into registers
     uint32_t a_base = sA + (uint32_t)s * C::kABytes, w_base = sW;
@@ -174,15 +182,17 @@ __device__ __forceinline__ void mma_issuer(const Bf16Params& P, int s, uint32_t 
       mma_commit(bar_acc);
     }
   }
+  return ok;
 }
 
 // Epilogue of one warp: slot s, row quadrant q (TMEM lanes / tile rows 32q..32q+31),
 // member JJ of the column pair (in K half h it owns columns h*H/2 + JJ*H/4 .. + H/4 - 1).
-template <int H, int NH, int JJ, int ACT>
-__device__ __forceinline__ void epilogue(const Bf16Params& P, int s, int q, int lane, uint32_t tmem, uint32_t sA,
-                                         uint32_t bar_act0, uint32_t bar_act1, uint32_t bar_acc, uint32_t tok_wait,
-                                         uint32_t tok_give, float* half_sum, volatile int* pair_ok,
-                                         volatile int* abort_flag) {
+template <int H, int NH, int JJ, int ACT, bool kMulti>
+__device__ __forceinline__ bool epilogue(const Bf16Params& P, const ColourGeom& geo, int n_rows, int n_tiles, int s,
+                                         int q, int lane, uint32_t tmem, uint32_t sA, uint32_t bar_act0,
+                                         uint32_t bar_act1, uint32_t bar_acc, uint32_t tok_wait, uint32_t tok_give,
+                                         float* half_sum, volatile int* pair_ok, volatile int* abort_flag,
+                                         uint32_t& acc_ph, uint32_t& tok_ph) {
   using C = Bf16Cfg<H, NH>;
   constexpr int HH = C::kHH, CW = C::kCW;
   const int rloc = 32 * q + lane;
@@ -190,7 +200,6 @@ __device__ __forceinline__ void epilogue(const Bf16Params& P, int s, int q, int 
   const uint32_t a_row = sA + (uint32_t)s * C::kABytes + (uint32_t)rloc * 128u;
   const uint32_t swz = (uint32_t)(rloc & 7) << 4;
   const int named = 1 + s * 4 + q;  // named barrier of the warp pair of these rows
-  uint32_t acc_ph = 0u, tok_ph = 0u;
   bool ok = true;
 
   auto put = [&](int c0, const uint32_t* pk) {  // CW columns from c0 of this row
@@ -215,8 +224,8 @@ __device__ __forceinline__ void epilogue(const Bf16Params& P, int s, int q, int 
   // wait for the other slot's turn to end: slot 1 phase n needs slot 0 phase n; slot 0
   // phase n needs slot 1 phase n-1 when that phase exists
   auto take_turn = [&](int k, int e) -> bool {
-    const bool need = (s == 1) || (e > 0 ? slot_tile(P, k, 1) < P.n_tiles
-                                         : (k > 0 && slot_tile(P, k - 1, 1) < P.n_tiles));
+    const bool need = (s == 1) || (e > 0 ? slot_tile(P, k, 1) < n_tiles
+                                         : (k > 0 && slot_tile(P, k - 1, 1) < n_tiles));
     if (!need) return true;
     bool r;
     if constexpr (ACT == kActTanh) r = __all_sync(0xffffffffu, wait_nap_inl(tok_wait, tok_ph, abort_flag, P.status));
@@ -227,18 +236,24 @@ __device__ __forceinline__ void epilogue(const Bf16Params& P, int s, int q, int 
 
   for (int k = 0; ok; ++k) {
     const int tile = slot_tile(P, k, s);
-    if (tile >= P.n_tiles) break;
+    if (tile >= n_tiles) break;
     const int row = tile * kTileRows + rloc;
-    const bool valid = row < P.n_rows;
-    const RowSite site = row_site(P.g, valid ? row : P.n_rows - 1);
+    const bool valid = row < n_rows;
+    const RowSite site = row_site(geo, valid ? row : n_rows - 1);
     const float x = (float)(site.px + 1) * (1.0f / kPts), y = (float)(site.py + 1) * (1.0f / kPts);
     const float* Bs = P.B + (size_t)site.s * H;
 
     // phase 0: first layer (Eq. 8), FP32 sum B[s] + W2 x, rounded to BF16, tanh
     {
+      // B is read through L2 only when this launch wrote it (whole-sweep kernel): the
+      // read-only path may hold lines from before the write
+      auto ldb = [](const float* a) {
+        if constexpr (kMulti) return __ldcg(reinterpret_cast<const float2*>(a));
+        else return __ldg(reinterpret_cast<const float2*>(a));
+      };
       float2 bb[CW / 2];  // half 0 is loaded before the turn is taken, overlapping the wait
 #pragma unroll
-      for (int i = 0; i < CW / 2; ++i) bb[i] = __ldg(reinterpret_cast<const float2*>(Bs + JJ * CW) + i);
+      for (int i = 0; i < CW / 2; ++i) bb[i] = ldb(Bs + JJ * CW + 2 * i);
       ok = take_turn(k, 0);
       if (ok) {
 #pragma unroll
@@ -246,7 +261,7 @@ __device__ __forceinline__ void epilogue(const Bf16Params& P, int s, int q, int 
           const int c0 = h * HH + JJ * CW;
           if (h == 1) {
 #pragma unroll
-            for (int i = 0; i < CW / 2; ++i) bb[i] = __ldg(reinterpret_cast<const float2*>(Bs + c0) + i);
+            for (int i = 0; i < CW / 2; ++i) bb[i] = ldb(Bs + c0 + 2 * i);
           }
           uint32_t pk[CW / 2];
 #pragma unroll
@@ -312,15 +327,114 @@ __device__ __forceinline__ void epilogue(const Bf16Params& P, int s, int q, int 
     if (JJ == 0 && ok && valid) {
       const float val = uacc + half_sum[s * kTileRows + rloc] + P.bout;
       if (P.additive)
-        P.u[site.idx] += cover_weight(P.g, site.ix, site.iy) * val;
+        P.u[site.idx] += cover_weight(geo, site.ix, site.iy) * val;
       else
         P.u[site.idx] = val;
     }
     named_barrier_sync(named, 64);
   }
+  return ok;
 }
 
-template <int H, int NH, int ACT>
+// ---------------------------------------------------------------- whole-sweep launch
+//
+// The multi-colour kernel runs a whole multiplicative sweep in one cooperative launch:
+// for each colour pass it forms the first-layer boundary term B itself (the boundary
+// gather of K1 and B[s] = W1 g_s + b0, W1 staged in the activation-tile area, which is
+// free between passes), waits at a device-wide barrier until every CTA has written its
+// part of B, runs the colour's tiles exactly as the single-colour kernel does, and
+// waits at a second barrier until every prediction of the colour is in the grid before
+// the next pass gathers. Only the 16 epilogue warps take part in the barriers; the MMA
+// issuers simply wait for the next pass's activations. Every wait is bounded.
+
+constexpr int kEpiAllBar = 9;  // named barrier of all epilogue warps (ids 1..8 pair the warps)
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned int* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Device-wide barrier of the epilogue warps: true when every CTA has arrived `target`
+// times in all; false (the same answer in every warp of the CTA) once the CTA aborts or
+// the bounded wait gives up.
+__device__ __forceinline__ bool epi_grid_sync(const Bf16Params& P, unsigned target, volatile int* abort_flag,
+                                              volatile int* go) {
+  named_barrier_sync(kEpiAllBar, kEpiWarps * 32);
+  if (threadIdx.x == 0) {
+    bool ok = *abort_flag == 0;
+    if (ok) {
+      __threadfence();
+      atomicAdd(P.sync, 1u);
+      const unsigned long long t0 = globaltimer();
+      while (ld_acquire_gpu(P.sync) < target) {
+        if (*abort_flag) {
+          ok = false;
+          break;
+        }
+        if (globaltimer() - t0 > kWaitLimitNs) {
+          *abort_flag = 1;
+          atomicExch(P.status, kDevErrTimeout);
+          ok = false;
+          break;
+        }
+        __nanosleep(64);
+      }
+      __threadfence();
+    }
+    *go = ok ? 1 : 0;
+  }
+  named_barrier_sync(kEpiAllBar, kEpiWarps * 32);
+  return *go != 0;
+}
+
+// K1 inside the whole-sweep kernel: B[s][:] = W1 g_s + b0 for the colour's subdomains,
+// one warp per subdomain (subdomains dealt to the CTAs' warps round robin). Lane l holds
+// boundary values l, 32 + l, 64 + l, 96 + l (the CCW order of K1) and H/32 consecutive
+// outputs; W1 (k-major, [128][H] FP32) is read from its staged copy in shared memory.
+template <int H>
+__device__ __forceinline__ void gather_pass(const Bf16Params& P, const ColourGeom& geo, const float* W1s, int warp,
+                                            int lane) {
+  constexpr int kJ = H / 32;
+  for (int sub = (int)blockIdx.x * kEpiWarps + warp; sub < geo.n_c; sub += (int)gridDim.x * kEpiWarps) {
+    const size_t nx = sub_stride(geo, sub);
+    const float* o = P.u + sub_point(geo, sub, 0, 0);
+    // the grid was written earlier in this launch: read through L2
+    float gv[4];
+    gv[0] = __ldcg(o + lane);                                    // (lane, 0)
+    gv[1] = __ldcg(o + (size_t)lane * nx + kPts);                // (32, lane)
+    gv[2] = __ldcg(o + (size_t)kPts * nx + (kPts - lane));       // (32 - lane, 32)
+    gv[3] = __ldcg(o + (size_t)(kPts - lane) * nx);              // (0, 32 - lane)
+    float acc[kJ];
+#pragma unroll
+    for (int i = 0; i < kJ; ++i) acc[i] = 0.f;
+#pragma unroll
+    for (int seg = 0; seg < 4; ++seg) {
+#pragma unroll 8
+      for (int t = 0; t < 32; ++t) {
+        const int k = seg * 32 + t;
+        const float gk = __shfl_sync(0xffffffffu, gv[seg], t);
+        const float* w = W1s + k * H + lane * kJ;
+        if constexpr (kJ == 4) {
+          const float4 v = *reinterpret_cast<const float4*>(w);
+          acc[0] = fmaf(v.x, gk, acc[0]);
+          acc[1] = fmaf(v.y, gk, acc[1]);
+          acc[2] = fmaf(v.z, gk, acc[2]);
+          acc[3] = fmaf(v.w, gk, acc[3]);
+        } else {
+          const float2 v = *reinterpret_cast<const float2*>(w);
+          acc[0] = fmaf(v.x, gk, acc[0]);
+          acc[1] = fmaf(v.y, gk, acc[1]);
+        }
+      }
+    }
+    float* Bo = const_cast<float*>(P.B) + (size_t)sub * H + lane * kJ;
+#pragma unroll
+    for (int i = 0; i < kJ; ++i) Bo[i] = acc[i] + __ldg(P.b0 + lane * kJ + i);
+  }
+}
+
+template <int H, int NH, int ACT, bool kMulti>
 __global__ void __launch_bounds__(kThreadsBf16, 1) mlp_bf16_kernel(const __grid_constant__ Bf16Params P) {
   using C = Bf16Cfg<H, NH>;
   extern __shared__ uint8_t smem_raw[];
@@ -345,6 +459,7 @@ __global__ void __launch_bounds__(kThreadsBf16, 1) mlp_bf16_kernel(const __grid_
     for (int i = 1; i <= 4; ++i) mbar_init(bar(i), 8);
     for (int i = 5; i <= 8; ++i) mbar_init(bar(i), 1);
     for (int i = 9; i <= 10; ++i) mbar_init(bar(i), 8);
+    if constexpr (kMulti) mbar_init(bar(11), 1);
     *abort_flag = 0;
     fence_barrier_init();
   }
@@ -367,8 +482,18 @@ __global__ void __launch_bounds__(kThreadsBf16, 1) mlp_bf16_kernel(const __grid_
         for (int l = 0; l < NH; ++l)
           bulk_g2s(sW + (uint32_t)l * H * H * 2, P.wimg + (size_t)l * H * H * 2, H * H * 2, bar(0));
       }
-      if (wait_bounded(bar(0), 0, abort_flag, P.status, true))
-        mma_issuer<H, NH, ACT>(P, s, tmem, sA, sW, bar(1 + 2 * s), bar(2 + 2 * s), bar(5 + s), abort_flag);
+      if (wait_bounded(bar(0), 0, abort_flag, P.status, true)) {
+        uint32_t ph0 = 0u, ph1 = 0u;
+        if constexpr (kMulti) {
+          bool ok = true;
+          for (int c = 0; ok && c < P.n_col; ++c)
+            ok = mma_issuer<H, NH, ACT>(P, P.n_tiles_c[c], s, tmem, sA, sW, bar(1 + 2 * s), bar(2 + 2 * s),
+                                        bar(5 + s), abort_flag, ph0, ph1);
+        } else {
+          mma_issuer<H, NH, ACT>(P, P.n_tiles, s, tmem, sA, sW, bar(1 + 2 * s), bar(2 + 2 * s), bar(5 + s),
+                                 abort_flag, ph0, ph1);
+        }
+      }
       // drain: every MMA this thread issued has completed before TMEM is released
       mma_commit(bar(7 + s));
       wait_bounded(bar(7 + s), 0, abort_flag, P.status, false);
@@ -376,12 +501,54 @@ __global__ void __launch_bounds__(kThreadsBf16, 1) mlp_bf16_kernel(const __grid_
     __syncwarp();
   } else {
     const int s = warp >> 3, jj = (warp >> 2) & 1, q = warp & 3;
-    if (jj == 0)
-      epilogue<H, NH, 0, ACT>(P, s, q, lane, tmem, sA, bar(1 + 2 * s), bar(2 + 2 * s), bar(5 + s), bar(9 + s),
-                         bar(10 - s), half_sum, pair_ok, abort_flag);
-    else
-      epilogue<H, NH, 1, ACT>(P, s, q, lane, tmem, sA, bar(1 + 2 * s), bar(2 + 2 * s), bar(5 + s), bar(9 + s),
-                         bar(10 - s), half_sum, pair_ok, abort_flag);
+    uint32_t acc_ph = 0u, tok_ph = 0u;
+    auto run = [&](const ColourGeom& geo, int n_rows, int n_tiles) {
+      if (jj == 0)
+        epilogue<H, NH, 0, ACT, kMulti>(P, geo, n_rows, n_tiles, s, q, lane, tmem, sA, bar(1 + 2 * s), bar(2 + 2 * s),
+                                        bar(5 + s), bar(9 + s), bar(10 - s), half_sum, pair_ok, abort_flag, acc_ph,
+                                        tok_ph);
+      else
+        epilogue<H, NH, 1, ACT, kMulti>(P, geo, n_rows, n_tiles, s, q, lane, tmem, sA, bar(1 + 2 * s), bar(2 + 2 * s),
+                                        bar(5 + s), bar(9 + s), bar(10 - s), half_sum, pair_ok, abort_flag, acc_ph,
+                                        tok_ph);
+    };
+    if constexpr (kMulti) {
+      volatile int* go = reinterpret_cast<volatile int*>(gen + C::kWBytes + 2 * C::kABytes + 112);
+      const float* W1s = reinterpret_cast<const float*>(gen + C::kWBytes);  // the activation-tile area
+      uint32_t w1_ph = 0u;
+      unsigned target = 0u;
+      for (int c = 0; c < P.n_col; ++c) {
+        // stage W1 over the (now idle) activation tiles; earlier generic writes there
+        // are ordered before the asynchronous copy
+        fence_proxy_async_smem();
+        named_barrier_sync(kEpiAllBar, kEpiWarps * 32);
+        if (threadIdx.x == 0) {
+          mbar_arrive_expect_tx(bar(11), 128u * H * 4u);
+          bulk_g2s(sA, P.W1t, 128u * H * 4u, bar(11));
+        }
+        if (hot_wait_warp<false>(bar(11), w1_ph, abort_flag, P.status)) gather_pass<H>(P, P.gc[c], W1s, warp, lane);
+        w1_ph ^= 1u;
+        target += gridDim.x;
+        if (!epi_grid_sync(P, target, abort_flag, go)) break;  // B of the pass complete everywhere
+        run(P.gc[c], P.n_rows_c[c], P.n_tiles_c[c]);
+        if (c + 1 == P.n_col) break;
+        // the turn tokens may hold phases nobody waited for (a slot with one tile more
+        // than the other): start the next pass from fresh token barriers
+        named_barrier_sync(kEpiAllBar, kEpiWarps * 32);
+        if (threadIdx.x == 0) {
+          for (int i = 9; i <= 10; ++i) {
+            mbar_inval(bar(i));
+            mbar_init(bar(i), 8);
+          }
+          fence_barrier_init();
+        }
+        tok_ph = 0u;
+        target += gridDim.x;
+        if (!epi_grid_sync(P, target, abort_flag, go)) break;  // the pass's predictions are in the grid
+      }
+    } else {
+      run(P.g, P.n_rows, P.n_tiles);
+    }
   }
 
   tc_fence_before();
@@ -392,7 +559,7 @@ __global__ void __launch_bounds__(kThreadsBf16, 1) mlp_bf16_kernel(const __grid_
   }
 }
 
-template <int H, int NH, int ACT>
+template <int H, int NH, int ACT, bool kMulti>
 cudaError_t launch_t(const Bf16Params& p, cudaStream_t st) {
   using C = Bf16Cfg<H, NH>;
   // per device: the dynamic shared memory to request and the grid cap (resident CTAs)
@@ -400,13 +567,13 @@ cudaError_t launch_t(const Bf16Params& p, cudaStream_t st) {
   int grid_cap = 0;
   size_t smem_bytes = 0;
   cudaError_t e0 = per_device(pd, [](int dev, int* cap, size_t* smem) {
-    cudaError_t e = cudaFuncSetAttribute(mlp_bf16_kernel<H, NH, ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(mlp_bf16_kernel<H, NH, ACT, kMulti>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)C::kSmem);
     if (e != cudaSuccess) return e;
     int sms = 0, per_sm = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_bf16_kernel<H, NH, ACT>, kThreadsBf16, C::kSmem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_bf16_kernel<H, NH, ACT, kMulti>, kThreadsBf16, C::kSmem);
     if (e != cudaSuccess) return e;
     // every resident CTA must be able to hold its tensor memory at once (512 columns):
     // if shared memory alone would admit more CTAs per SM, request more of it
@@ -416,9 +583,9 @@ cudaError_t launch_t(const Bf16Params& p, cudaStream_t st) {
       int smem_sm = 0;
       cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
       *smem = (size_t)smem_sm / (size_t)(tmem_cap + 1) + 1024;
-      e = cudaFuncSetAttribute(mlp_bf16_kernel<H, NH, ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
+      e = cudaFuncSetAttribute(mlp_bf16_kernel<H, NH, ACT, kMulti>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
       if (e != cudaSuccess) return e;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_bf16_kernel<H, NH, ACT>, kThreadsBf16, *smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_bf16_kernel<H, NH, ACT, kMulti>, kThreadsBf16, *smem);
       if (e != cudaSuccess) return e;
     }
     if (per_sm > tmem_cap || per_sm < 1) return cudaErrorInvalidConfiguration;
@@ -426,30 +593,57 @@ cudaError_t launch_t(const Bf16Params& p, cudaStream_t st) {
     return cudaSuccess;
   }, &grid_cap, &smem_bytes);
   if (e0 != cudaSuccess) return e0;
-  int grid = (p.n_tiles + kSlots - 1) / kSlots;
-  if (grid > grid_cap) grid = grid_cap;
-  if (grid < 1) return cudaSuccess;
-  mlp_bf16_kernel<H, NH, ACT><<<grid, kThreadsBf16, smem_bytes, st>>>(p);
-  return cudaGetLastError();
+  if constexpr (kMulti) {
+    // every CTA takes part in every device-wide barrier, so all must be resident at
+    // once: a cooperative launch of at most the resident-CTA count
+    int most = 0;
+    for (int c = 0; c < p.n_col; ++c) most = p.n_tiles_c[c] > most ? p.n_tiles_c[c] : most;
+    int grid = (most + kSlots - 1) / kSlots;
+    if (grid > grid_cap) grid = grid_cap;
+    if (grid < 1) grid = 1;
+    cudaError_t e = cudaMemsetAsync(p.sync, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
+    void* args[] = {const_cast<Bf16Params*>(&p)};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&mlp_bf16_kernel<H, NH, ACT, true>),
+                                       dim3(grid), dim3(kThreadsBf16), args, smem_bytes, st);
+  } else {
+    int grid = (p.n_tiles + kSlots - 1) / kSlots;
+    if (grid > grid_cap) grid = grid_cap;
+    if (grid < 1) return cudaSuccess;
+    mlp_bf16_kernel<H, NH, ACT, false><<<grid, kThreadsBf16, smem_bytes, st>>>(p);
+    return cudaGetLastError();
+  }
 }
 
-template <int ACT>
+template <int ACT, bool kMulti>
 cudaError_t dispatch(const DevNet& net, const Bf16Params& p, cudaStream_t st) {
   if (net.width == 128) {
     switch (net.n_hidden) {
-      case 1: return launch_t<128, 1, ACT>(p, st);
-      case 2: return launch_t<128, 2, ACT>(p, st);
-      case 3: return launch_t<128, 3, ACT>(p, st);
-      case 4: return launch_t<128, 4, ACT>(p, st);
-      default: return launch_t<128, 5, ACT>(p, st);
+      case 1: return launch_t<128, 1, ACT, kMulti>(p, st);
+      case 2: return launch_t<128, 2, ACT, kMulti>(p, st);
+      case 3: return launch_t<128, 3, ACT, kMulti>(p, st);
+      case 4: return launch_t<128, 4, ACT, kMulti>(p, st);
+      default: return launch_t<128, 5, ACT, kMulti>(p, st);
     }
   }
   switch (net.n_hidden) {
-    case 1: return launch_t<64, 1, ACT>(p, st);
-    case 2: return launch_t<64, 2, ACT>(p, st);
-    case 3: return launch_t<64, 3, ACT>(p, st);
-    case 4: return launch_t<64, 4, ACT>(p, st);
-    default: return launch_t<64, 5, ACT>(p, st);
+    case 1: return launch_t<64, 1, ACT, kMulti>(p, st);
+    case 2: return launch_t<64, 2, ACT, kMulti>(p, st);
+    case 3: return launch_t<64, 3, ACT, kMulti>(p, st);
+    case 4: return launch_t<64, 4, ACT, kMulti>(p, st);
+    default: return launch_t<64, 5, ACT, kMulti>(p, st);
+  }
+}
+
+void fill_net(const DevNet& net, Bf16Params& p) {
+  p.wimg = static_cast<const uint8_t*>(net.wimg_bf16);
+  p.bout = net.bout;
+  for (int l = 0; l < kMaxHidden; ++l)
+    for (int j = 0; j < 128; ++j) p.bias[l][j] = (l < net.n_hidden && j < net.width) ? net.h_bh[l * net.width + j] : 0.f;
+  for (int j = 0; j < 128; ++j) {
+    p.wout[j] = j < net.width ? net.h_wout[j] : 0.f;
+    p.w2[j][0] = j < net.width ? net.h_W2[2 * j] : 0.f;
+    p.w2[j][1] = j < net.width ? net.h_W2[2 * j + 1] : 0.f;
   }
 }
 
@@ -463,25 +657,42 @@ cudaError_t launch_mlp_bf16(const float* B, const ColourGeom& g, const DevNet& n
                             int* dev_status, cudaStream_t st) {
   if (g.n_c <= 0) return cudaSuccess;
   if (!bf16_supported(net)) return cudaErrorNotSupported;
-  Bf16Params p;
+  Bf16Params p{};
   p.B = B;
   p.u = u;
-  p.wimg = static_cast<const uint8_t*>(net.wimg_bf16);
   p.status = dev_status;
   p.g = g;
   p.n_rows = g.n_c * g.rows_per_sub;
   p.n_tiles = (p.n_rows + kTileRows - 1) / kTileRows;
   p.additive = additive;
-  p.bout = net.bout;
-  for (int l = 0; l < kMaxHidden; ++l)
-    for (int j = 0; j < 128; ++j) p.bias[l][j] = (l < net.n_hidden && j < net.width) ? net.h_bh[l * net.width + j] : 0.f;
-  for (int j = 0; j < 128; ++j) {
-    p.wout[j] = j < net.width ? net.h_wout[j] : 0.f;
-    p.w2[j][0] = j < net.width ? net.h_W2[2 * j] : 0.f;
-    p.w2[j][1] = j < net.width ? net.h_W2[2 * j + 1] : 0.f;
+  fill_net(net, p);
+  if (net.act == kActGelu) return dispatch<kActGelu, false>(net, p, st);
+  return dispatch<kActTanh, false>(net, p, st);
+}
+
+bool bf16_sweep_supported(const DevNet& net) { return bf16_supported(net) && net.embed_c == 0; }
+
+cudaError_t launch_mlp_bf16_sweep(const ColourGeom* gc, int n_col, const DevNet& net, float* u, float* B,
+                                  unsigned int* sync, int* dev_status, cudaStream_t st) {
+  if (n_col < 1 || n_col > 4) return cudaErrorInvalidValue;
+  if (!bf16_sweep_supported(net)) return cudaErrorNotSupported;
+  Bf16Params p{};
+  p.B = B;
+  p.u = u;
+  p.status = dev_status;
+  p.additive = 0;
+  p.n_col = n_col;
+  for (int c = 0; c < n_col; ++c) {
+    p.gc[c] = gc[c];
+    p.n_rows_c[c] = gc[c].n_c * gc[c].rows_per_sub;
+    p.n_tiles_c[c] = (p.n_rows_c[c] + kTileRows - 1) / kTileRows;
   }
-  if (net.act == kActGelu) return dispatch<kActGelu>(net, p, st);
-  return dispatch<kActTanh>(net, p, st);
+  p.W1t = net.W1t;
+  p.b0 = net.b0;
+  p.sync = sync;
+  fill_net(net, p);
+  if (net.act == kActGelu) return dispatch<kActGelu, true>(net, p, st);
+  return dispatch<kActTanh, true>(net, p, st);
 }
 
 }  // namespace mf

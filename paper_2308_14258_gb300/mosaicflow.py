@@ -30,6 +30,8 @@ QUERY = {"full": 0, "centre": 1, "center": 1}
 OPTIMIZER = {"sgd": 0, "lamb": 1}
 ENGINE = {"auto": 0, "gemm": 1}
 ACTIVATION = {"tanh": 0, "gelu": 1}
+LAUNCH = {"per_colour": 0, "graph": 1, "sweep": 2, "auto": 3}
+LAUNCH_NAMES = {v: k for k, v in LAUNCH.items()}
 
 # Every exported symbol the header declares (checked by the CPU test suite).
 EXPORTS = ["mf_last_error", "mf_version", "mf_ctx_create", "mf_ctx_destroy", "mf_ctx_device", "mf_load_sdnet", "mf_load_sdnet_ex", "mf_free_sdnet", "mf_create_grid",
@@ -62,14 +64,14 @@ class GridDesc(C.Structure):
 class SweepOpts(C.Structure):
     _fields_ = [("n_sweeps", C.c_int), ("schedule", C.c_int), ("precision", C.c_int),
                 ("colours", C.c_int), ("eps", C.c_double), ("check_every", C.c_int),
-                ("profile", C.c_int), ("eps_coarse", C.c_double), ("query", C.c_int), ("graph", C.c_int)]
+                ("profile", C.c_int), ("eps_coarse", C.c_double), ("query", C.c_int), ("launch_mode", C.c_int)]
 
 
 class SweepResult(C.Structure):
     _fields_ = [("sweeps_done", C.c_int), ("delta", C.c_double), ("kernel_launches", C.c_int),
                 ("mlp_launches", C.c_int), ("ms_gather", C.c_double), ("ms_mlp", C.c_double),
                 ("ms_reduce", C.c_double), ("sweeps_bf16", C.c_int), ("graph_sweeps", C.c_int),
-                ("status", C.c_int)]
+                ("status", C.c_int), ("launch_mode", C.c_int), ("gather_block", C.c_int)]
 
 
 class TrainDesc(C.Structure):
@@ -232,6 +234,14 @@ class SweepOutcome:
     sweeps_bf16: int = 0
     graph_sweeps: int = 0
     status: int = 0
+    launch_mode: str = "per_colour"
+    gather_block: int = 16
+
+
+def _outcome(res) -> SweepOutcome:
+    return SweepOutcome(res.sweeps_done, res.delta, res.kernel_launches, res.mlp_launches, res.ms_gather, res.ms_mlp,
+                        res.ms_reduce, res.sweeps_bf16, res.graph_sweeps, res.status,
+                        LAUNCH_NAMES.get(res.launch_mode, str(res.launch_mode)), res.gather_block)
 
 
 class Grid:
@@ -274,14 +284,15 @@ class Grid:
 
     def sweep(self, net: SDNet, n_sweeps: int = 1, schedule: str = "M", precision: str = "fp32",
               colours: int = 0, eps: float = 0.0, check_every: int = 1, stream=None,
-              profile: bool = False, eps_coarse: float = 0.0, query: str = "full") -> SweepOutcome:
+              profile: bool = False, eps_coarse: float = 0.0, query: str = "full",
+              launch_mode: str = "per_colour") -> SweepOutcome:
+        """launch_mode "per_colour" (gather + SDNet launch per colour) or "sweep" (one
+        cooperative launch per BF16 sweep)."""
         opts = SweepOpts(n_sweeps, SCHEDULE[schedule], PREC[precision], colours, eps, check_every,
-                         1 if profile else 0, eps_coarse, QUERY[query])
+                         1 if profile else 0, eps_coarse, QUERY[query], LAUNCH[launch_mode])
         res = SweepResult()
         _check(load().mf_sweep(self._h, net._h, C.byref(opts), C.byref(res), _stream_ptr(stream)))
-        return SweepOutcome(res.sweeps_done, res.delta, res.kernel_launches, res.mlp_launches,
-                            res.ms_gather, res.ms_mlp, res.ms_reduce, res.sweeps_bf16, res.graph_sweeps,
-                            res.status)
+        return _outcome(res)
 
     def assemble(self, net: SDNet, precision: str = "fp32", stream=None) -> SweepOutcome:
         """Algorithm 2's final step after centre-line sweeps: every subdomain predicts all
@@ -333,14 +344,15 @@ class Batch:
         return dst
 
     def sweep(self, net: SDNet, n_sweeps: int = 1, precision: str = "fp32", eps: float = 0.0,
-              check_every: int = 1, query: str = "full", graph: bool = False, stream=None) -> SweepOutcome:
-        opts = SweepOpts(n_sweeps, 0, PREC[precision], 0, eps, check_every, 0, 0.0, QUERY[query],
-                         1 if graph else 0)
+              check_every: int = 1, query: str = "full", graph: bool = False, stream=None,
+              launch_mode: str | None = None) -> SweepOutcome:
+        """launch_mode: "per_colour", "graph", "sweep" (one cooperative launch per BF16
+        sweep) or "auto" (autotuned at the first call); graph=True is "graph"."""
+        mode = LAUNCH[launch_mode] if launch_mode is not None else (LAUNCH["graph"] if graph else 0)
+        opts = SweepOpts(n_sweeps, 0, PREC[precision], 0, eps, check_every, 0, 0.0, QUERY[query], mode)
         res = SweepResult()
         _check(load().mf_batch_sweep(self._h, net._h, C.byref(opts), C.byref(res), _stream_ptr(stream)))
-        return SweepOutcome(res.sweeps_done, res.delta, res.kernel_launches, res.mlp_launches,
-                            res.ms_gather, res.ms_mlp, res.ms_reduce, res.sweeps_bf16, res.graph_sweeps,
-                            res.status)
+        return _outcome(res)
 
     def residual(self, q, stream=None):
         mx, rms = C.c_double(), C.c_double()
