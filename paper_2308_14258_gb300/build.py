@@ -21,7 +21,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libmosaicflow.so")
 
 SOURCES = ["mf_api.cu", "mf_gather.cu", "mf_reduce.cu", "mf_mlp_fp32.cu", "mf_mlp_bf16.cu", "mf_noalloc.cu", "mf_batch.cu",
-           "mf_train.cu", "mf_train_tc.cu", "mf_train_gemm.cu", "mf_selftest.cu"]
+           "mf_train.cu", "mf_train_tc.cu", "mf_train_gemm.cu", "mf_mlp_f32tc.cu", "mf_selftest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

@@ -244,7 +244,12 @@ mf_status mf_load_sdnet_ex(mf_ctx* ctx, const mf_sdnet_desc_ex* desc, const floa
   const size_t sz_W1t = up(W1t.size() * 4), sz_W2 = up(W2.size() * 4), sz_b0 = up((size_t)H * 4),
                sz_WhT = up(WhT.size() * 4), sz_bh = up(bh.size() * 4), sz_wout = up((size_t)H * 4),
                sz_img = up(img.size() * 2), sz_conv = up(n_conv * 4 + 4);
-  const size_t total = sz_W1t + sz_W2 + sz_b0 + sz_WhT + sz_bh + sz_wout + sz_img + sz_conv;
+  // F16 hi/lo images for the FP32 tensor-core kernel: width 128, and every hidden
+  // weight within the F16 range (else that kernel is not offered for this SDNet)
+  bool f16_ok = H == 128;
+  for (size_t i = 0; f16_ok && i < WhT.size(); ++i) f16_ok = std::fabs(WhT[i]) < 65504.0f;
+  const size_t sz_f16 = f16_ok ? up(mf::f32tc_image_bytes(NH)) : 0;
+  const size_t total = sz_W1t + sz_W2 + sz_b0 + sz_WhT + sz_bh + sz_wout + sz_img + sz_conv + sz_f16;
   cudaError_t e = cudaMalloc(&net->dmem, total);
   if (e != cudaSuccess) {
     delete net;
@@ -266,6 +271,7 @@ mf_status mf_load_sdnet_ex(mf_ctx* ctx, const mf_sdnet_desc_ex* desc, const floa
   net->d.wout = (const float*)place(wout, (size_t)H * 4, sz_wout);
   net->d.wimg_bf16 = place(img.data(), img.size() * 2, sz_img);
   const float* conv = (const float*)place(w, n_conv * 4, sz_conv);  // cw1 | cb1 | cw2 | cb2, as packed
+  void* f16img = f16_ok ? place(nullptr, 0, sz_f16) : nullptr;
   if (!net->d.W1t || !net->d.W2 || !net->d.b0 || !net->d.WhT || !net->d.bh || !net->d.wout || !net->d.wimg_bf16 ||
       !conv) {
     cudaError_t err = cudaGetLastError();
@@ -286,6 +292,17 @@ mf_status mf_load_sdnet_ex(mf_ctx* ctx, const mf_sdnet_desc_ex* desc, const floa
   net->d.cb2 = C > 0 ? conv + (cb2 - w) : nullptr;
   net->d.bout = bout;
   net->d.wimg_bytes = img.size() * 2;
+  net->d.wimg_f16 = nullptr;
+  if (f16img) {
+    cudaError_t pe = mf::f32tc_pack(net->d.WhT, NH, f16img, nullptr);
+    if (pe == cudaSuccess) pe = cudaDeviceSynchronize();
+    if (pe != cudaSuccess) {
+      cudaFree(net->dmem);
+      delete net;
+      return cuda_fail(pe, "mf_load_sdnet: F16 images");
+    }
+    net->d.wimg_f16 = f16img;
+  }
   net->h_bh = bh;
   net->h_wout.assign(wout, wout + H);
   net->h_W2 = W2;
@@ -398,7 +415,8 @@ mf_status sweep_impl(mf_grid* g, const mf_sdnet* net, const mf_sweep_opts* o, mf
   if (o->n_sweeps < 0) return fail(MF_ERR_INVALID_ARG, "mf_sweep: n_sweeps < 0");
   if (o->schedule != MF_SCHEDULE_MULTIPLICATIVE && o->schedule != MF_SCHEDULE_ADDITIVE)
     return fail(MF_ERR_INVALID_ARG, "mf_sweep: unknown schedule");
-  if (o->precision != MF_PREC_FP32 && o->precision != MF_PREC_BF16 && o->precision != MF_PREC_MIXED)
+  if (o->precision != MF_PREC_FP32 && o->precision != MF_PREC_BF16 && o->precision != MF_PREC_MIXED &&
+      o->precision != MF_PREC_FP32_SIMT)
     return fail(MF_ERR_INVALID_ARG, "mf_sweep: unknown precision");
   if (o->precision == MF_PREC_MIXED && !(o->eps_coarse > 0.0 && std::isfinite(o->eps_coarse)))
     return fail(MF_ERR_INVALID_ARG, "mf_sweep: MF_PREC_MIXED needs eps_coarse > 0");
@@ -409,13 +427,14 @@ mf_status sweep_impl(mf_grid* g, const mf_sdnet* net, const mf_sweep_opts* o, mf
   if (o->query == MF_QUERY_CENTRE && o->schedule == MF_SCHEDULE_ADDITIVE)
     return fail(MF_ERR_INVALID_ARG, "mf_sweep: centre-line sweeps use the multiplicative schedule");
   if (!std::isfinite(o->eps)) return fail(MF_ERR_INVALID_ARG, "mf_sweep: eps must be finite");
-  if (o->precision != MF_PREC_FP32 && !mf::bf16_supported(net->d))
+  if ((o->precision == MF_PREC_BF16 || o->precision == MF_PREC_MIXED) && !mf::bf16_supported(net->d))
     return fail(MF_ERR_UNSUPPORTED, "mf_sweep: BF16 path needs 1..5 hidden layers");
   if (o->launch_mode != MF_LAUNCH_PER_COLOUR && o->launch_mode != MF_LAUNCH_SWEEP)
     return fail(MF_ERR_INVALID_ARG, "mf_sweep: launch_mode must be MF_LAUNCH_PER_COLOUR or MF_LAUNCH_SWEEP");
   const bool sweep_launch = o->launch_mode == MF_LAUNCH_SWEEP;
   if (sweep_launch && (o->schedule != MF_SCHEDULE_MULTIPLICATIVE || (o->colours != 0 && o->colours != 15) ||
-                       o->precision == MF_PREC_FP32 || !mf::bf16_sweep_supported(net->d)))
+                       o->precision == MF_PREC_FP32 || o->precision == MF_PREC_FP32_SIMT ||
+                       !mf::bf16_sweep_supported(net->d)))
     return fail(MF_ERR_UNSUPPORTED, "mf_sweep: MF_LAUNCH_SWEEP runs BF16 multiplicative sweeps of all colours "
                                     "with an SDNet without a boundary embedding");
   if (net->device != g->device) return fail(MF_ERR_INVALID_ARG, "mf_sweep: grid and SDNet on different devices");
@@ -477,7 +496,9 @@ mf_status sweep_impl(mf_grid* g, const mf_sdnet* net, const mf_sweep_opts* o, mf
       if (bf16)
         MF_CUDA(mf::launch_mlp_bf16(g->B, cg, net->d, g->u, additive ? 1 : 0, g->status, st), "mf_sweep: bf16 mlp");
       else
-        MF_CUDA(mf::launch_mlp_fp32(g->B, cg, net->d, g->u, additive ? 1 : 0, st), "mf_sweep: fp32 mlp");
+        MF_CUDA(mf::launch_mlp_fp32_path(g->B, cg, net->d, g->u, additive ? 1 : 0, g->status,
+                                         o->precision == MF_PREC_FP32_SIMT, st),
+                "mf_sweep: fp32 mlp");
       MF_CUDA(pt.mark(kPhaseMlp), "mf_sweep: event");
       launches += 2;
       mlp_launches += 1;

@@ -99,7 +99,7 @@ cudaError_t enqueue_sweep(mf_batch* b, const mf::DevNet& net, int prec, int quer
     cudaError_t e = mf::launch_gather_boundary(u, g, net, b->B, st, gather);
     if (e != cudaSuccess) return e;
     e = prec == MF_PREC_BF16 ? mf::launch_mlp_bf16(b->B, g, net, u, 0, b->status, st)
-                             : mf::launch_mlp_fp32(b->B, g, net, u, 0, st);
+                             : mf::launch_mlp_fp32_path(b->B, g, net, u, 0, b->status, prec == MF_PREC_FP32_SIMT, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -360,8 +360,8 @@ mf_status batch_sweep_impl(mf_batch* b, const mf_sdnet* net, const mf_sweep_opts
   if (o->n_sweeps < 0) return fail(MF_ERR_INVALID_ARG, "mf_batch_sweep: n_sweeps < 0");
   if (o->schedule != MF_SCHEDULE_MULTIPLICATIVE)
     return fail(MF_ERR_INVALID_ARG, "mf_batch_sweep: batches use the multiplicative schedule");
-  if (o->precision != MF_PREC_FP32 && o->precision != MF_PREC_BF16)
-    return fail(MF_ERR_INVALID_ARG, "mf_batch_sweep: precision must be MF_PREC_FP32 or MF_PREC_BF16");
+  if (o->precision != MF_PREC_FP32 && o->precision != MF_PREC_BF16 && o->precision != MF_PREC_FP32_SIMT)
+    return fail(MF_ERR_INVALID_ARG, "mf_batch_sweep: precision must be MF_PREC_FP32, MF_PREC_FP32_SIMT or MF_PREC_BF16");
   if (o->query != MF_QUERY_FULL && o->query != MF_QUERY_CENTRE)
     return fail(MF_ERR_INVALID_ARG, "mf_batch_sweep: unknown query");
   if (o->colours != 0 && o->colours != 15) return fail(MF_ERR_INVALID_ARG, "mf_batch_sweep: colours must be 0 (all)");

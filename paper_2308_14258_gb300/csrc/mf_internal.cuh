@@ -168,6 +168,7 @@ struct DevNet {
   float bout;
   const void* wimg_bf16; // [n_hidden] BF16 images in the tensor-core shared-memory layout
   size_t wimg_bytes;     // bytes of all images
+  const void* wimg_f16;  // [n_hidden][hi, lo] F16 split images (width 128), or null
   const float* h_bh;     // host copies: hidden biases [n_hidden][H]
   const float* h_wout;   // [H]
   const float* h_W2;     // [H][2]
@@ -189,6 +190,23 @@ cudaError_t launch_mlp_fp32(const float* B, const ColourGeom& g, const DevNet& n
 cudaError_t launch_mlp_bf16(const float* B, const ColourGeom& g, const DevNet& net,
                             float* u, int additive, int* dev_status, cudaStream_t st);
 bool bf16_supported(const DevNet& net);
+
+// K3t: the FP32 SDNet on the tensor cores, each hidden product split in three F16
+// products with FP32 accumulation (width 128, tanh); same contract as launch_mlp_fp32.
+cudaError_t launch_mlp_f32tc(const float* B, const ColourGeom& g, const DevNet& net, float* u, int additive,
+                             int* dev_status, cudaStream_t st);
+bool f32tc_supported(const DevNet& net);
+size_t f32tc_image_bytes(int n_hidden);
+// hi/lo F16 images of the hidden weights (WhT: [n_hidden][k][n] FP32) into img
+cudaError_t f32tc_pack(const float* WhT, int n_hidden, void* img, cudaStream_t st);
+
+// The FP32-accuracy SDNet launch of a sweep: the tensor-core kernel where the SDNet
+// allows it and simt is false, else the SIMT kernel.
+inline cudaError_t launch_mlp_fp32_path(const float* B, const ColourGeom& g, const DevNet& net, float* u,
+                                        int additive, int* dev_status, bool simt, cudaStream_t st) {
+  if (!simt && f32tc_supported(net)) return launch_mlp_f32tc(B, g, net, u, additive, dev_status, st);
+  return launch_mlp_fp32(B, g, net, u, additive, st);
+}
 
 // K3 over a whole multiplicative sweep in one cooperative launch: for each of the n_col
 // colour passes gc[0..n_col-1] in order, the boundary gather and B = W1 g + b0 (into B,
