@@ -518,10 +518,14 @@ def main():
     value = aggregate_rate(evals_per_sweep * args.steps, sum(ms) / 1e3, world)
     total_s = world * evals_per_sweep * args.steps / value
 
-    # FP32 path on the same workload (fewer steps: ~13x slower)
-    k32 = max(2, args.steps // 8) if args.fp32_steps < 0 else args.fp32_steps
-    ms32, mlp32, _, _ = timed_steps("fp32", k32)
+    # FP32 paths on the same workload: MF_PREC_FP32 (split-F16 tensor cores) and the
+    # SIMT kernel (fewer steps: ~16x slower than BF16)
+    k32 = max(3, args.steps // 4) if args.fp32_steps < 0 else args.fp32_steps
+    ms32, mlp32, mlp32_launch, _ = timed_steps("fp32", k32)
     fp32_value = evals_per_sweep * k32 / (sum(ms32) / 1e3) if k32 > 0 else None
+    ks = 2 if args.fp32_steps < 0 else min(2, args.fp32_steps)
+    ms32s, _, _, _ = timed_steps("fp32_simt", ks)
+    fp32_simt_value = evals_per_sweep * ks / (sum(ms32s) / 1e3) if ks > 0 else None
 
     # centre-line (interface-only) sweeps of the same grid: Algorithm 2's per-iteration work
     k_c = max(3, min(args.steps, 10))
@@ -676,7 +680,13 @@ def main():
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "sweeps_per_s": world * args.steps / total_s,
         "fp32": {"value": fp32_value, "unit": UNIT, "ms_per_step": sum(ms32) / k32 if k32 else None,
+                 "kernel": "mlp_f32tc_kernel: hidden products as three F16 tcgen05 products, FP32 accumulation",
+                 "per_launch_ms": mlp32 / max(1, mlp32_launch),
+                 "fp32_tflops_algorithmic": (evals_per_sweep * FLOP_PER_EVAL / 4.0) / (mlp32 / max(1, mlp32_launch) / 1e3) / 1e12
+                 if mlp32_launch else None,
                  "speedup_bf16_over_fp32": value / world / fp32_value if fp32_value else None},
+        "fp32_simt": {"value": fp32_simt_value, "unit": UNIT, "ms_per_step": sum(ms32s) / ks if ks else None,
+                      "kernel": "mlp_fp32_kernel: FFMA and tanhf on the CUDA cores"},
         "err_vs_oracle_bf16_sweep": err,
         "centre_lines": {"sweeps_per_s": 1e3 * k_c / sum(cl_ms), "ms_per_sweep": sum(cl_ms) / k_c,
                          "point_evals_per_sweep": n_sub_c, "unit": "sweeps/s",
