@@ -74,6 +74,8 @@ def parse():
                          "profiling captures)")
     ap.add_argument("--train-only", action="store_true",
                     help="run only the training-step measurement and print its JSON object (profiling aid)")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="run only the batched-workload measurement and print its JSON object (profiling aid)")
     return ap.parse_args()
 
 
@@ -309,12 +311,22 @@ def measure_converged(m, I, torch, np, net, p, weights, stream, rank, with_oracl
       until delta < 1e-5;
     * bf16: BF16 sweeps alone (40, well past their plateau).
     The stop value 1e-5 lies above the FP32 rounding floor of delta on this grid
-    (about 1.5e-6). Each field is compared with the FP32 fixed point (FP32 sweeps
-    continued to 250 in all, where delta sits at its floor), as max |u - u_ref| /
-    max |u_ref|; the target is 1e-3."""
+    (about 1.5e-6). Each field is compared with the FP32 fixed point (FP32 sweeps to
+    250, where delta sits at its floor), as max |u - u_ref| / max |u_ref|.
+    to_1e-3: the same iterations one sweep at a time, the error against the fixed point
+    taken on the device after every sweep; the sweeps each needs until the field is
+    within 1e-3 (the target), and that many sweeps at the timed per-sweep cost."""
     res, fields = {}, {}
+    # the FP32 fixed point first
+    g = m.Grid(p.lx, p.ly, p.bc)
+    o = g.sweep(net, 250, "M", "fp32", check_every=25, stream=stream)
+    ref_t = torch.empty((g.ny, g.nx), dtype=torch.float32, device="cuda")
+    g.download(ref_t, stream=stream)
+    ref = ref_t.double().cpu().numpy()
+    del g
+    scale = float(np.abs(ref).max())
+    res["reference"] = {"what": "FP32 sweeps to 250 from the zero interior", "delta": o.delta}
     runs = (("fp32", "fp32", 400, 1e-5, 0.0), ("mixed", "mixed", 400, 1e-5, 1e-2), ("bf16", "bf16", 40, 0.0, 0.0))
-    ref_grid = None
     for name, prec, n, eps, eps_c in runs:
         g = m.Grid(p.lx, p.ly, p.bc)
         torch.cuda.synchronize()
@@ -327,20 +339,62 @@ def measure_converged(m, I, torch, np, net, p, weights, stream, rank, with_oracl
         fields[name] = g.download(stream=stream).astype(np.float64)
         res[name] = {"sweeps": o.sweeps_done, "sweeps_bf16": o.sweeps_bf16,
                      "sweeps_fp32": o.sweeps_done - o.sweeps_bf16, "delta": o.delta,
-                     "ms": e0.elapsed_time(e1)}
-        if name == "fp32":
-            ref_grid = g
-        else:
-            del g
-    # the FP32 fixed point: continue the FP32 run until delta has reached its floor
-    o = ref_grid.sweep(net, 250 - res["fp32"]["sweeps"], "M", "fp32", check_every=10, stream=stream)
-    ref = ref_grid.download(stream=stream).astype(np.float64)
-    del ref_grid
-    scale = float(np.abs(ref).max())
-    res["reference"] = {"what": "FP32 sweeps continued to 250 from the zero interior", "delta": o.delta}
-    for name in ("fp32", "mixed", "bf16"):
-        res[name]["max_rel_err_vs_fp32_fixed_point"] = float(np.abs(fields[name] - ref).max() / scale)
+                     "ms": e0.elapsed_time(e1),
+                     "max_rel_err_vs_fp32_fixed_point": float(np.abs(fields[name] - ref).max() / scale)}
+        del g
     res["speedup_mixed_over_fp32"] = res["fp32"]["ms"] / res["mixed"]["ms"]
+
+    # sweeps to a field within 1e-3 of the fixed point
+    def sweep_ms(prec):
+        g = m.Grid(p.lx, p.ly, p.bc)
+        g.sweep(net, 1, "M", prec, stream=stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.sweep(net, 4, "M", prec, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / 4
+    t32, t16 = sweep_ms("fp32"), sweep_ms("bf16")
+    cur = torch.empty_like(ref_t)
+
+    def err_now(g):
+        g.download(cur, stream=stream)
+        with torch.cuda.stream(stream):
+            e = float((cur - ref_t).abs().max()) / scale
+        return e
+
+    to = {"target": 1e-3, "ms_per_sweep": {"fp32": t32, "bf16": t16}}
+    g = m.Grid(p.lx, p.ly, p.bc)
+    n32 = None
+    for k in range(1, 201):
+        g.sweep(net, 1, "M", "fp32", stream=stream)
+        if err_now(g) <= 1e-3:
+            n32 = k
+            break
+    to["fp32"] = {"sweeps": n32, "ms": n32 * t32 if n32 else None}
+    g = m.Grid(p.lx, p.ly, p.bc)
+    nb, prev_d, e_bf16 = 0, float("inf"), None
+    for k in range(1, 61):  # BF16 until a sweep no longer reduces delta (the MIXED rule)
+        d = g.sweep(net, 1, "M", "bf16", stream=stream).delta
+        nb = k
+        if d < 1e-2 or d >= prev_d:
+            break
+        prev_d = d
+    e_bf16 = err_now(g)
+    nf = 0
+    if e_bf16 > 1e-3:
+        for k in range(1, 201):
+            g.sweep(net, 1, "M", "fp32", stream=stream)
+            if err_now(g) <= 1e-3:
+                nf = k
+                break
+    to["mixed"] = {"sweeps_bf16": nb, "err_after_bf16": e_bf16, "sweeps_fp32": nf,
+                   "ms": nb * t16 + nf * t32}
+    if to["fp32"]["ms"] and to["mixed"]["ms"]:
+        to["speedup_mixed_over_fp32"] = to["fp32"]["ms"] / to["mixed"]["ms"]
+    del g
+    res["to_1e-3"] = to
     res["workload"] = "large_L64 grid from the zero interior, SDNet 6x128 (seed 2), multiplicative schedule"
     res["stop"] = ("delta < 1e-5 (Algorithm 2); MIXED switches from BF16 to FP32 at delta < 1e-2 or when a BF16 "
                    "sweep no longer reduces delta")
@@ -360,6 +414,32 @@ def measure_converged(m, I, torch, np, net, p, weights, stream, rank, with_oracl
         res["mixed"]["oracle_check"] = ("24 sampled colour-3 subdomains: FP64 oracle prediction from the converged "
                                         "field's boundary vs its interior, max abs / max |u|")
     return res
+
+
+def measure_batched(m, I, torch, stream):
+    """The batched workload: 256 problems of sides 2..32 units (seed 4), BF16, one gather
+    and one SDNet launch per colour over all problems; plain launches and graph replay."""
+    wl = I.batched(256)
+    bnet = m.SDNet(wl.weights(), 128, 6)
+    bt = m.Batch([(p.lx, p.ly) for p in wl.problems], [p.bc for p in wl.problems])
+    b_evals = sum((2 * p.lx - 1) * (2 * p.ly - 1) for p in wl.problems) * 961
+    bt.sweep(bnet, 2, "bf16", stream=stream)  # warm-up (uncaptured)
+    res = {}
+    for mode in ("plain", "graph"):
+        kb = 4
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        o = bt.sweep(bnet, kb, "bf16", graph=(mode == "graph"), check_every=kb, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        res[mode] = {"value": b_evals * kb / t, "ms_per_sweep": 1e3 * t / kb, "graph_sweeps": o.graph_sweeps}
+    batched = {"workload": "256 problems, sides uniform in {2,4,8,16,32} units (seed 4), 8-mode BC seed 1000+q, "
+                           "SDNet 6x128 BF16; grids 287 MB (> L2)",
+               "unit": UNIT, "evals_per_sweep": b_evals, **res}
+    del bt
+    return batched
 
 
 def measure_train(args, m, I, torch, np, stream, rank):
@@ -485,6 +565,9 @@ def main():
     if args.train_only:
         print(json.dumps({"train": measure_train(args, m, I, torch, np, stream, rank)}))
         return
+    if args.batched_only:
+        print(json.dumps({"batched": measure_batched(m, I, torch, stream)}))
+        return
 
     def timed_steps(prec, k, profile=True):
         ms, mlp_ms, mlp_launch, launches = [], 0.0, 0, 0
@@ -543,28 +626,7 @@ def main():
     n_sub_c = n_sub * 61
 
     # the batched workload: 256 problems of sides 2..32 units, one SDNet launch per colour
-    batched = None
-    if args.L == 64 and not args.no_batched:
-        wl = I.batched(256)
-        bnet = m.SDNet(wl.weights(), 128, 6)
-        bt = m.Batch([(p.lx, p.ly) for p in wl.problems], [p.bc for p in wl.problems])
-        b_evals = sum((2 * p.lx - 1) * (2 * p.ly - 1) for p in wl.problems) * 961
-        bt.sweep(bnet, 2, "bf16", stream=stream)  # warm-up (uncaptured)
-        res = {}
-        for mode in ("plain", "graph"):
-            kb = 4
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            o = bt.sweep(bnet, kb, "bf16", graph=(mode == "graph"), check_every=kb, stream=stream)
-            e1.record(stream)
-            e1.synchronize()
-            t = e0.elapsed_time(e1) / 1e3
-            res[mode] = {"value": b_evals * kb / t, "ms_per_sweep": 1e3 * t / kb, "graph_sweeps": o.graph_sweeps}
-        batched = {"workload": "256 problems, sides uniform in {2,4,8,16,32} units (seed 4), 8-mode BC seed 1000+q, "
-                               "SDNet 6x128 BF16; grids 287 MB (> L2)",
-                   "unit": UNIT, "evals_per_sweep": b_evals, **res}
-        del bt
+    batched = measure_batched(m, I, torch, stream) if (args.L == 64 and not args.no_batched) else None
 
     # launch modes of a sweep (per colour, graph replay, one whole-sweep cooperative
     # launch, autotuned) on the large grid and on a batch of 256 small problems (L = 2)

@@ -287,7 +287,8 @@ mf_status mf_batch_residual(const mf_batch* batch, int problem, double* max_abs,
  * `u` is the caller's device grid (ny x nx FP32, row-major, boundary included), read
  * and updated in place; `net` was loaded earlier with mf_load_sdnet under a context of
  * the current device (the call does not switch devices; another device returns
- * MF_ERR_INVALID_ARG); `precision` is MF_PREC_FP32 or MF_PREC_BF16. If `delta` is not
+ * MF_ERR_INVALID_ARG); `precision` is MF_PREC_FP32 (here always the CUDA-core FP32
+ * kernel of MF_PREC_FP32_SIMT) or MF_PREC_BF16. If `delta` is not
  * NULL it receives delta of the last sweep (-1 when n_sweeps is 0). The call is
  * synchronous: it waits for its work on `stream` to finish, then returns.
  * Memory: nothing is allocated. All scratch lives in one fixed array of about 4.7 MB

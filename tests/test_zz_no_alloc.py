@@ -17,6 +17,10 @@ from paper_2308_14258_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp32": 1e-5, "bf16": 3e-2}
+# mf_sweep precision that runs the same kernel as the allocation-free sweep: its FP32
+# path is the CUDA-core kernel (mf_sweep's MF_PREC_FP32 runs the tensor-core FP32 kernel
+# for these SDNets, which agrees with it to about 3e-6, not bit for bit)
+SAME_KERNEL = {"fp32": "fp32_simt", "bf16": "bf16"}
 
 
 @pytest.fixture(scope="module")
@@ -43,7 +47,7 @@ def test_noalloc_matches_allocating_sweep_twice(m, prec, lx, ly, width, depth):
     grid.upload(u0)
     mine = torch.from_numpy(u0.copy()).cuda()
     for call in range(2):
-        ref = grid.sweep(net, 1, "M", prec)
+        ref = grid.sweep(net, 1, "M", SAME_KERNEL[prec])
         expect = grid.download().astype(np.float64)
         d = m.sweep_noalloc(mine, lx, ly, net, 1, prec)
         torch.cuda.synchronize()
@@ -80,7 +84,7 @@ def test_noalloc_at_its_size_limit(m, prec):
     grid.upload(u0)
     mine = torch.from_numpy(u0.copy()).cuda()
     for call in range(2):
-        ref = grid.sweep(net, 1, "M", prec)
+        ref = grid.sweep(net, 1, "M", SAME_KERNEL[prec])
         expect = grid.download().astype(np.float64)
         d = m.sweep_noalloc(mine, lx, ly, net, 1, prec)
         got = mine.cpu().numpy().astype(np.float64)
@@ -113,7 +117,7 @@ def test_noalloc_several_sweeps_on_a_side_stream(m, prec):
     net = m.SDNet(weights, 128, 6)
     grid = m.Grid(lx, ly, bc)
     side = torch.cuda.Stream()
-    ref = grid.sweep(net, 3, "M", prec, stream=side)
+    ref = grid.sweep(net, 3, "M", SAME_KERNEL[prec], stream=side)
     expect = grid.download(stream=side).astype(np.float64)
     with torch.cuda.stream(side):
         mine = torch.from_numpy(u0.copy()).to("cuda", non_blocking=False)
