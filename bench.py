@@ -42,14 +42,14 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # DRAM traffic of one SDNet (tensor-core) launch from an ncu capture, valid only while
 # the kernel source is unchanged (keyed by the source hash).
 NCU_TRAFFIC = {
-    # ncu --set full, colour 0 of the L = 64 grid: dram__bytes_read 2.64 MB + write 0.32 MB
-    "75b10fbd1291c16e": 2956288,
+    # ncu --set full, colour 0 of the L = 64 grid: dram__bytes_read 2.636 MB + write 0.312 MB
+    "49df8b9f8596f8af": 2948096,
 }
 # The unit that bounds the same kernel, from the same capture: the MUFU pipe (tanh),
 # sm__pipe_xu_cycles_active of elapsed; the tanh floor is 98,304 tanh per 128-row tile
 # at 16 per clock per SM.
 NCU_MUFU_BUSY = {
-    "75b10fbd1291c16e": 0.7277,
+    "49df8b9f8596f8af": 0.7275,
 }
 
 

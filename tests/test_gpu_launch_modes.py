@@ -143,3 +143,26 @@ def test_launch_mode_validation(m):
     with pytest.raises(m.MFError) as e:
         b.sweep(net, 1, "fp32", launch_mode="sweep")
     assert e.value.status == m.MF_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("width,depth,query", [(64, 4, "full"), (128, 6, "centre"), (64, 3, "centre")])
+def test_batch_whole_sweep_other_shapes(m, width, depth, query):
+    """The whole-sweep launch over a batch (subdomain tables) for width-64 SDNets (two
+    CTAs per SM) and for centre-line queries, against the per-colour launches."""
+    sizes = [(2, 2), (1, 3), (3, 1), (2, 3), (1, 1)] * 3
+    w = I.xavier_sdnet(I.SDNetShape(width, depth), 69, bias_scale=0.1)
+    net = m.SDNet(w, width, depth)
+    bcs, us = [], []
+    for q, (lx, ly) in enumerate(sizes):
+        bc, u = state(lx, ly, 200 + q)
+        bcs.append(bc)
+        us.append(u)
+    outs = {}
+    for mode in ("per_colour", "sweep"):
+        b = m.Batch(sizes, bcs)
+        for q, u in enumerate(us):
+            b.upload(q, u)
+        b.sweep(net, 2, "bf16", query=query, launch_mode=mode)
+        outs[mode] = [b.download(q) for q in range(len(sizes))]
+    for q in range(len(sizes)):
+        assert np.array_equal(outs["sweep"][q], outs["per_colour"][q]), q
