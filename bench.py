@@ -705,10 +705,25 @@ def main():
     e2e_value = aggregate_rate(evals_per_sweep * k_e2e, sum(e2e_ms) / 1e3, world)
     nbytes = grid.nx * grid.ny * 4
 
-    # accuracy of this run's BF16 sweep against the FP64 oracle on sampled subdomains
+    # accuracy of this run's BF16 sweep against the FP64 oracle on sampled subdomains,
+    # and of the GPU's delta and residual (FP32 per point, FP64 sums) against the
+    # oracle's FP64 values on the same grids
     err = None
     cpu = None
+    norms = None
     if rank == 0 and not args.no_cpu_baseline:
+        from oracle import mosaic_flow as orc
+        before = grid.download().astype(np.float64)
+        o1 = grid.sweep(net, 1, "M", "bf16", stream=stream)
+        after1 = grid.download().astype(np.float64)
+        r_max, r_rms = grid.residual(stream=stream)
+        d_ref = orc.delta(after1, before)
+        o_max, o_rms = orc.residual(after1)
+        norms = {"delta": o1.delta, "delta_rel_err_vs_fp64": abs(o1.delta - d_ref) / d_ref,
+                 "residual_max": r_max, "residual_max_rel_err_vs_fp64": abs(r_max - o_max) / o_max,
+                 "residual_rms": r_rms, "residual_rms_rel_err_vs_fp64": abs(r_rms - o_rms) / o_rms,
+                 "how": "GPU reduction (FP32 per point with error-free residual sums, FP64 accumulation) against "
+                        "the FP64 oracle on the same two grids"}
         state = grid.download()
         grid.sweep(net, 1, "M", "bf16", colours=1, stream=stream)
         after = grid.download()
@@ -750,6 +765,7 @@ def main():
         "fp32_simt": {"value": fp32_simt_value, "unit": UNIT, "ms_per_step": sum(ms32s) / ks if ks else None,
                       "kernel": "mlp_fp32_kernel: FFMA and tanhf on the CUDA cores"},
         "err_vs_oracle_bf16_sweep": err,
+        "convergence_norms": norms,
         "centre_lines": {"sweeps_per_s": 1e3 * k_c / sum(cl_ms), "ms_per_sweep": sum(cl_ms) / k_c,
                          "point_evals_per_sweep": n_sub_c, "unit": "sweeps/s",
                          "note": "interface-only sweeps (61 centre-cross points per subdomain, Algorithm 2)"},
