@@ -545,10 +545,13 @@ mf_status run_chunk_fused(mf_trainer* t, int F, const float* G, const FusedTerm 
   float* part32[2] = {t->part, t->part + (size_t)(R[0] / 32) * 3 * H};
   int grid_used = 0;
   TR_CUDA(gemm_boundary(t, G, F, st), "train: boundary GEMM");
-  for (int k = 0; k < 2; ++k)
-    TR_CUDA(mf::tc_first_fwd(t->Bf, t->w, t->w + t->off_b0, term[k].X, term[k].n, R[k], k == 0 ? 4 : 1,
-                             static_cast<uint8_t*>(t->A[0]) + (k == 0 ? 0 : (size_t)nt[0] * tile), st),
-            "train: first layer");
+  // with two or more hidden forward layers the first two-layer launch forms A_0 itself
+  const bool first_in_fwd2 = NH >= 3;
+  if (!first_in_fwd2)
+    for (int k = 0; k < 2; ++k)
+      TR_CUDA(mf::tc_first_fwd(t->Bf, t->w, t->w + t->off_b0, term[k].X, term[k].n, R[k], k == 0 ? 4 : 1,
+                               static_cast<uint8_t*>(t->A[0]) + (k == 0 ? 0 : (size_t)nt[0] * tile), st),
+              "train: first layer");
   // hidden layers 1..NH-1 forward, two per launch where two remain (layer l's output
   // stays on chip as layer l+1's input, besides being stored for the backward pass)
   for (int l = 1; l < NH;) {
@@ -556,6 +559,18 @@ mf_status run_chunk_fused(mf_trainer* t, int F, const float* G, const FusedTerm 
       mf::TcFwd2Params fp{static_cast<const uint8_t*>(t->A[l - 1]), static_cast<uint8_t*>(t->A[l]),
                           static_cast<uint8_t*>(t->A[l + 1]), wimg(l), wimg(l + 1), t->w + t->offb[l],
                           t->w + t->offb[l + 1], nt[0], nt[0] + nt[1], t->status};
+      if (l == 1 && first_in_fwd2) {
+        fp.first = 1;
+        fp.Bf = t->Bf;
+        fp.W0 = t->w;
+        fp.b0 = t->w + t->off_b0;
+        for (int k = 0; k < 2; ++k) {
+          fp.X[k] = term[k].X;
+          fp.n[k] = term[k].n;
+          fp.R[k] = R[k];
+        }
+        fp.A0_out = static_cast<uint8_t*>(t->A[0]);
+      }
       TR_CUDA(mf::tc_layer_fwd2(fp, st), "train: fused two-layer forward");
       l += 2;
     } else {

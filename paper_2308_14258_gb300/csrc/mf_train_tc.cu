@@ -389,14 +389,20 @@ __global__ void __launch_bounds__(kThreadsTc, 1) tc_fwd_kernel(const __grid_cons
 // B operand of layer l+1's MMA, so A_l is never read back from HBM: a pair moves 3 tiles
 // per tile of input instead of the 4 of two single-layer launches.
 // Warps: 0 MMA issuer, 1 loads, 2-9 stage a (layer l: accumulator 1 -> tile X), 10-17
-// stage b (layer l+1: accumulator 2 -> staging tile Y). TMEM: accumulator 1 double-
-// buffered [0, 256), accumulator 2 [256, 384), W_l [384, 448), W_{l+1} [448, 512).
+// stage b (layer l+1: accumulator 2 -> staging tile Y), 18-21 first-layer producers. In
+// the launch of layers 1 and 2 the producers (one thread per feature) form each A_0 tile
+// in its input slot from the per-function boundary term and the points (Eq. 8, the
+// Taylor-mode first layer of tc_first_fwd_kernel) and store it for the backward pass, so
+// A_0 is written once and never read back; otherwise the load warp fills the slots and
+// the producers idle. TMEM: accumulator 1 double-buffered [0, 256), accumulator 2
+// [256, 384), W_l [384, 448), W_{l+1} [448, 512).
 // Shared memory: three input slots, two X tiles, two Y tiles (224 KB).
 // Barriers: 1..3 in_full[s]; 4..6 in_empty[s]; 7, 8 acc1_full[b]; 9, 10 acc1_empty[b]
 // (8 warps); 11, 12 x_full[b] (8 warps); 13, 14 x_empty[b] (MMA 2 done); 15 acc2_full;
 // 16 acc2_empty (8 warps); 17 drain.
 constexpr int kF2Stages = 3;
-constexpr int kThreadsF2 = 18 * 32;
+constexpr int kF2Prod = 18;  // first producer warp
+constexpr int kThreadsF2 = (kF2Prod + 4) * 32;
 constexpr int kF2Bars = 18;
 enum {
   kF2InF = 1, kF2InE = 4, kF2A1F = 7, kF2A1E = 9, kF2XF = 11, kF2XE = 13, kF2A2F = 15, kF2A2E = 16,
@@ -472,7 +478,7 @@ __global__ void __launch_bounds__(kThreadsF2, 1) tc_fwd2_kernel(const __grid_con
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
   const uint32_t A1 = tmem, A2 = tmem + 256, W1t = tmem + 384, W2t = tmem + 448;
-  if (warp >= 2) {
+  if (warp >= 2 && warp < kF2Prod) {
     const int stage_b = warp >= 10 ? 1 : 0;
     const int hh = ((warp - 2) >> 2) & 1;
     const uint8_t* img = static_cast<const uint8_t*>(stage_b ? P.wimg2 : P.wimg1);
@@ -526,7 +532,7 @@ __global__ void __launch_bounds__(kThreadsF2, 1) tc_fwd2_kernel(const __grid_con
     }
     __syncwarp();
   } else if (warp == 1) {
-    if (lane == 0) {
+    if (lane == 0 && !P.first) {
       int issued = 0;
       for (int it = 0; it < n_it; ++it) {
         const int s = it % kF2Stages;
@@ -542,6 +548,96 @@ __global__ void __launch_bounds__(kThreadsF2, 1) tc_fwd2_kernel(const __grid_con
         wait_bounded(S.bar(kF2InF + it % kF2Stages), (uint32_t)((it / kF2Stages) & 1), abort_flag, P.status, false);
     }
     __syncwarp();
+  } else if (warp >= kF2Prod) {
+    if (P.first) {
+      // first-layer producers: thread k = feature k; one named barrier (3) per tile before
+      // and after the slot is written, reached by all four warps, aborted or not. The
+      // points' coordinates and the boundary term are fetched one tile ahead (registers,
+      // then the coordinate buffer once every producer is done with the current tile),
+      // so the loads' latency is hidden behind the current tile's arithmetic.
+      const int k = threadIdx.x - kF2Prod * 32;
+      const bool lead = k == 0;
+      const float w2x = P.W0[(size_t)k * 130 + 128], w2y = P.W0[(size_t)k * 130 + 129];
+      const float nlap = -2.0f * (w2x * w2x + w2y * w2y);
+      const float bk0 = P.b0[k];
+      float* coords = reinterpret_cast<float*>(gen + (sBar - base) + 8 * kF2Bars + 64);
+      // tile it's coordinate floats k and k + 128 and the boundary term of its first function
+      auto fetch = [&](int it, float& c0, float& c1, float& bf) {
+        const int t = (int)blockIdx.x + it * (int)gridDim.x;
+        const int term = t < P.n_tiles4 ? 0 : 1;
+        const int PT = term == 0 ? kTR / 4 : kTR, tt = term == 0 ? t : t - P.n_tiles4;
+        const int R = P.R[term], p0 = tt * PT;
+        const float* X = P.X[term] + 2 * (size_t)p0;
+        c0 = k < 2 * PT && p0 + (k >> 1) < R ? __ldg(X + k) : 0.0f;
+        c1 = k + 128 < 2 * PT && p0 + ((k + 128) >> 1) < R ? __ldg(X + k + 128) : 0.0f;
+        bf = p0 < R ? __ldg(P.Bf + (size_t)(p0 / P.n[term]) * kW + k) : 0.0f;
+      };
+      float c0 = 0.0f, c1 = 0.0f, bkf = 0.0f;
+      if (n_it > 0) {
+        fetch(0, c0, c1, bkf);
+        coords[k] = c0;
+        coords[k + 128] = c1;
+      }
+      bool ok = true;
+      for (int it = 0; it < n_it; ++it) {
+        const int s = it % kF2Stages;
+        const int t = (int)blockIdx.x + it * (int)gridDim.x;
+        const float bkt = bkf;
+        if (it + 1 < n_it) fetch(it + 1, c0, c1, bkf);
+        // MMA 1 of the slot's previous tile is done with it ...
+        if (ok && it >= kF2Stages)
+          ok = wait_warp_fast(S.bar(kF2InE + s), (uint32_t)(((it / kF2Stages) - 1) & 1), abort_flag, P.status);
+        // ... and so is the store of that tile's A_0 (at most the two newer ones pending)
+        if (lead) bulk_wait_read<kF2Stages - 1>();
+        named_barrier_sync(3, 128);
+        const uint32_t ts = sIn + (uint32_t)s * kTile;
+        if (ok) {
+          const int term = t < P.n_tiles4 ? 0 : 1;
+          const int C = term == 0 ? 4 : 1, PT = kTR / C, tt = term == 0 ? t : t - P.n_tiles4;
+          const int R = P.R[term], n = P.n[term], f0 = tt * PT / n;
+          for (int p = 0; p < PT; p += 8) {
+            const int pt0 = tt * PT + p;
+            if (pt0 >= R) {
+              for (int c = 0; c < C; ++c) st_shared_v4(ts + tile_chunk(k, (c * PT + p) >> 3), 0u, 0u, 0u, 0u);
+              continue;
+            }
+            const int f = pt0 / n;
+            const float bk = (f == f0 ? bkt : __ldg(P.Bf + (size_t)f * kW + k)) + bk0;
+            uint32_t w[4][4];
+#pragma unroll
+            for (int i = 0; i < 8; i += 2) {
+              float o[4][2];
+#pragma unroll
+              for (int u = 0; u < 2; ++u) {
+                const float2 xy = *reinterpret_cast<const float2*>(coords + 2 * (p + i + u));
+                float a, sd;
+                tanh_sech2(fmaf(w2y, xy.y, fmaf(w2x, xy.x, bk)), a, sd);
+                o[0][u] = a;
+                o[1][u] = sd * w2x;
+                o[2][u] = sd * w2y;
+                o[3][u] = a * sd * nlap;
+              }
+#pragma unroll
+              for (int c = 0; c < 4; ++c) w[c][i >> 1] = pack2(o[c][0], o[c][1]);
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+              if (c < C) st_shared_v4(ts + tile_chunk(k, (c * PT + p) >> 3), w[c][0], w[c][1], w[c][2], w[c][3]);
+          }
+          fence_proxy_async_smem();
+        }
+        named_barrier_sync(3, 128);
+        if (lead && ok && !*abort_flag) {
+          bulk_s2g(P.A0_out + (size_t)t * kTile, ts, kTile);
+          bulk_commit();
+          mbar_arrive(S.bar(kF2InF + s));
+        }
+        // every producer has read this tile's coordinates: the next tile's replace them
+        coords[k] = c0;
+        coords[k + 128] = c1;
+      }
+      if (lead) bulk_wait_all<0>();
+    }
   } else {
     const bool stage_b = warp >= 10;
     const int e = warp - (stage_b ? 10 : 2);  // 0..7 within the stage
@@ -1526,7 +1622,7 @@ __global__ void tc_sum_float_kernel(const float* __restrict__ part, int n, float
 
 constexpr size_t kFwdSmem = 1024 + kStagesF * kTile + 2 * kTile + 8 * kFwdBars + 16 + 64;
 constexpr size_t kBwdSmem = 1024 + (kSlotsA + kSlotsG + 2) * kTile + 8 * kBwdBars + 16 + 64;
-constexpr size_t kFwd2Smem = 1024 + (kF2Stages + 4) * kTile + 8 * kF2Bars + 16 + 64;
+constexpr size_t kFwd2Smem = 1024 + (kF2Stages + 4) * kTile + 8 * kF2Bars + 64 + 1024;  // + point coordinates
 static_assert(kFwd2Smem <= 232448, "two-layer forward kernel shared memory");
 static_assert(kFwdSmem <= 232448, "forward kernel shared memory");
 static_assert(kBwdSmem <= 232448, "backward kernel shared memory");

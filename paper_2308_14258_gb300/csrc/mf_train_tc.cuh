@@ -33,6 +33,16 @@ struct TcFwd2Params {
   int n_tiles4;
   int n_tiles;
   int* status;
+  // first = 1 (layers 1 and 2): A_{l-1} = A_0 is formed in the launch from the first
+  // layer (Eq. 8) instead of loaded from A_in, and stored to A0_out for the backward pass
+  int first;
+  const float* Bf;       // [F][128] W1 g per function (b0 not included)
+  const float* W0;       // [128][130] first-layer weights (W1 | W2)
+  const float* b0;       // [128]
+  const float* X[2];     // points of the collocation term [0] and the data term [1]
+  int n[2];              // points per function of each term
+  int R[2];              // points of each term
+  uint8_t* A0_out;       // tiles of A_0
 };
 
 // One loss term of a backward launch: [0] the collocation points (four channels, the
