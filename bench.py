@@ -291,14 +291,17 @@ def run_reference(args, world, rank):
 def train_tile_traffic(F, Nc, Nb, NH):
     """Algorithmic HBM bytes of one fused training step: a layer's activations (or
     gradients) are one buffer of 32 KB tiles of 128 GEMM rows (four Taylor channels of
-    32 collocation points, or 128 data points). The first layer writes A_0 (1 pass);
-    each two-layer forward launch reads A_{l-1} and writes A_l, A_{l+1} (3 passes, for
-    hidden layers 1..NH-1); the top backward reads A_{NH-1} and writes gA (2); each
-    hidden backward layer reads A_{l-1}, gA_l and writes gA_{l-1} (3, layers NH-1..2);
-    layer 1 reads A_0 and gA_1 (2)."""
+    32 collocation points, or 128 data points). Each two-layer forward launch reads
+    A_{l-1} and writes A_l, A_{l+1} (3 passes, for hidden layers 1..NH-1), a single-layer
+    one reads and writes one (2); the first of them forms A_0 on chip and writes it
+    instead of reading it (3), and only with one hidden layer does a first-layer kernel
+    write A_0 (1 pass) for a forward launch to read. The top backward reads A_{NH-1} and
+    writes gA (2); each hidden backward layer reads A_{l-1}, gA_l and writes gA_{l-1} (3,
+    layers NH-1..2); layer 1 reads A_0 and gA_1 (2)."""
     tiles = 4 * F * Nc // 128 + (F * Nb + 127) // 128
     buf = tiles * 32 * 1024
-    passes = 1 + 3 * ((NH - 1) // 2) + (2 if (NH - 1) % 2 else 0) + 2 + 3 * (NH - 2) + 2
+    fwd = 3 * ((NH - 1) // 2) + (2 if (NH - 1) % 2 else 0) + (0 if NH >= 3 else 1)
+    passes = fwd + 2 + 3 * (NH - 2) + 2
     return passes * buf
 
 

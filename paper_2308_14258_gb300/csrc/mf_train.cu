@@ -318,47 +318,69 @@ __global__ void convert_kernel(const float* __restrict__ src, T* __restrict__ ds
     dst[i] = to_t<T>(src[i]);
 }
 
-__global__ void sgd_kernel(float* __restrict__ w, const float* __restrict__ g, float lr, size_t n) {
+// True when the gradient pass that precedes an update succeeded: no kernel wait gave up
+// and both loss terms are finite. The update kernels read it on the device and do
+// nothing otherwise, so a failed step leaves the weights and moments as they were.
+__device__ __forceinline__ bool grad_pass_ok(const int* status, const double* loss) {
+  return *status == mf::kDevErrNone && isfinite(loss[1]) && isfinite(loss[2]);
+}
+
+__global__ void sgd_kernel(float* __restrict__ w, const float* __restrict__ g, float lr, size_t n,
+                           const int* __restrict__ status, const double* __restrict__ loss) {
+  if (!grad_pass_ok(status, loss)) return;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     w[i] -= lr * g[i];
 }
 
-// LAMB stage 1: moments and the raw update r (You et al., ICLR 2020).
-__global__ void lamb_moments_kernel(const float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
-                                    float* __restrict__ v, float* __restrict__ r, size_t n, float b1, float b2,
-                                    float c1, float c2, float eps, float wd) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const float gi = g[i];
+// LAMB (You et al., ICLR 2020), one block per parameter tensor (W0, b0, each W_l and
+// b_l, w_out, b_out): the moments and the raw update r of every element, then ||w||
+// and ||r|| of the tensor (per-thread FP64 sums, combined in a fixed order), then the
+// trust-ratio step w -= lr (||w|| / ||r||) r. One launch for the whole update.
+constexpr int kLambThreads = 1024;
+__global__ void __launch_bounds__(kLambThreads) lamb_kernel(float* __restrict__ w, const float* __restrict__ g,
+                                                            float* __restrict__ m, float* __restrict__ v,
+                                                            float* __restrict__ r,
+                                                            const unsigned long long* __restrict__ ranges, float lr,
+                                                            float b1, float b2, float c1, float c2, float eps,
+                                                            float wd, const int* __restrict__ status,
+                                                            const double* __restrict__ loss) {
+  if (!grad_pass_ok(status, loss)) return;
+  const size_t b = ranges[2 * blockIdx.x], e = ranges[2 * blockIdx.x + 1];
+  double aw = 0.0, ar = 0.0;
+#pragma unroll 4
+  for (size_t i = b + threadIdx.x; i < e; i += kLambThreads) {
+    const float gi = g[i], wi = w[i];
     const float mi = b1 * m[i] + (1.f - b1) * gi;
     const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    const float ri = (mi / c1) / (sqrtf(vi / c2) + eps) + wd * wi;
     m[i] = mi;
     v[i] = vi;
-    r[i] = (mi / c1) / (sqrtf(vi / c2) + eps) + wd * w[i];
+    r[i] = ri;
+    aw += (double)wi * wi;
+    ar += (double)ri * ri;
   }
-}
-
-// LAMB stage 2: per parameter tensor, ||w|| and ||r|| (one block per tensor, fixed
-// order) and the trust-ratio step w -= lr * (||w|| / ||r||) * r.
-__global__ void lamb_apply_kernel(float* __restrict__ w, const float* __restrict__ r,
-                                  const unsigned long long* __restrict__ ranges, float lr) {
-  const size_t b = ranges[2 * blockIdx.x], e = ranges[2 * blockIdx.x + 1];
-  __shared__ double sw[256], sr[256];
-  double aw = 0.0, ar = 0.0;
-  for (size_t i = b + threadIdx.x; i < e; i += blockDim.x) {
-    aw += (double)w[i] * w[i];
-    ar += (double)r[i] * r[i];
+  __shared__ double sw[kLambThreads / 32], sr[kLambThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    aw += __shfl_down_sync(0xffffffffu, aw, o);
+    ar += __shfl_down_sync(0xffffffffu, ar, o);
   }
-  sw[threadIdx.x] = aw;
-  sr[threadIdx.x] = ar;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { sw[warp] = aw; sr[warp] = ar; }
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) { sw[threadIdx.x] += sw[threadIdx.x + o]; sr[threadIdx.x] += sr[threadIdx.x + o]; }
-    __syncthreads();
+  if (warp == 0) {
+    aw = sw[lane];
+    ar = sr[lane];
+    for (int o = 16; o > 0; o >>= 1) {
+      aw += __shfl_down_sync(0xffffffffu, aw, o);
+      ar += __shfl_down_sync(0xffffffffu, ar, o);
+    }
+    if (lane == 0) { sw[0] = aw; sr[0] = ar; }
   }
+  __syncthreads();
   const double wn = sqrt(sw[0]), rn = sqrt(sr[0]);
   const float trust = (wn > 0.0 && rn > 0.0) ? (float)(wn / rn) : 1.f;
-  __syncthreads();
-  for (size_t i = b + threadIdx.x; i < e; i += blockDim.x) w[i] -= lr * trust * r[i];
+  // each thread steps the elements whose r it wrote
+  for (size_t i = b + threadIdx.x; i < e; i += kLambThreads) w[i] -= lr * trust * r[i];
 }
 
 }  // namespace
@@ -695,11 +717,9 @@ mf_status run_term(mf_trainer* t, int C, int F, int n, const float* G, const flo
 mf_status refresh_gemm_weights(mf_trainer* t, cudaStream_t st) {
   const size_t HH = (size_t)t->H * t->H;
   if (t->fused) {
-    const size_t img = mf::tc_image_bytes();
-    for (int l = 1; l <= t->NH; ++l) {
-      char* base = static_cast<char*>(t->timg) + (size_t)(l - 1) * 2 * img;
-      TR_CUDA(mf::tc_pack_weights(t->w + t->offW[l], base, base + img, st), "train: weight images");
-    }
+    mf::TcPackLayers L{};
+    for (int l = 1; l <= t->NH; ++l) L.W[l - 1] = t->w + t->offW[l];
+    TR_CUDA(mf::tc_pack_layers(L, t->NH, t->timg, st), "train: weight images");
     return MF_OK;
   }
   for (int l = 1; l <= t->NH; ++l) {
@@ -710,6 +730,42 @@ mf_status refresh_gemm_weights(mf_trainer* t, cudaStream_t st) {
       convert_kernel<float><<<64, 256, 0, st>>>(t->w + t->offW[l], static_cast<float*>(t->wq) + (l - 1) * HH, HH);
   }
   TR_CUDA(cudaGetLastError(), "train: weight copy");
+  return MF_OK;
+}
+
+// The gradient pass of one step, enqueued on st (Algorithm 1, steps 1-2: the data points'
+// value channel, the collocation points' four Taylor channels): gradients into t->g, the
+// loss into t->loss, and the loss and the device status word copied to pinned host
+// memory. The caller synchronises st and then calls grad_outcome.
+mf_status enqueue_grad(mf_trainer* t, int F, int Nc, int Nb, const float* G, const float* Xc, const float* Xb,
+                       const float* Yb, cudaStream_t st) {
+  TR_CUDA(cudaMemsetAsync(t->g, 0, t->n_params * 4, st), "train: zero grads");
+  TR_CUDA(cudaMemsetAsync(t->loss, 0, 3 * sizeof(double), st), "train: zero loss");
+  TR_CUDA(cudaMemsetAsync(t->status, 0, sizeof(int), st), "train: reset status");
+  mf_status s;
+  if (t->fused) {
+    s = run_terms_fused(t, F, Nc, Nb, G, Xc, Xb, Yb, st);
+  } else {
+    s = run_term(t, 1, F, Nb, G, Xb, Yb, t->loss + 1, st);
+    if (s == MF_OK) s = run_term(t, 4, F, Nc, G, Xc, nullptr, t->loss + 2, st);
+  }
+  if (s != MF_OK) return s;
+  TR_CUDA(cudaMemcpyAsync(t->h_loss, t->loss, 3 * sizeof(double), cudaMemcpyDeviceToHost, st), "train: loss");
+  TR_CUDA(cudaMemcpyAsync(t->h_status, t->status, sizeof(int), cudaMemcpyDeviceToHost, st), "train: status");
+  return MF_OK;
+}
+
+// The outcome of a synchronised gradient pass: MF_ERR_TIMEOUT if a kernel wait gave up,
+// MF_ERR_DIVERGED if a loss term is not finite; the loss (total, data, PDE) into loss3.
+mf_status grad_outcome(mf_trainer* t, double* loss3, const char* who) {
+  if (*t->h_status != mf::kDevErrNone) return tfail(MF_ERR_TIMEOUT, std::string(who) + ": a kernel wait timed out");
+  if (loss3) {
+    loss3[1] = t->h_loss[1];
+    loss3[2] = t->h_loss[2];
+    loss3[0] = loss3[1] + loss3[2];
+  }
+  if (!std::isfinite(t->h_loss[1]) || !std::isfinite(t->h_loss[2]))
+    return tfail(MF_ERR_DIVERGED, std::string(who) + ": loss is not finite");
   return MF_OK;
 }
 
@@ -910,55 +966,47 @@ mf_status mf_train_grad(mf_trainer* t, int F, int Nc, int Nb, const float* G, co
   if (s != MF_OK) return s;
   TR_ON_DEVICE(t->device, "mf_train_grad");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  TR_CUDA(cudaMemsetAsync(t->g, 0, t->n_params * 4, st), "mf_train_grad: zero grads");
-  TR_CUDA(cudaMemsetAsync(t->loss, 0, 3 * sizeof(double), st), "mf_train_grad: zero loss");
-  TR_CUDA(cudaMemsetAsync(t->status, 0, sizeof(int), st), "mf_train_grad: reset status");
-  // Algorithm 1, step 1: data points (value channel only); step 2: collocation points
-  // (four Taylor channels); the gradients of both terms accumulate in t->g.
-  if (t->fused) {
-    s = run_terms_fused(t, F, Nc, Nb, G, Xc, Xb, Yb, st);
-  } else {
-    s = run_term(t, 1, F, Nb, G, Xb, Yb, t->loss + 1, st);
-    if (s == MF_OK) s = run_term(t, 4, F, Nc, G, Xc, nullptr, t->loss + 2, st);
-  }
+  s = enqueue_grad(t, F, Nc, Nb, G, Xc, Xb, Yb, st);
   if (s != MF_OK) return s;
-  TR_CUDA(cudaMemcpyAsync(t->h_loss, t->loss, 3 * sizeof(double), cudaMemcpyDeviceToHost, st), "mf_train_grad: loss");
-  TR_CUDA(cudaMemcpyAsync(t->h_status, t->status, sizeof(int), cudaMemcpyDeviceToHost, st), "mf_train_grad: status");
   TR_CUDA(cudaStreamSynchronize(st), "mf_train_grad: synchronize");
-  if (*t->h_status != mf::kDevErrNone) return tfail(MF_ERR_TIMEOUT, "mf_train_grad: a kernel wait timed out");
-  if (loss3) {
-    loss3[1] = t->h_loss[1];
-    loss3[2] = t->h_loss[2];
-    loss3[0] = loss3[1] + loss3[2];
-  }
-  if (!std::isfinite(t->h_loss[1]) || !std::isfinite(t->h_loss[2]))
-    return tfail(MF_ERR_DIVERGED, "mf_train_grad: loss is not finite");
-  return MF_OK;
+  return grad_outcome(t, loss3, "mf_train_grad");
 }
 
 mf_status mf_train_step(mf_trainer* t, int F, int Nc, int Nb, const float* G, const float* Xc, const float* Xb,
                         const float* Yb, float lr, double* loss3, void* stream) {
+  if (!t) return tfail(MF_ERR_INVALID_ARG, "mf_train_step: null trainer");
   if (!std::isfinite(lr)) return tfail(MF_ERR_INVALID_ARG, "mf_train_step: lr must be finite");
-  mf_status s = mf_train_grad(t, F, Nc, Nb, G, Xc, Xb, Yb, loss3, stream);
+  mf_status s = validate_batch(t, F, Nc, Nb, G, Xc, Xb, Yb);
   if (s != MF_OK) return s;
   TR_ON_DEVICE(t->device, "mf_train_step");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (t->optimizer == MF_OPT_SGD) {
-    sgd_kernel<<<256, 256, 0, st>>>(t->w, t->g, lr, t->n_params);
+  s = enqueue_grad(t, F, Nc, Nb, G, Xc, Xb, Yb, st);
+  if (s != MF_OK) return s;
+  // the update follows the gradient pass on the stream without a host round trip: its
+  // kernels read the pass's status word and loss on the device and skip the update if
+  // the pass failed (the host reports the failure after the one synchronisation)
+  const bool lamb = t->optimizer != MF_OPT_SGD;
+  if (!lamb) {
+    sgd_kernel<<<256, 256, 0, st>>>(t->w, t->g, lr, t->n_params, t->status, t->loss);
   } else {
     ++t->step;
     // bias corrections in double: 1 - beta^k cancels badly in FP32 for beta near 1
     const float c1 = (float)(1.0 - pow((double)t->beta1, t->step));
     const float c2 = (float)(1.0 - pow((double)t->beta2, t->step));
-    lamb_moments_kernel<<<256, 256, 0, st>>>(t->w, t->g, t->m, t->v, t->r, t->n_params, t->beta1, t->beta2, c1, c2,
-                                             t->eps, t->wd);
-    lamb_apply_kernel<<<t->n_groups, 256, 0, st>>>(t->w, t->r, t->ranges, lr);
+    lamb_kernel<<<t->n_groups, kLambThreads, 0, st>>>(t->w, t->g, t->m, t->v, t->r, t->ranges, lr, t->beta1,
+                                                      t->beta2, c1, c2, t->eps, t->wd, t->status, t->loss);
   }
-  TR_CUDA(cudaGetLastError(), "mf_train_step: update");
-  s = refresh_gemm_weights(t, st);
-  if (s != MF_OK) return s;
-  TR_CUDA(cudaStreamSynchronize(st), "mf_train_step: synchronize");
-  return MF_OK;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) s = refresh_gemm_weights(t, st);
+  const cudaError_t es = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = es;
+  if (e != cudaSuccess || s != MF_OK) {
+    if (lamb) --t->step;
+    return e != cudaSuccess ? tcuda(e, "mf_train_step: update") : s;
+  }
+  s = grad_outcome(t, loss3, "mf_train_step");
+  if (s != MF_OK && lamb) --t->step;  // the update was skipped on the device
+  return s;
 }
 
 }  // extern "C"

@@ -13,6 +13,7 @@
 // shared memory, products are accumulated in FP32, and every sum over rows or functions
 // is taken in a fixed order (per-block partials added by one ordered column sum), so the
 // results do not depend on timing.
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -21,6 +22,8 @@
 
 namespace mf {
 namespace {
+
+namespace cg = cooperative_groups;
 
 constexpr int kNB = 128;     // boundary values per function (columns of W1)
 constexpr int kLd0 = kNB + 2;  // row length of W0 in the packed weights
@@ -57,24 +60,52 @@ __global__ void boundary_fwd_kernel(const float* __restrict__ W0, const float* _
     if (f0 + q < F) Bf[(size_t)(f0 + q) * H + j] = acc[q];
 }
 
-// gW0[j][k] += sum_f S[f][j] G[f][k] for k < 128: block (j-tile, k-tile) of 32 x 32
-// outputs, the functions streamed through shared memory 32 at a time, in order.
-__global__ void boundary_grad_kernel(const float* __restrict__ S, const float* __restrict__ G, int F, int H,
-                                     float* __restrict__ gW0) {
+// gW0[j][k] += sum_f S[f][j] G[f][k] for k < 128: output tiles of 32 x 32. The functions
+// are split into kGradSplit consecutive ranges, one CTA of a thread-block cluster each
+// (the ranges streamed through shared memory 32 functions at a time, in order); the
+// cluster's first CTA then adds the CTAs' partial tiles in rank order, read through
+// distributed shared memory, so the sum does not depend on timing.
+constexpr int kGradSplit = 8;
+__global__ void __cluster_dims__(1, 1, kGradSplit) __launch_bounds__(256)
+    boundary_grad_kernel(const float* __restrict__ S, const float* __restrict__ G, int F, int H,
+                         float* __restrict__ gW0) {
   __shared__ float ss[32][33], sg[32][33];
-  const int tk = threadIdx.x & 31, tj = threadIdx.x >> 5;
+  __shared__ float part[32 * 32];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int tk = threadIdx.x & 31, tr = threadIdx.x >> 5;  // this thread: rows tr + 8 i, column tk
   const int j0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
-  float acc = 0.f;
-  for (int f0 = 0; f0 < F; f0 += 32) {
-    const int f = f0 + tj;  // row of the tiles this thread loads
-    ss[tj][tk] = (f < F && j0 + tk < H) ? S[(size_t)f * H + j0 + tk] : 0.f;
-    sg[tj][tk] = f < F ? G[(size_t)f * kNB + k0 + tk] : 0.f;
+  const int per = ((F + kGradSplit - 1) / kGradSplit + 31) & ~31;
+  const int fb = (int)cluster.block_rank() * per, fe = min(F, fb + per);
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int f0 = fb; f0 < fe; f0 += 32) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = tr + 8 * i, f = f0 + r;
+      ss[r][tk] = (f < fe && j0 + tk < H) ? S[(size_t)f * H + j0 + tk] : 0.f;
+      sg[r][tk] = f < fe ? G[(size_t)f * kNB + k0 + tk] : 0.f;
+    }
     __syncthreads();
 #pragma unroll 8
-    for (int q = 0; q < 32; ++q) acc = fmaf(ss[q][tj], sg[q][tk], acc);
+    for (int q = 0; q < 32; ++q) {
+      const float gq = sg[q][tk];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) acc[i] = fmaf(ss[q][tr + 8 * i], gq, acc[i]);
+    }
     __syncthreads();
   }
-  if (j0 + tj < H) gW0[(size_t)(j0 + tj) * kLd0 + k0 + tk] += acc;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) part[(tr + 8 * i) * 32 + tk] = acc[i];
+  cluster.sync();
+  if (cluster.block_rank() == 0) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int jj = tr + 8 * i;
+      float sum = 0.f;
+      for (int c = 0; c < kGradSplit; ++c) sum += cluster.map_shared_rank(part, c)[jj * 32 + tk];
+      if (j0 + jj < H) gW0[(size_t)(j0 + jj) * kLd0 + k0 + tk] += sum;
+    }
+  }
+  cluster.sync();  // the partial tiles stay in place until the first CTA has read them
 }
 
 // Row products of the GEMM engine: out[r][n] = sum_k in[r][k] M[k][n], with M = W^T
@@ -280,7 +311,7 @@ cudaError_t train_boundary_fwd(const float* W0, const float* G, int F, int H, fl
 cudaError_t train_boundary_grad(const float* S, const float* G, int F, int H, float* gW0, cudaStream_t st) {
   if (F <= 0) return cudaSuccess;
   if (H != 64 && H != 128) return cudaErrorInvalidValue;
-  boundary_grad_kernel<<<dim3(H / 32, kNB / 32), 1024, 0, st>>>(S, G, F, H, gW0);
+  boundary_grad_kernel<<<dim3(H / 32, kNB / 32, kGradSplit), 256, 0, st>>>(S, G, F, H, gW0);
   return cudaGetLastError();
 }
 

@@ -440,6 +440,60 @@ __device__ __forceinline__ void fwd_epilogue_tile(uint32_t acc, bool c4, int hh,
   }
 }
 
+// Warp-uniform bounded wait that sleeps between polls: for the first-layer producers,
+// which run ahead of the MMA issuer, so that their waiting leaves the issue slots to the
+// epilogue warps of the same scheduler.
+__device__ __forceinline__ bool wait_warp_nap(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status) {
+  return __all_sync(0xffffffffu, wait_nap_inl(bar, parity, abort_flag, status));
+}
+
+// One A_0 tile of C channels (PT = 128 / C points from p_begin) into the swizzled tile at
+// ts: thread k (feature k) evaluates the first layer (Eq. 8) in Taylor mode for every
+// point, z = B[f][k] + b0[k] + w2x x + w2y y, and stores tanh z, and for C = 4 also the
+// derivative channels sech^2 z w2x, sech^2 z w2y and -2 tanh z sech^2 z |w2|^2. Point p of
+// the tile is (coords[2p], coords[2p + 1]); bk_first is B[f][k] of the tile's first point.
+template <int C>
+__device__ __forceinline__ void first_layer_tile(uint32_t ts, const float* coords, int k, int p_begin, int R, int n,
+                                                 const float* __restrict__ Bf, float bk_first, float bk0, float w2x,
+                                                 float w2y, float nlap) {
+  constexpr int PT = kTR / C;
+  int fnext = (p_begin / n + 1) * n;  // first point of the next function
+  float bk = bk_first + bk0;
+#pragma unroll 1
+  for (int p = 0; p < PT; p += 8) {
+    const int pt0 = p_begin + p;
+    if (pt0 >= R) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) st_shared_v4(ts + tile_chunk(k, (c * PT + p) >> 3), 0u, 0u, 0u, 0u);
+      continue;
+    }
+    if (pt0 >= fnext) {  // the tile crosses into the next function
+      const int f = pt0 / n;
+      fnext = (f + 1) * n;
+      bk = __ldg(Bf + (size_t)f * kW + k) + bk0;
+    }
+    uint32_t w[C][4];
+#pragma unroll
+    for (int i = 0; i < 8; i += 2) {
+      float o[4][2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const float2 xy = *reinterpret_cast<const float2*>(coords + 2 * (p + i + u));
+        float a, sd;
+        tanh_sech2(fmaf(w2y, xy.y, fmaf(w2x, xy.x, bk)), a, sd);
+        o[0][u] = a;
+        o[1][u] = sd * w2x;
+        o[2][u] = sd * w2y;
+        o[3][u] = a * sd * nlap;
+      }
+#pragma unroll
+      for (int c = 0; c < C; ++c) w[c][i >> 1] = pack2(o[c][0], o[c][1]);
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c) st_shared_v4(ts + tile_chunk(k, (c * PT + p) >> 3), w[c][0], w[c][1], w[c][2], w[c][3]);
+  }
+}
+
 __global__ void __launch_bounds__(kThreadsF2, 1) tc_fwd2_kernel(const __grid_constant__ TcFwd2Params P) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_addr(smem_raw);
@@ -586,44 +640,16 @@ __global__ void __launch_bounds__(kThreadsF2, 1) tc_fwd2_kernel(const __grid_con
         if (it + 1 < n_it) fetch(it + 1, c0, c1, bkf);
         // MMA 1 of the slot's previous tile is done with it ...
         if (ok && it >= kF2Stages)
-          ok = wait_warp_fast(S.bar(kF2InE + s), (uint32_t)(((it / kF2Stages) - 1) & 1), abort_flag, P.status);
+          ok = wait_warp_nap(S.bar(kF2InE + s), (uint32_t)(((it / kF2Stages) - 1) & 1), abort_flag, P.status);
         // ... and so is the store of that tile's A_0 (at most the two newer ones pending)
         if (lead) bulk_wait_read<kF2Stages - 1>();
         named_barrier_sync(3, 128);
         const uint32_t ts = sIn + (uint32_t)s * kTile;
         if (ok) {
-          const int term = t < P.n_tiles4 ? 0 : 1;
-          const int C = term == 0 ? 4 : 1, PT = kTR / C, tt = term == 0 ? t : t - P.n_tiles4;
-          const int R = P.R[term], n = P.n[term], f0 = tt * PT / n;
-          for (int p = 0; p < PT; p += 8) {
-            const int pt0 = tt * PT + p;
-            if (pt0 >= R) {
-              for (int c = 0; c < C; ++c) st_shared_v4(ts + tile_chunk(k, (c * PT + p) >> 3), 0u, 0u, 0u, 0u);
-              continue;
-            }
-            const int f = pt0 / n;
-            const float bk = (f == f0 ? bkt : __ldg(P.Bf + (size_t)f * kW + k)) + bk0;
-            uint32_t w[4][4];
-#pragma unroll
-            for (int i = 0; i < 8; i += 2) {
-              float o[4][2];
-#pragma unroll
-              for (int u = 0; u < 2; ++u) {
-                const float2 xy = *reinterpret_cast<const float2*>(coords + 2 * (p + i + u));
-                float a, sd;
-                tanh_sech2(fmaf(w2y, xy.y, fmaf(w2x, xy.x, bk)), a, sd);
-                o[0][u] = a;
-                o[1][u] = sd * w2x;
-                o[2][u] = sd * w2y;
-                o[3][u] = a * sd * nlap;
-              }
-#pragma unroll
-              for (int c = 0; c < 4; ++c) w[c][i >> 1] = pack2(o[c][0], o[c][1]);
-            }
-#pragma unroll
-            for (int c = 0; c < 4; ++c)
-              if (c < C) st_shared_v4(ts + tile_chunk(k, (c * PT + p) >> 3), w[c][0], w[c][1], w[c][2], w[c][3]);
-          }
+          if (t < P.n_tiles4)
+            first_layer_tile<4>(ts, coords, k, t * (kTR / 4), P.R[0], P.n[0], P.Bf, bkt, bk0, w2x, w2y, nlap);
+          else
+            first_layer_tile<1>(ts, coords, k, (t - P.n_tiles4) * kTR, P.R[1], P.n[1], P.Bf, bkt, bk0, w2x, w2y, nlap);
           fence_proxy_async_smem();
         }
         named_barrier_sync(3, 128);
@@ -1501,11 +1527,15 @@ __global__ void __launch_bounds__(kW) tc_first_bwd_kernel(const float* __restric
   o[2 * kW + j] = sy;
 }
 
-// W (FP32, [out][in]) -> BF16 image in the K-major 128-byte-swizzled operand layout,
-// as W itself (rows = out) or transposed (rows = in).
-__global__ void tc_pack_kernel(const float* __restrict__ W, uint16_t* __restrict__ img, int transpose) {
+// Every hidden layer's W (FP32, [out][in]) -> its two BF16 images in the K-major
+// 128-byte-swizzled operand layout, W itself (rows = out) and W^T (rows = in), in one
+// launch: block (element block, orientation, layer).
+__global__ void tc_pack_kernel(TcPackLayers L, uint16_t* __restrict__ images) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= kW * kW) return;
+  const int transpose = blockIdx.y, l = blockIdx.z;
+  const float* __restrict__ W = L.W[l];
+  uint16_t* img = images + ((size_t)l * 2 + transpose) * (kWImg / 2);
   const int row = idx / kW, k = idx % kW;
   const float v = transpose ? W[(size_t)k * kW + row] : W[(size_t)row * kW + k];
   const uint32_t off = (uint32_t)(k >> 6) * (kW * 128u) + (uint32_t)row * 128u +
@@ -1641,9 +1671,9 @@ int tc_partial_groups() { return 4; }
 size_t tc_image_bytes() { return kWImg; }
 int tc_partial_ctas() { return grid_for(1 << 30); }
 
-cudaError_t tc_pack_weights(const float* W, void* img, void* imgT, cudaStream_t st) {
-  tc_pack_kernel<<<kW * kW / 256, 256, 0, st>>>(W, static_cast<uint16_t*>(img), 0);
-  tc_pack_kernel<<<kW * kW / 256, 256, 0, st>>>(W, static_cast<uint16_t*>(imgT), 1);
+cudaError_t tc_pack_layers(const TcPackLayers& L, int n_layers, void* images, cudaStream_t st) {
+  if (n_layers < 1 || n_layers > kTcMaxLayers) return cudaErrorInvalidValue;
+  tc_pack_kernel<<<dim3(kW * kW / 256, 2, n_layers), 256, 0, st>>>(L, static_cast<uint16_t*>(images));
   return cudaGetLastError();
 }
 

@@ -5,7 +5,12 @@
 
 namespace mf {
 
-constexpr int kTcMaxLayers = 8;  // hidden layers a batched column sum handles
+constexpr int kTcMaxLayers = 8;  // hidden layers a batched column sum or a weight pack handles
+
+// FP32 hidden weight matrices of one weight pack, layer by layer
+struct TcPackLayers {
+  const float* W[kTcMaxLayers];
+};
 
 // Forward of one hidden layer over all tiles: A_out = Taylor-mode tanh(W A_in^T + b).
 // The collocation points' tiles (four Taylor channels) come first, then the data
@@ -89,7 +94,9 @@ int tc_tiles(int R, int C); // tiles of R points with C channels (the last one p
 size_t tc_image_bytes();    // bytes of one 128 x 128 BF16 weight image
 int tc_partial_ctas();      // most CTAs a backward launch uses (partial-buffer rows)
 int tc_partial_groups();    // partial sums per CTA of g_b, g_wout, g_bout and the loss
-cudaError_t tc_pack_weights(const float* W, void* img, void* imgT, cudaStream_t st);
+// hidden weight matrices W_1..W_n (FP32 [128][128] each) -> n (W, W^T) image pairs,
+// back to back from `images` (2 n tc_image_bytes()), in one launch
+cudaError_t tc_pack_layers(const TcPackLayers& L, int n_layers, void* images, cudaStream_t st);
 cudaError_t tc_first_fwd(const float* Bf, const float* W0, const float* b0, const float* X, int n, int R, int C,
                          void* A0, cudaStream_t st);
 cudaError_t tc_first_bwd(const float* Bf, const float* W0, const float* b0, const float* X, int n, int R, int C,

@@ -145,13 +145,15 @@ def test_sgd_step(m, prec):
     assert e2 <= TOL[prec]
 
 
-def test_lamb_steps_match_oracle_update(m):
+@pytest.mark.parametrize("width,depth,prec", [(64, 3, "fp32"), (128, 4, "bf16")])
+def test_lamb_steps_match_oracle_update(m, width, depth, prec):
     """Three LAMB steps: each update equals the oracle's LAMB applied to the GPU's own
-    gradient of that step (the optimiser is checked apart from the gradient)."""
-    width, depth = 64, 3
+    gradient of that step (the optimiser is checked apart from the gradient), on the
+    GEMM engine (width 64) and on the fused engine (width 128, whose weight images are
+    re-packed after every update)."""
     w = I.xavier_sdnet(I.SDNetShape(width, depth), 9, bias_scale=0.1)
     G, Xc, Xb, Yb = to_dev(*batch(2, 64, 128, 9))
-    tr = m.Trainer(w, width, depth, "fp32", "lamb", max_functions=2, max_points=128,
+    tr = m.Trainer(w, width, depth, prec, "lamb", max_functions=2, max_points=128,
                    beta1=0.9, beta2=0.999, eps=1e-6, weight_decay=0.01)
     mm = np.zeros(w.size)
     vv = np.zeros(w.size)
@@ -163,6 +165,32 @@ def test_lamb_steps_match_oracle_update(m):
         got = tr.weights().astype(np.float64)
         step = np.abs(ref - w_before).max()
         assert np.abs(got - ref).max() <= 1e-3 * step + 1e-7, k
+
+
+@pytest.mark.parametrize("opt", ["lamb", "sgd"])
+@pytest.mark.parametrize("width,depth,prec", [(64, 3, "fp32"), (128, 4, "bf16")])
+def test_failed_step_updates_nothing(m, width, depth, prec, opt):
+    """A step whose loss is not finite reports MF_ERR_DIVERGED and updates nothing (the
+    update kernels read the gradient pass's outcome on the device): the weights stay
+    bit-identical, and the next good step equals a fresh trainer's first step, so the
+    moments and the step count were left alone too."""
+    import torch
+    w = I.xavier_sdnet(I.SDNetShape(width, depth), 5, bias_scale=0.1)
+    G, Xc, Xb, Yb = to_dev(*batch(4, 128, 128, 5))
+    bad = Yb.clone()
+    bad[1, 3] = float("nan")
+    tr = m.Trainer(w, width, depth, prec, opt, max_functions=4, max_points=128)
+    w0 = tr.weights().copy()
+    with pytest.raises(m.MFError) as e:
+        tr.step(G, Xc, Xb, bad, 1e-3)
+    assert e.value.status == m.MF_ERR_DIVERGED
+    assert np.array_equal(tr.weights(), w0)
+    tr.step(G, Xc, Xb, Yb, 1e-3)
+    fresh = m.Trainer(w, width, depth, prec, opt, max_functions=4, max_points=128)
+    fresh.step(G, Xc, Xb, Yb, 1e-3)
+    torch.cuda.synchronize()
+    assert np.array_equal(tr.weights(), fresh.weights())
+    assert not np.array_equal(tr.weights(), w0)
 
 
 def test_training_reduces_loss(m):
