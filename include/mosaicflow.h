@@ -366,7 +366,8 @@ mf_status mf_trainer_get_grads(const mf_trainer* trainer, float* dst, int dst_on
  * with N the SDNet of Eq. 7-8 and Delta_x its Laplacian in the query coordinate.
  * Device arrays (FP32, row-major, read only): G [F][128] boundary values of each
  * function (CCW from the corner, as in a subdomain), Xc [F][Nc][2] collocation points,
- * Xb [F][Nb][2] data points, Yb [F][Nb] their targets. Nc and Nb must be multiples of 64
+ * Xb [F][Nb][2] data points, Yb [F][Nb] their targets, each starting on a 16-byte
+ * boundary (the kernels read them 16 bytes at a time). Nc and Nb must be multiples of 64
  * and at most max_points; F >= 1. The gradient stays on the device (mf_trainer_get_grads).
  * If loss3 is not NULL it receives (L, L_data, L_pde) in that order. Synchronises `stream`.
  * Errors: MF_ERR_INVALID_ARG, MF_ERR_DIVERGED (a loss term is not finite),
@@ -376,7 +377,10 @@ mf_status mf_train_grad(mf_trainer* trainer, int F, int Nc, int Nb, const float*
 
 /* mf_train_step -- mf_train_grad followed by the optimiser update with learning rate lr
  * (Algorithm 1, step 4; LAMB as used for SDNet training in Section 5.2). Arguments and
- * errors as mf_train_grad; the weights are not updated when the loss is not finite. */
+ * errors as mf_train_grad. The update is enqueued behind the gradient pass and reads
+ * its outcome on the device: when a loss term is not finite or a wait gave up, the
+ * weights, the optimiser moments and the step count stay as they were. Synchronises
+ * `stream` once. */
 mf_status mf_train_step(mf_trainer* trainer, int F, int Nc, int Nb, const float* G, const float* Xc,
                         const float* Xb, const float* Yb, float lr, double* loss3, void* stream);
 

@@ -772,6 +772,10 @@ mf_status grad_outcome(mf_trainer* t, double* loss3, const char* who) {
 mf_status validate_batch(const mf_trainer* t, int F, int Nc, int Nb, const void* G, const void* Xc, const void* Xb,
                          const void* Yb) {
   if (!G || !Xc || !Xb || !Yb) return tfail(MF_ERR_INVALID_ARG, "mf_train: null input");
+  // the kernels read the inputs in 16-byte vectors and copies
+  if ((reinterpret_cast<uintptr_t>(G) | reinterpret_cast<uintptr_t>(Xc) | reinterpret_cast<uintptr_t>(Xb) |
+       reinterpret_cast<uintptr_t>(Yb)) & 15u)
+    return tfail(MF_ERR_INVALID_ARG, "mf_train: G, Xc, Xb and Yb must start on a 16-byte boundary");
   if (F < 1) return tfail(MF_ERR_INVALID_ARG, "mf_train: F must be >= 1");
   if (Nc < kRB || Nc > t->Nmax || Nc % kRB) return tfail(MF_ERR_INVALID_ARG, "mf_train: Nc must be a multiple of 64 up to max_points");
   if (Nb < kRB || Nb > t->Nmax || Nb % kRB) return tfail(MF_ERR_INVALID_ARG, "mf_train: Nb must be a multiple of 64 up to max_points");

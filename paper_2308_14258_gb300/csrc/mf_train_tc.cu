@@ -1194,6 +1194,7 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
     const float w2x = kFirst ? P.W0[(size_t)j * 130 + 128] : 0.f;
     const float w2y = kFirst ? P.W0[(size_t)j * 130 + 129] : 0.f;
     const float lap = w2x * w2x + w2y * w2y;
+    const float lap6 = 6.0f * lap, lapm2 = -2.0f * lap, m4w2x = -4.0f * w2x, m4w2y = -4.0f * w2y;
     const float b0j = kFirst ? P.b0[j] : 0.f;
     auto epi2_first = [&](int it, int t, auto Cc) {
       constexpr int C = decltype(Cc)::value;
@@ -1255,12 +1256,16 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
             if constexpr (C == 4) {
               const float g0 = __uint_as_float(v[0][i]), g1 = __uint_as_float(v[1][i]);
               const float g2 = __uint_as_float(v[2][i]), g3 = __uint_as_float(v[3][i]);
-              const float td = -2.0f * a * sd;
-              const float tp = -2.0f * sd * sd + 4.0f * a * a * sd;
-              const float gz = g0 * sd + (g1 * w2x + g2 * w2y) * td + g3 * tp * lap;
+              // with s = sech^2 z, ds/dz = -2 tanh z s and d(-2 tanh z s)/dz = s (6 tanh^2 z - 2):
+              //   g_z = s (g0 - 2 a (g1 w2x + g2 w2y) + g3 |w2|^2 (6 a^2 - 2)),
+              //   g_w2x += g_z x + s (g1 - 4 a g3 w2x), g_w2y likewise
+              const float gw = fmaf(g1, w2x, g2 * w2y);
+              const float q = fmaf(lap6, a * a, lapm2);
+              const float gz = sd * fmaf(-2.0f * a, gw, fmaf(g3, q, g0));
+              const float t3 = g3 * a;
               s0 += gz;
-              sx += fmaf(gz, x, fmaf(g1, sd, 2.0f * g3 * td * w2x));
-              sy += fmaf(gz, y, fmaf(g2, sd, 2.0f * g3 * td * w2y));
+              sx = fmaf(sd, fmaf(t3, m4w2x, g1), fmaf(gz, x, sx));
+              sy = fmaf(sd, fmaf(t3, m4w2y, g2), fmaf(gz, y, sy));
             } else {
               const float gz = __uint_as_float(v[0][8 * g8 + i]) * sd;
               s0 += gz;

@@ -260,6 +260,13 @@ def test_invalid_arguments(m):
         tr.grad(G.cpu(), Xc, Xb, Yb)
     with pytest.raises(m.MFError):               # unsupported width
         m.Trainer(I.xavier_sdnet(I.SDNetShape(32, 3), 1), 32, 3, "fp32")
+    # inputs that do not start on a 16-byte boundary are refused before any launch
+    Xc_flat = torch.zeros(Xc.numel() + 2, device="cuda")
+    Xc_odd = Xc_flat[2:].view(Xc.shape)            # 8 bytes past an aligned start
+    Xc_odd.copy_(Xc)
+    with pytest.raises(m.MFError) as e:
+        tr.grad(G, Xc_odd, Xb, Yb)
+    assert e.value.status == m.MF_ERR_INVALID_ARG
     bad = w.copy()
     bad[5] = np.nan
     with pytest.raises(m.MFError):
