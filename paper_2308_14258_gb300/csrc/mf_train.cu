@@ -334,53 +334,56 @@ __global__ void sgd_kernel(float* __restrict__ w, const float* __restrict__ g, f
 
 // LAMB (You et al., ICLR 2020), one block per parameter tensor (W0, b0, each W_l and
 // b_l, w_out, b_out): the moments and the raw update r of every element, then ||w||
-// and ||r|| of the tensor (per-thread FP64 sums, combined in a fixed order), then the
-// trust-ratio step w -= lr (||w|| / ||r||) r. One launch for the whole update.
+// and ||r|| of the tensor, then the trust-ratio step w -= lr (||w|| / ||r||) r. One
+// launch for the whole update. The squares are summed in FP32 per thread (at most a few
+// dozen terms) and per warp (a fixed shuffle tree), and the warp sums in FP64 in warp
+// order, so the norms do not depend on timing; FP64 arithmetic, slow on this part, is
+// kept to the last 32 terms.
 constexpr int kLambThreads = 1024;
 __global__ void __launch_bounds__(kLambThreads) lamb_kernel(float* __restrict__ w, const float* __restrict__ g,
                                                             float* __restrict__ m, float* __restrict__ v,
                                                             float* __restrict__ r,
                                                             const unsigned long long* __restrict__ ranges, float lr,
-                                                            float b1, float b2, float c1, float c2, float eps,
-                                                            float wd, const int* __restrict__ status,
+                                                            float b1, float b2, float inv_c1, float inv_c2,
+                                                            float eps, float wd, const int* __restrict__ status,
                                                             const double* __restrict__ loss) {
   if (!grad_pass_ok(status, loss)) return;
   const size_t b = ranges[2 * blockIdx.x], e = ranges[2 * blockIdx.x + 1];
-  double aw = 0.0, ar = 0.0;
+  float aw = 0.f, ar = 0.f;
 #pragma unroll 4
   for (size_t i = b + threadIdx.x; i < e; i += kLambThreads) {
     const float gi = g[i], wi = w[i];
     const float mi = b1 * m[i] + (1.f - b1) * gi;
     const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-    const float ri = (mi / c1) / (sqrtf(vi / c2) + eps) + wd * wi;
+    const float ri = (mi * inv_c1) / (sqrtf(vi * inv_c2) + eps) + wd * wi;
     m[i] = mi;
     v[i] = vi;
     r[i] = ri;
-    aw += (double)wi * wi;
-    ar += (double)ri * ri;
+    aw = fmaf(wi, wi, aw);
+    ar = fmaf(ri, ri, ar);
   }
-  __shared__ double sw[kLambThreads / 32], sr[kLambThreads / 32];
   for (int o = 16; o > 0; o >>= 1) {
     aw += __shfl_down_sync(0xffffffffu, aw, o);
     ar += __shfl_down_sync(0xffffffffu, ar, o);
   }
+  __shared__ float sw[kLambThreads / 32], sr[kLambThreads / 32];
+  __shared__ float s_trust;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) { sw[warp] = aw; sr[warp] = ar; }
   __syncthreads();
-  if (warp == 0) {
-    aw = sw[lane];
-    ar = sr[lane];
-    for (int o = 16; o > 0; o >>= 1) {
-      aw += __shfl_down_sync(0xffffffffu, aw, o);
-      ar += __shfl_down_sync(0xffffffffu, ar, o);
+  if (threadIdx.x == 0) {
+    double dw = 0.0, dr = 0.0;
+    for (int k = 0; k < kLambThreads / 32; ++k) {
+      dw += (double)sw[k];
+      dr += (double)sr[k];
     }
-    if (lane == 0) { sw[0] = aw; sr[0] = ar; }
+    const double wn = sqrt(dw), rn = sqrt(dr);
+    s_trust = (wn > 0.0 && rn > 0.0) ? (float)(wn / rn) : 1.f;
   }
   __syncthreads();
-  const double wn = sqrt(sw[0]), rn = sqrt(sr[0]);
-  const float trust = (wn > 0.0 && rn > 0.0) ? (float)(wn / rn) : 1.f;
+  const float step = lr * s_trust;
   // each thread steps the elements whose r it wrote
-  for (size_t i = b + threadIdx.x; i < e; i += kLambThreads) w[i] -= lr * trust * r[i];
+  for (size_t i = b + threadIdx.x; i < e; i += kLambThreads) w[i] -= step * r[i];
 }
 
 }  // namespace
@@ -995,10 +998,10 @@ mf_status mf_train_step(mf_trainer* t, int F, int Nc, int Nb, const float* G, co
   } else {
     ++t->step;
     // bias corrections in double: 1 - beta^k cancels badly in FP32 for beta near 1
-    const float c1 = (float)(1.0 - pow((double)t->beta1, t->step));
-    const float c2 = (float)(1.0 - pow((double)t->beta2, t->step));
+    const float inv_c1 = (float)(1.0 / (1.0 - pow((double)t->beta1, t->step)));
+    const float inv_c2 = (float)(1.0 / (1.0 - pow((double)t->beta2, t->step)));
     lamb_kernel<<<t->n_groups, kLambThreads, 0, st>>>(t->w, t->g, t->m, t->v, t->r, t->ranges, lr, t->beta1,
-                                                      t->beta2, c1, c2, t->eps, t->wd, t->status, t->loss);
+                                                      t->beta2, inv_c1, inv_c2, t->eps, t->wd, t->status, t->loss);
   }
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) s = refresh_gemm_weights(t, st);

@@ -1548,24 +1548,33 @@ __global__ void tc_pack_kernel(TcPackLayers L, uint16_t* __restrict__ images) {
   img[off / 2] = bf16_bits(v);
 }
 
+// Sum of p[b * stride] over the rows b = r0, r0 + 8, r0 + 16, ... below r1, in four
+// interleaved partial sums (rows 32k + r0, + 8, + 16, + 24) added in a fixed order, so
+// that four loads are in flight per thread and the result does not depend on timing.
+__device__ __forceinline__ float col_sum_stride8(const float* __restrict__ p, int r0, int r1, size_t stride) {
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+  int b = r0;
+  for (; b + 24 < r1; b += 32) {
+    a0 += p[(size_t)b * stride];
+    a1 += p[(size_t)(b + 8) * stride];
+    a2 += p[(size_t)(b + 16) * stride];
+    a3 += p[(size_t)(b + 24) * stride];
+  }
+  if (b < r1) a0 += p[(size_t)b * stride];
+  if (b + 8 < r1) a1 += p[(size_t)(b + 8) * stride];
+  if (b + 16 < r1) a2 += p[(size_t)(b + 16) * stride];
+  return (a0 + a1) + (a2 + a3);
+}
+
 // out[j] (+)= sum over b < nblk of part[b * stride + j]. A block covers 32 columns with
-// 8 row groups (group r adds rows r, r + 8, ... into two interleaved sums); the group sums
+// 8 row groups (group r adds rows r, r + 8, ... with col_sum_stride8); the group sums
 // are combined in a fixed order, so the result does not depend on timing.
 __global__ void tc_colsum_kernel(const float* __restrict__ part, int nblk, int stride, int n, float* __restrict__ out,
                                  int accumulate) {
   __shared__ float sm[8][32];
   const int c = threadIdx.x & 31, r = threadIdx.x >> 5;
   const int j = blockIdx.x * 32 + c;
-  float s0 = 0.f, s1 = 0.f;
-  if (j < n) {
-    int b = r;
-    for (; b + 8 < nblk; b += 16) {
-      s0 += part[(size_t)b * stride + j];
-      s1 += part[(size_t)(b + 8) * stride + j];
-    }
-    if (b < nblk) s0 += part[(size_t)b * stride + j];
-  }
-  sm[r][c] = s0 + s1;
+  sm[r][c] = j < n ? col_sum_stride8(part + j, r, nblk, (size_t)stride) : 0.f;
   __syncthreads();
   if (r == 0 && j < n) {
     float t = 0.f;
@@ -1585,16 +1594,7 @@ __global__ void tc_colsum_stage1_kernel(const float* __restrict__ part, int nrow
   const int c = threadIdx.x & 31, r = threadIdx.x >> 5;
   const int col = blockIdx.x * 32 + c;
   const int r0 = blockIdx.y * rpc, r1 = min(nrows, r0 + rpc);
-  float s0 = 0.f, s1 = 0.f;
-  if (col < ncols) {
-    int b = r0 + r;
-    for (; b + 8 < r1; b += 16) {
-      s0 += part[(size_t)b * stride + col];
-      s1 += part[(size_t)(b + 8) * stride + col];
-    }
-    if (b < r1) s0 += part[(size_t)b * stride + col];
-  }
-  sm[r][c] = s0 + s1;
+  sm[r][c] = col < ncols ? col_sum_stride8(part + col, r0 + r, r1, (size_t)stride) : 0.f;
   __syncthreads();
   if (r == 0 && col < ncols) {
     float t = 0.f;
@@ -1616,16 +1616,7 @@ __global__ void tc_colsum_layers_kernel(const float* __restrict__ part, size_t l
   const int c = threadIdx.x & 31, r = threadIdx.x >> 5;
   const int j = blockIdx.x * 32 + c;
   const float* pl = part + (size_t)blockIdx.y * layer_stride;
-  float s0 = 0.f, s1 = 0.f;
-  if (j < ncols) {
-    int b = r;
-    for (; b + 8 < nrows; b += 16) {
-      s0 += pl[(size_t)b * ncols + j];
-      s1 += pl[(size_t)(b + 8) * ncols + j];
-    }
-    if (b < nrows) s0 += pl[(size_t)b * ncols + j];
-  }
-  sm[r][c] = s0 + s1;
+  sm[r][c] = j < ncols ? col_sum_stride8(pl + j, r, nrows, (size_t)ncols) : 0.f;
   __syncthreads();
   if (r == 0 && j < ncols) {
     float t = 0.f;
