@@ -31,6 +31,7 @@
 // every other step in the kernels below. The first layer's boundary term and its
 // gradient are the small products of mf_train_gemm.cu in both engines. Reductions use
 // fixed-order block partials throughout, so results do not depend on timing.
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -50,6 +51,8 @@ void set_last_error(const std::string& msg);
 }
 
 namespace {
+
+namespace cg = cooperative_groups;
 
 constexpr int kRB = 64;        // rows per block in the row-tiled kernels
 constexpr int kNB = 128;       // boundary values per function
@@ -332,41 +335,54 @@ __global__ void sgd_kernel(float* __restrict__ w, const float* __restrict__ g, f
     w[i] -= lr * g[i];
 }
 
-// LAMB (You et al., ICLR 2020), one block per parameter tensor (W0, b0, each W_l and
-// b_l, w_out, b_out): the moments and the raw update r of every element, then ||w||
-// and ||r|| of the tensor, then the trust-ratio step w -= lr (||w|| / ||r||) r. One
-// launch for the whole update. The squares are summed in FP32 per thread (at most a few
-// dozen terms) and per warp (a fixed shuffle tree), and the warp sums in FP64 in warp
-// order, so the norms do not depend on timing; FP64 arithmetic, slow on this part, is
-// kept to the last 32 terms.
-constexpr int kLambThreads = 1024;
-__global__ void __launch_bounds__(kLambThreads) lamb_kernel(float* __restrict__ w, const float* __restrict__ g,
-                                                            float* __restrict__ m, float* __restrict__ v,
-                                                            float* __restrict__ r,
-                                                            const unsigned long long* __restrict__ ranges, float lr,
-                                                            float b1, float b2, float inv_c1, float inv_c2,
-                                                            float eps, float wd, const int* __restrict__ status,
-                                                            const double* __restrict__ loss) {
+// LAMB (You et al., ICLR 2020): the moments and the raw update r of every element, then
+// ||w|| and ||r|| of each parameter tensor (W0, b0, each W_l and b_l, w_out, b_out), then
+// the trust-ratio step w -= lr (||w|| / ||r||) r, in one launch. A tensor is one
+// thread-block cluster of kLambSplit CTAs; CTA c takes the c-th of kLambSplit equal
+// slices and keeps its elements' w and r in registers (at most kLambPer per thread).
+// Squares are summed in FP32 per thread and per warp (fixed shuffle tree), the warp sums
+// in FP64 in warp order, and the CTAs' sums in rank order through distributed shared
+// memory, so the norms do not depend on timing; FP64 arithmetic, slow on this part, is
+// kept to the last few terms.
+constexpr int kLambSplit = 8, kLambThreads = 256, kLambPer = 12;
+constexpr size_t kLambMaxTensor = (size_t)kLambSplit * kLambThreads * kLambPer;
+__global__ void __cluster_dims__(kLambSplit, 1, 1) __launch_bounds__(kLambThreads)
+    lamb_kernel(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                const unsigned long long* __restrict__ ranges, float lr, float b1, float b2, float inv_c1,
+                float inv_c2, float eps, float wd, const int* __restrict__ status, const double* __restrict__ loss) {
+  // the same outcome for every CTA of the cluster, so none waits at the cluster barriers
   if (!grad_pass_ok(status, loss)) return;
-  const size_t b = ranges[2 * blockIdx.x], e = ranges[2 * blockIdx.x + 1];
+  cg::cluster_group cluster = cg::this_cluster();
+  const unsigned rank = cluster.block_rank();
+  const int tensor = (int)(blockIdx.x / kLambSplit);
+  const size_t b = ranges[2 * tensor], e = ranges[2 * tensor + 1];
+  const size_t per = (e - b + kLambSplit - 1) / kLambSplit;
+  const size_t cb = b + rank * per, ce = cb + per < e ? cb + per : e;
+  float wr[kLambPer], rr[kLambPer];
   float aw = 0.f, ar = 0.f;
-#pragma unroll 4
-  for (size_t i = b + threadIdx.x; i < e; i += kLambThreads) {
-    const float gi = g[i], wi = w[i];
-    const float mi = b1 * m[i] + (1.f - b1) * gi;
-    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-    const float ri = (mi * inv_c1) / (sqrtf(vi * inv_c2) + eps) + wd * wi;
-    m[i] = mi;
-    v[i] = vi;
-    r[i] = ri;
-    aw = fmaf(wi, wi, aw);
-    ar = fmaf(ri, ri, ar);
+#pragma unroll
+  for (int q = 0; q < kLambPer; ++q) {
+    const size_t i = cb + threadIdx.x + (size_t)q * kLambThreads;
+    wr[q] = rr[q] = 0.f;
+    if (i < ce) {
+      const float gi = g[i], wi = w[i];
+      const float mi = b1 * m[i] + (1.f - b1) * gi;
+      const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+      const float ri = (mi * inv_c1) / (sqrtf(vi * inv_c2) + eps) + wd * wi;
+      m[i] = mi;
+      v[i] = vi;
+      wr[q] = wi;
+      rr[q] = ri;
+      aw = fmaf(wi, wi, aw);
+      ar = fmaf(ri, ri, ar);
+    }
   }
   for (int o = 16; o > 0; o >>= 1) {
     aw += __shfl_down_sync(0xffffffffu, aw, o);
     ar += __shfl_down_sync(0xffffffffu, ar, o);
   }
   __shared__ float sw[kLambThreads / 32], sr[kLambThreads / 32];
+  __shared__ double cta_w, cta_r;
   __shared__ float s_trust;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) { sw[warp] = aw; sr[warp] = ar; }
@@ -377,13 +393,26 @@ __global__ void __launch_bounds__(kLambThreads) lamb_kernel(float* __restrict__ 
       dw += (double)sw[k];
       dr += (double)sr[k];
     }
-    const double wn = sqrt(dw), rn = sqrt(dr);
+    cta_w = dw;
+    cta_r = dr;
+  }
+  cluster.sync();
+  if (threadIdx.x == 0) {
+    double tw = 0.0, tr = 0.0;
+    for (unsigned c = 0; c < kLambSplit; ++c) {
+      tw += *cluster.map_shared_rank(&cta_w, c);
+      tr += *cluster.map_shared_rank(&cta_r, c);
+    }
+    const double wn = sqrt(tw), rn = sqrt(tr);
     s_trust = (wn > 0.0 && rn > 0.0) ? (float)(wn / rn) : 1.f;
   }
-  __syncthreads();
+  cluster.sync();  // s_trust is set, and no CTA leaves while another reads its sums
   const float step = lr * s_trust;
-  // each thread steps the elements whose r it wrote
-  for (size_t i = b + threadIdx.x; i < e; i += kLambThreads) w[i] -= step * r[i];
+#pragma unroll
+  for (int q = 0; q < kLambPer; ++q) {
+    const size_t i = cb + threadIdx.x + (size_t)q * kLambThreads;
+    if (i < ce) w[i] = wr[q] - step * rr[q];
+  }
 }
 
 }  // namespace
@@ -396,7 +425,7 @@ struct mf_trainer {
   size_t Rmax = 0, n_params = 0;
   std::vector<size_t> offW, offb;  // hidden layer l = 1..NH
   size_t off_b0 = 0, off_wout = 0, off_bout = 0;
-  float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr, *r = nullptr;
+  float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
   void* wq = nullptr;              // GEMM copies of the hidden weights [NH][H][H]
   std::vector<void*> A;            // [NH+1] GEMM-type [4][Rmax][H]
   std::vector<float*> Z;           // [NH+1] FP32 [4][Rmax][H] (index 0 unused)
@@ -796,7 +825,7 @@ mf_status mf_destroy_trainer(mf_trainer* t) {
   for (void* p : t->A) cudaFree(p);
   for (float* p : t->Z) cudaFree(p);
   for (float* p : t->a) cudaFree(p);
-  cudaFree(t->w); cudaFree(t->g); cudaFree(t->m); cudaFree(t->v); cudaFree(t->r);
+  cudaFree(t->w); cudaFree(t->g); cudaFree(t->m); cudaFree(t->v);
   cudaFree(t->wq); cudaFree(t->gA); cudaFree(t->gZ); cudaFree(t->Bf); cudaFree(t->S); cudaFree(t->part); cudaFree(t->sums);
   cudaFree(t->lpart); cudaFree(t->loss); cudaFree(t->ranges);
   cudaFree(t->timg); cudaFree(t->tc_gw); cudaFree(t->tc_gb); cudaFree(t->tc_scratch); cudaFree(t->tc_small);
@@ -865,7 +894,6 @@ mf_status mf_create_trainer(mf_ctx* ctx, const mf_train_desc* d, const float* we
   alloc((void**)&t->g, t->n_params * 4);
   alloc((void**)&t->m, t->n_params * 4);
   alloc((void**)&t->v, t->n_params * 4);
-  alloc((void**)&t->r, t->n_params * 4);
   alloc(&t->wq, (size_t)t->NH * HH * es);
   t->A.assign(t->NH + 1, nullptr);
   t->Z.assign(t->NH + 1, nullptr);
@@ -919,6 +947,11 @@ mf_status mf_create_trainer(mf_ctx* ctx, const mf_train_desc* d, const float* we
   rg.push_back(t->off_wout); rg.push_back(t->off_wout + H);
   rg.push_back(t->off_bout); rg.push_back(t->off_bout + 1);
   t->n_groups = (int)rg.size() / 2;
+  for (size_t k = 0; k < rg.size(); k += 2)
+    if (rg[k + 1] - rg[k] > kLambMaxTensor) {
+      mf_destroy_trainer(t);
+      return tfail(MF_ERR_INVALID_ARG, "mf_create_trainer: a parameter tensor exceeds the optimiser's capacity");
+    }
   alloc((void**)&t->ranges, rg.size() * 8);
   if (e == cudaSuccess) e = cudaMemcpy(t->ranges, rg.data(), rg.size() * 8, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(t->w, weights, t->n_params * 4, cudaMemcpyHostToDevice);
@@ -1000,8 +1033,9 @@ mf_status mf_train_step(mf_trainer* t, int F, int Nc, int Nb, const float* G, co
     // bias corrections in double: 1 - beta^k cancels badly in FP32 for beta near 1
     const float inv_c1 = (float)(1.0 / (1.0 - pow((double)t->beta1, t->step)));
     const float inv_c2 = (float)(1.0 / (1.0 - pow((double)t->beta2, t->step)));
-    lamb_kernel<<<t->n_groups, kLambThreads, 0, st>>>(t->w, t->g, t->m, t->v, t->r, t->ranges, lr, t->beta1,
-                                                      t->beta2, inv_c1, inv_c2, t->eps, t->wd, t->status, t->loss);
+    lamb_kernel<<<t->n_groups * kLambSplit, kLambThreads, 0, st>>>(t->w, t->g, t->m, t->v, t->ranges, lr, t->beta1,
+                                                                   t->beta2, inv_c1, inv_c2, t->eps, t->wd, t->status,
+                                                                   t->loss);
   }
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) s = refresh_gemm_weights(t, st);
