@@ -17,14 +17,24 @@ constexpr int kGatherThreads = 256;
 
 // kSubPerBlock subdomains per block (4, 8 or 16; the default 16 has each warp gather
 // two): fewer per block spread a small colour over more SMs, more per block share each
-// weight load among more subdomains.
+// weight load among more subdomains. W1 (128 x H FP32) is staged in shared memory with
+// 16-byte loads issued all at once: read straight from L2 inside the product loop, a
+// few loads in flight per thread left the kernel latency-bound.
 template <int H, int kSubPerBlock>
 __global__ void __launch_bounds__(kGatherThreads)
 gather_boundary_kernel(const float* __restrict__ u, ColourGeom g, const float* __restrict__ W1t,
                        const float* __restrict__ b0, float* __restrict__ B) {
   __shared__ float gs[kSubPerBlock][kNbdry];
+  extern __shared__ float4 w1s4[];  // [128][H / 4]
+  const float* w1s = reinterpret_cast<const float*>(w1s4);
   const int s0 = blockIdx.x * kSubPerBlock;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  {
+    constexpr int kVec = kNbdry * H / 4;
+    const float4* src = reinterpret_cast<const float4*>(W1t);
+#pragma unroll
+    for (int i = 0; i < kVec / kGatherThreads; ++i) w1s4[threadIdx.x + i * kGatherThreads] = __ldg(src + threadIdx.x + i * kGatherThreads);
+  }
 
   // Gather: bottom and top strips are 32 consecutive floats (one 128-byte coalesced
   // request per warp); the left and right strips are one value per grid row.
@@ -53,7 +63,7 @@ gather_boundary_kernel(const float* __restrict__ u, ColourGeom g, const float* _
   for (int i = 0; i < kPer; ++i) acc[i] = 0.f;
 #pragma unroll 4
   for (int k = 0; k < kNbdry; ++k) {
-    const float w = __ldg(W1t + k * H + j);
+    const float w = w1s[k * H + j];
 #pragma unroll
     for (int i = 0; i < kPer; ++i) {
       const int sl = grp + i * kGroups;
@@ -187,11 +197,27 @@ __global__ void zero_interior_kernel(float* __restrict__ u, int nx, int ny) {
 template <int H>
 cudaError_t launch_gather_h(const float* u, const ColourGeom& g, const DevNet& net, float* B, int subs,
                             cudaStream_t st) {
+  constexpr size_t kW1Bytes = (size_t)kNbdry * H * sizeof(float);  // staged W1 (64 KB at H = 128)
+  static PerDevice pd;
+  cudaError_t e = per_device(pd, [](int, int*, size_t*) {
+    cudaError_t e1 = cudaFuncSetAttribute(gather_boundary_kernel<H, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)kW1Bytes);
+    if (e1 == cudaSuccess)
+      e1 = cudaFuncSetAttribute(gather_boundary_kernel<H, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kW1Bytes);
+    if (e1 == cudaSuccess)
+      e1 = cudaFuncSetAttribute(gather_boundary_kernel<H, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kW1Bytes);
+    return e1;
+  });
+  if (e != cudaSuccess) return e;
   const int blocks = (g.n_c + subs - 1) / subs;
   switch (subs) {
-    case 4: gather_boundary_kernel<H, 4><<<blocks, kGatherThreads, 0, st>>>(u, g, net.W1t, net.b0, B); break;
-    case 8: gather_boundary_kernel<H, 8><<<blocks, kGatherThreads, 0, st>>>(u, g, net.W1t, net.b0, B); break;
-    case 16: gather_boundary_kernel<H, 16><<<blocks, kGatherThreads, 0, st>>>(u, g, net.W1t, net.b0, B); break;
+    case 4: gather_boundary_kernel<H, 4><<<blocks, kGatherThreads, kW1Bytes, st>>>(u, g, net.W1t, net.b0, B); break;
+    case 8: gather_boundary_kernel<H, 8><<<blocks, kGatherThreads, kW1Bytes, st>>>(u, g, net.W1t, net.b0, B); break;
+    case 16:
+      gather_boundary_kernel<H, 16><<<blocks, kGatherThreads, kW1Bytes, st>>>(u, g, net.W1t, net.b0, B);
+      break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
