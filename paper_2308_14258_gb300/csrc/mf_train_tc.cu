@@ -984,6 +984,18 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
     };
 
     // ---- epilogue 1 of tile it: g_Z from the recomputed Z and the incoming gradient
+    // layer 1 (kFirst): the first layer's weights of feature j, and this warp's buffers in
+    // the upper half of the staging tile (which layer 1 does not otherwise use): the
+    // coordinates of its points (two tiles x 64 floats) and B[f][j] + b0[j] of their
+    // function (two tiles x 32 lanes). Epilogue 1 of a tile loads them from global memory
+    // at its start and stores them here at its end, so their latency is hidden behind
+    // epilogue 1's work; epilogue 2 of the tile, an iteration later, reads them here.
+    const float w2x = kFirst ? P.W0[(size_t)j * 130 + 128] : 0.f;
+    const float w2y = kFirst ? P.W0[(size_t)j * 130 + 129] : 0.f;
+    const float lap = w2x * w2x + w2y * w2y;
+    const float lap6 = 6.0f * lap, lapm2 = -2.0f * lap, m4w2x = -4.0f * w2x, m4w2y = -4.0f * w2y;
+    const float b0j = kFirst ? P.b0[j] : 0.f;
+    float* first_buf = reinterpret_cast<float*>(gen + (sOut - base) + 16384) + e * 192;  // [2][64] xy, [2][32] B
     auto epi1_c = [&](int it, int t, auto Cc) {
       constexpr int C = decltype(Cc)::value;
       constexpr int PT = kTR / C;   // points per tile
@@ -994,6 +1006,16 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
       const int sgs = it % kSlotsG;
       const uint32_t sg = sG + (uint32_t)sgs * kTile;
       float* rb = red + (it & 1) * (16 * 32);  // top: [4 quarters][4 quadrants][NP points]
+      [[maybe_unused]] float xc0 = 0.f, xc1 = 0.f, bkc = 0.f;
+      if constexpr (kFirst) {
+        // this warp's points' coordinates (NP points, 2 NP floats: lane l takes floats l and
+        // 32 + l) and B + b0 of their function, for epilogue 2 of this tile
+        const int pt_q = tl * PT + p0;
+        const float* Xq = T.X + 2 * (size_t)pt_q;
+        if (lane < 2 * NP && pt_q + (lane >> 1) < T.n_pts) xc0 = __ldg(Xq + lane);
+        if (32 + lane < 2 * NP && pt_q + 16 + (lane >> 1) < T.n_pts) xc1 = __ldg(Xq + 32 + lane);
+        if (pt_q < T.n_pts) bkc = __ldg(P.Bf + (size_t)(pt_q / T.n_per_fn) * kW + j) + b0j;
+      }
       if (ok) ok = wait_warp_fast(S.bar(kBD1F), (uint32_t)(it & 1), abort_flag, P.status);
       if (ok && !top) ok = wait_warp_fast(S.bar(kBGF + sgs), (uint32_t)((it / kSlotsG) & 1), abort_flag, P.status);
       if (ok) tc_fence_after();
@@ -1183,6 +1205,14 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
         __syncwarp();
         if (lane == 0) mbar_arrive(S.bar(kBGZF));
       }
+      if constexpr (kFirst) {
+        __syncwarp();
+        float* fb = first_buf + (it & 1) * 64;
+        fb[lane] = xc0;
+        fb[32 + lane] = xc1;
+        first_buf[128 + (it & 1) * 32 + lane] = bkc;
+        __syncwarp();
+      }
     };
 
     auto tile_of = [&](int it) { return (int)blockIdx.x + it * (int)gridDim.x; };
@@ -1191,11 +1221,6 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
     // goes through the first layer's backward (Eq. 8 in Taylor mode, the formulas of
     // tc_first_bwd_kernel) into per-32-point partial sums of g_z, g_z x + g_zx and
     // g_z y + g_zy for feature j; no gA_0 tile is written.
-    const float w2x = kFirst ? P.W0[(size_t)j * 130 + 128] : 0.f;
-    const float w2y = kFirst ? P.W0[(size_t)j * 130 + 129] : 0.f;
-    const float lap = w2x * w2x + w2y * w2y;
-    const float lap6 = 6.0f * lap, lapm2 = -2.0f * lap, m4w2x = -4.0f * w2x, m4w2y = -4.0f * w2y;
-    const float b0j = kFirst ? P.b0[j] : 0.f;
     auto epi2_first = [&](int it, int t, auto Cc) {
       constexpr int C = decltype(Cc)::value;
       constexpr int PT = kTR / C;
@@ -1204,17 +1229,9 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
       const TcTerm& T = P.term[C == 4 ? 0 : 1];
       const int tl = C == 4 ? t : t - n4;
       const int pt_q = tl * PT + p0;  // this thread's first point
-      const float bk = pt_q < T.n_pts ? P.Bf[(size_t)(pt_q / T.n_per_fn) * kW + j] + b0j : 0.f;
-      // the 8 points' coordinates (four channels) are loaded before the wait on D2
-      float xy4[C == 4 ? 16 : 1];
-      if constexpr (C == 4) {
-        const float4* xp = reinterpret_cast<const float4*>(T.X + 2 * (size_t)pt_q);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const float4 q4 = xp[u];
-          xy4[4 * u] = q4.x; xy4[4 * u + 1] = q4.y; xy4[4 * u + 2] = q4.z; xy4[4 * u + 3] = q4.w;
-        }
-      }
+      // coordinates and B + b0, loaded by this warp's epilogue 1 of the tile
+      const float* xyb = first_buf + (it & 1) * 64;
+      const float bk = first_buf[128 + (it & 1) * 32 + lane];
       uint32_t v[C == 4 ? 4 : 1][C == 4 ? 8 : 32];
       if (ok) ok = wait_warp_fast(S.bar(kBD2F), (uint32_t)(it & 1), abort_flag, P.status);
       if (ok) {
@@ -1237,17 +1254,8 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
           const int pt0 = pt_q + 8 * g8;
           if (pt0 >= T.n_pts) break;  // padding of the value channel's last tile
           float xy[16];
-          if constexpr (C == 4) {
 #pragma unroll
-            for (int u = 0; u < 16; ++u) xy[u] = xy4[u];
-          } else {
-            const float4* xp = reinterpret_cast<const float4*>(T.X + 2 * (size_t)pt0);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const float4 q4 = xp[u];
-              xy[4 * u] = q4.x; xy[4 * u + 1] = q4.y; xy[4 * u + 2] = q4.z; xy[4 * u + 3] = q4.w;
-            }
-          }
+          for (int u = 0; u < 16; ++u) xy[u] = xyb[16 * g8 + u];
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
             const float x = xy[2 * i], y = xy[2 * i + 1];
