@@ -54,6 +54,9 @@ typedef int mf_status;
 #define MF_PREC_BF16 1  /* BF16 weights/activations on tcgen05 tensor cores, FP32 accumulate */
 #define MF_PREC_MIXED 2 /* BF16 sweeps until delta < eps_coarse or stalls, then FP32 refinement */
 #define MF_PREC_FP32_SIMT 3 /* FP32 weights and activations on the CUDA cores (FMA), accurate tanh */
+#define MF_PREC_F16 4   /* F16 weights/activations on the tcgen05 tensor cores, FP32 accumulate: the BF16
+                           kernel with the other 16-bit type (three more mantissa bits, the same speed);
+                           per-colour launches; SDNets whose hidden weights lie within the F16 range */
 
 #define MF_SCHEDULE_MULTIPLICATIVE 0 /* colours 0..3 in turn, each reads the latest grid */
 #define MF_SCHEDULE_ADDITIVE 1       /* all colours read the old grid; overlaps averaged */
@@ -259,8 +262,9 @@ mf_status mf_batch_download(const mf_batch* batch, int problem, float* dst, int 
 
 /* mf_batch_sweep -- multiplicative sweeps (all four colours) of every problem of the
  * batch at once (Section 4.1's batching of atomic subdomains, applied across problems):
- * each colour of all problems is one batch. Options as mf_sweep (precision MF_PREC_FP32
- * or MF_PREC_BF16; MF_QUERY_FULL or MF_QUERY_CENTRE; colours must be 0). delta is taken
+ * each colour of all problems is one batch. Options as mf_sweep (precision MF_PREC_FP32,
+ * MF_PREC_FP32_SIMT, MF_PREC_BF16 or MF_PREC_F16; MF_QUERY_FULL or MF_QUERY_CENTRE;
+ * colours must be 0). delta is taken
  * over all problems' grid points together. Launch modes (opts->launch_mode):
  *  - MF_LAUNCH_PER_COLOUR: per colour one gather launch and one SDNet launch;
  *  - MF_LAUNCH_GRAPH: sweeps after the first are replayed from a CUDA graph of one

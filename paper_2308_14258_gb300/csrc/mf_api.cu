@@ -2,6 +2,7 @@
 // sweep driver (Section 2.4, Section 4.1, Algorithm 2). All arithmetic of the sweep
 // runs in the kernels of this library; this file only validates, allocates, packs and
 // enqueues.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -71,12 +72,19 @@ uint16_t bf16_rne(float f) {
 // BF16 image of one H x H matrix W[n][k] (row n = output unit) as the B operand of
 // tcgen05.mma: K-major, 128-byte swizzle: K blocks of 64 elements, each block holds
 // H rows of 128 bytes, 16-byte chunk c of row n stored at chunk c ^ (n mod 8).
-void pack_sw128(const float* W, int H, uint16_t* img) {
+// f16: F16 elements (round to nearest even) instead of BF16.
+void pack_sw128(const float* W, int H, uint16_t* img, bool f16 = false) {
   for (int n = 0; n < H; ++n)
     for (int k = 0; k < H; ++k) {
       const int kb = k / 64, w = k % 64, chunk = w / 8, e = w % 8;
       const size_t off = (size_t)kb * H * 64 + (size_t)n * 64 + (size_t)((chunk ^ (n & 7)) * 8) + e;
-      img[off] = bf16_rne(W[(size_t)n * H + k]);
+      const float x = W[(size_t)n * H + k];
+      if (f16) {
+        const __half h = __float2half_rn(x);
+        std::memcpy(&img[off], &h, sizeof(uint16_t));
+      } else {
+        img[off] = bf16_rne(x);
+      }
     }
 }
 
@@ -223,7 +231,8 @@ mf_status mf_load_sdnet_ex(mf_ctx* ctx, const mf_sdnet_desc_ex* desc, const floa
     W2[2 * j] = W0[(size_t)j * (n_in + 2) + n_in];
     W2[2 * j + 1] = W0[(size_t)j * (n_in + 2) + n_in + 1];
   }
-  std::vector<uint16_t> img((size_t)NH * H * H);
+  std::vector<uint16_t> img((size_t)NH * H * H), img16((size_t)NH * H * H);
+  bool f16s_ok = true;  // every hidden weight within the F16 range: the F16 sweep is offered
   for (int l = 0; l < NH; ++l) {
     const float* Wl = p;  p += (size_t)H * H;
     const float* bl = p;  p += H;
@@ -231,6 +240,8 @@ mf_status mf_load_sdnet_ex(mf_ctx* ctx, const mf_sdnet_desc_ex* desc, const floa
       for (int k = 0; k < H; ++k) WhT[(size_t)l * H * H + (size_t)k * H + n] = Wl[(size_t)n * H + k];
     std::memcpy(&bh[(size_t)l * H], bl, sizeof(float) * H);
     pack_sw128(Wl, H, &img[(size_t)l * H * H]);
+    for (size_t i = 0; i < (size_t)H * H; ++i) f16s_ok = f16s_ok && std::fabs(Wl[i]) < 65504.0f;
+    if (f16s_ok) pack_sw128(Wl, H, &img16[(size_t)l * H * H], true);
   }
   const float* wout = p;  p += H;
   const float bout = *p;
@@ -239,7 +250,8 @@ mf_status mf_load_sdnet_ex(mf_ctx* ctx, const mf_sdnet_desc_ex* desc, const floa
   MF_ON_DEVICE(ctx->device, "mf_load_sdnet: cudaSetDevice");
   mf_sdnet* net = new mf_sdnet();
   net->device = ctx->device;
-  // one allocation: W1t | W2 | b0 | WhT | bh | wout | BF16 images | conv (each 256-byte aligned)
+  // one allocation: W1t | W2 | b0 | WhT | bh | wout | BF16 images | conv | F16 split images |
+  // F16 images (each 256-byte aligned)
   auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t sz_W1t = up(W1t.size() * 4), sz_W2 = up(W2.size() * 4), sz_b0 = up((size_t)H * 4),
                sz_WhT = up(WhT.size() * 4), sz_bh = up(bh.size() * 4), sz_wout = up((size_t)H * 4),
@@ -249,7 +261,8 @@ mf_status mf_load_sdnet_ex(mf_ctx* ctx, const mf_sdnet_desc_ex* desc, const floa
   bool f16_ok = H == 128;
   for (size_t i = 0; f16_ok && i < WhT.size(); ++i) f16_ok = std::fabs(WhT[i]) < 65504.0f;
   const size_t sz_f16 = f16_ok ? up(mf::f32tc_image_bytes(NH)) : 0;
-  const size_t total = sz_W1t + sz_W2 + sz_b0 + sz_WhT + sz_bh + sz_wout + sz_img + sz_conv + sz_f16;
+  const size_t sz_img16 = f16s_ok ? sz_img : 0;
+  const size_t total = sz_W1t + sz_W2 + sz_b0 + sz_WhT + sz_bh + sz_wout + sz_img + sz_conv + sz_f16 + sz_img16;
   cudaError_t e = cudaMalloc(&net->dmem, total);
   if (e != cudaSuccess) {
     delete net;
@@ -272,8 +285,9 @@ mf_status mf_load_sdnet_ex(mf_ctx* ctx, const mf_sdnet_desc_ex* desc, const floa
   net->d.wimg_bf16 = place(img.data(), img.size() * 2, sz_img);
   const float* conv = (const float*)place(w, n_conv * 4, sz_conv);  // cw1 | cb1 | cw2 | cb2, as packed
   void* f16img = f16_ok ? place(nullptr, 0, sz_f16) : nullptr;
+  const void* img16_d = f16s_ok ? place(img16.data(), img16.size() * 2, sz_img16) : nullptr;
   if (!net->d.W1t || !net->d.W2 || !net->d.b0 || !net->d.WhT || !net->d.bh || !net->d.wout || !net->d.wimg_bf16 ||
-      !conv) {
+      !conv || (f16s_ok && !img16_d)) {
     cudaError_t err = cudaGetLastError();
     cudaFree(net->dmem);
     delete net;
@@ -293,6 +307,7 @@ mf_status mf_load_sdnet_ex(mf_ctx* ctx, const mf_sdnet_desc_ex* desc, const floa
   net->d.bout = bout;
   net->d.wimg_bytes = img.size() * 2;
   net->d.wimg_f16 = nullptr;
+  net->d.wimg_f16s = img16_d;
   if (f16img) {
     cudaError_t pe = mf::f32tc_pack(net->d.WhT, NH, f16img, nullptr);
     if (pe == cudaSuccess) pe = cudaDeviceSynchronize();
@@ -416,7 +431,7 @@ mf_status sweep_impl(mf_grid* g, const mf_sdnet* net, const mf_sweep_opts* o, mf
   if (o->schedule != MF_SCHEDULE_MULTIPLICATIVE && o->schedule != MF_SCHEDULE_ADDITIVE)
     return fail(MF_ERR_INVALID_ARG, "mf_sweep: unknown schedule");
   if (o->precision != MF_PREC_FP32 && o->precision != MF_PREC_BF16 && o->precision != MF_PREC_MIXED &&
-      o->precision != MF_PREC_FP32_SIMT)
+      o->precision != MF_PREC_FP32_SIMT && o->precision != MF_PREC_F16)
     return fail(MF_ERR_INVALID_ARG, "mf_sweep: unknown precision");
   if (o->precision == MF_PREC_MIXED && !(o->eps_coarse > 0.0 && std::isfinite(o->eps_coarse)))
     return fail(MF_ERR_INVALID_ARG, "mf_sweep: MF_PREC_MIXED needs eps_coarse > 0");
@@ -429,12 +444,14 @@ mf_status sweep_impl(mf_grid* g, const mf_sdnet* net, const mf_sweep_opts* o, mf
   if (!std::isfinite(o->eps)) return fail(MF_ERR_INVALID_ARG, "mf_sweep: eps must be finite");
   if ((o->precision == MF_PREC_BF16 || o->precision == MF_PREC_MIXED) && !mf::bf16_supported(net->d))
     return fail(MF_ERR_UNSUPPORTED, "mf_sweep: BF16 path needs 1..5 hidden layers");
+  if (o->precision == MF_PREC_F16 && !mf::f16_supported(net->d))
+    return fail(MF_ERR_UNSUPPORTED, "mf_sweep: F16 path needs 1..5 hidden layers and weights within the F16 range");
   if (o->launch_mode != MF_LAUNCH_PER_COLOUR && o->launch_mode != MF_LAUNCH_SWEEP)
     return fail(MF_ERR_INVALID_ARG, "mf_sweep: launch_mode must be MF_LAUNCH_PER_COLOUR or MF_LAUNCH_SWEEP");
   const bool sweep_launch = o->launch_mode == MF_LAUNCH_SWEEP;
   if (sweep_launch && (o->schedule != MF_SCHEDULE_MULTIPLICATIVE || (o->colours != 0 && o->colours != 15) ||
                        o->precision == MF_PREC_FP32 || o->precision == MF_PREC_FP32_SIMT ||
-                       !mf::bf16_sweep_supported(net->d)))
+                       o->precision == MF_PREC_F16 || !mf::bf16_sweep_supported(net->d)))
     return fail(MF_ERR_UNSUPPORTED, "mf_sweep: MF_LAUNCH_SWEEP runs BF16 multiplicative sweeps of all colours "
                                     "with an SDNet without a boundary embedding");
   if (net->device != g->device) return fail(MF_ERR_INVALID_ARG, "mf_sweep: grid and SDNet on different devices");
@@ -457,6 +474,7 @@ mf_status sweep_impl(mf_grid* g, const mf_sdnet* net, const mf_sweep_opts* o, mf
   for (int k = 0; k < o->n_sweeps; ++k) {
     const bool check = coarse || ((k + 1) % o->check_every == 0) || (k + 1 == o->n_sweeps);
     const bool bf16 = mixed ? coarse : (o->precision == MF_PREC_BF16);
+    const bool f16 = o->precision == MF_PREC_F16;
     if (check || additive)
       MF_CUDA(cudaMemcpyAsync(g->prev, g->u, bytes, cudaMemcpyDeviceToDevice, st), "mf_sweep: snapshot");
     if (additive) {
@@ -495,6 +513,9 @@ mf_status sweep_impl(mf_grid* g, const mf_sdnet* net, const mf_sweep_opts* o, mf
       MF_CUDA(pt.mark(kPhaseGather), "mf_sweep: event");
       if (bf16)
         MF_CUDA(mf::launch_mlp_bf16(g->B, cg, net->d, g->u, additive ? 1 : 0, g->status, st), "mf_sweep: bf16 mlp");
+      else if (f16)
+        MF_CUDA(mf::launch_mlp_bf16(g->B, cg, net->d, g->u, additive ? 1 : 0, g->status, st, true),
+                "mf_sweep: f16 mlp");
       else
         MF_CUDA(mf::launch_mlp_fp32_path(g->B, cg, net->d, g->u, additive ? 1 : 0, g->status,
                                          o->precision == MF_PREC_FP32_SIMT, st),

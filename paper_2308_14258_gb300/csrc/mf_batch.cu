@@ -98,8 +98,9 @@ cudaError_t enqueue_sweep(mf_batch* b, const mf::DevNet& net, int prec, int quer
     if (g.n_c == 0) continue;
     cudaError_t e = mf::launch_gather_boundary(u, g, net, b->B, st, gather);
     if (e != cudaSuccess) return e;
-    e = prec == MF_PREC_BF16 ? mf::launch_mlp_bf16(b->B, g, net, u, 0, b->status, st)
-                             : mf::launch_mlp_fp32_path(b->B, g, net, u, 0, b->status, prec == MF_PREC_FP32_SIMT, st);
+    e = (prec == MF_PREC_BF16 || prec == MF_PREC_F16)
+            ? mf::launch_mlp_bf16(b->B, g, net, u, 0, b->status, st, prec == MF_PREC_F16)
+            : mf::launch_mlp_fp32_path(b->B, g, net, u, 0, b->status, prec == MF_PREC_FP32_SIMT, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -360,8 +361,10 @@ mf_status batch_sweep_impl(mf_batch* b, const mf_sdnet* net, const mf_sweep_opts
   if (o->n_sweeps < 0) return fail(MF_ERR_INVALID_ARG, "mf_batch_sweep: n_sweeps < 0");
   if (o->schedule != MF_SCHEDULE_MULTIPLICATIVE)
     return fail(MF_ERR_INVALID_ARG, "mf_batch_sweep: batches use the multiplicative schedule");
-  if (o->precision != MF_PREC_FP32 && o->precision != MF_PREC_BF16 && o->precision != MF_PREC_FP32_SIMT)
-    return fail(MF_ERR_INVALID_ARG, "mf_batch_sweep: precision must be MF_PREC_FP32, MF_PREC_FP32_SIMT or MF_PREC_BF16");
+  if (o->precision != MF_PREC_FP32 && o->precision != MF_PREC_BF16 && o->precision != MF_PREC_FP32_SIMT &&
+      o->precision != MF_PREC_F16)
+    return fail(MF_ERR_INVALID_ARG,
+                "mf_batch_sweep: precision must be MF_PREC_FP32, MF_PREC_FP32_SIMT, MF_PREC_BF16 or MF_PREC_F16");
   if (o->query != MF_QUERY_FULL && o->query != MF_QUERY_CENTRE)
     return fail(MF_ERR_INVALID_ARG, "mf_batch_sweep: unknown query");
   if (o->colours != 0 && o->colours != 15) return fail(MF_ERR_INVALID_ARG, "mf_batch_sweep: colours must be 0 (all)");
@@ -372,6 +375,8 @@ mf_status batch_sweep_impl(mf_batch* b, const mf_sdnet* net, const mf_sweep_opts
   if (net_device != b->device) return fail(MF_ERR_INVALID_ARG, "mf_batch_sweep: batch and SDNet on different devices");
   if (o->precision == MF_PREC_BF16 && !mf::bf16_supported(*d))
     return fail(MF_ERR_UNSUPPORTED, "mf_batch_sweep: BF16 path needs 1..5 hidden layers");
+  if (o->precision == MF_PREC_F16 && !mf::f16_supported(*d))
+    return fail(MF_ERR_UNSUPPORTED, "mf_batch_sweep: F16 path needs 1..5 hidden layers and weights in the F16 range");
   if (o->launch_mode < MF_LAUNCH_PER_COLOUR || o->launch_mode > MF_LAUNCH_AUTO)
     return fail(MF_ERR_INVALID_ARG, "mf_batch_sweep: unknown launch_mode");
   if (o->launch_mode == MF_LAUNCH_SWEEP && (o->precision != MF_PREC_BF16 || !mf::bf16_sweep_supported(*d)))

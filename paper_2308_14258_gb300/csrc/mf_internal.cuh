@@ -169,6 +169,7 @@ struct DevNet {
   const void* wimg_bf16; // [n_hidden] BF16 images in the tensor-core shared-memory layout
   size_t wimg_bytes;     // bytes of all images
   const void* wimg_f16;  // [n_hidden][hi, lo] F16 split images (width 128), or null
+  const void* wimg_f16s; // [n_hidden] F16 images (the F16 sweep's B operands), or null
   const float* h_bh;     // host copies: hidden biases [n_hidden][H]
   const float* h_wout;   // [H]
   const float* h_W2;     // [H][2]
@@ -186,10 +187,12 @@ cudaError_t launch_gather_boundary(const float* u, const ColourGeom& g, const De
 cudaError_t launch_mlp_fp32(const float* B, const ColourGeom& g, const DevNet& net,
                             float* u, int additive, cudaStream_t st);
 
-// K3: BF16 tcgen05 SDNet with TMEM accumulators, same contract as launch_mlp_fp32.
+// K3: BF16 tcgen05 SDNet with TMEM accumulators, same contract as launch_mlp_fp32;
+// f16: F16 operands and activations instead (needs the F16 weight images).
 cudaError_t launch_mlp_bf16(const float* B, const ColourGeom& g, const DevNet& net,
-                            float* u, int additive, int* dev_status, cudaStream_t st);
+                            float* u, int additive, int* dev_status, cudaStream_t st, bool f16 = false);
 bool bf16_supported(const DevNet& net);
+bool f16_supported(const DevNet& net);
 
 // K3t: the FP32 SDNet on the tensor cores, each hidden product split in three F16
 // products with FP32 accumulation (width 128, tanh); same contract as launch_mlp_fp32.

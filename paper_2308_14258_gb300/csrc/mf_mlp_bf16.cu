@@ -1,5 +1,6 @@
-// K3: BF16 SDNet over one colour on the 5th-generation tensor cores, fused with the
-// scatter into the grid.
+// K3: BF16 (or F16) SDNet over one colour on the 5th-generation tensor cores, fused with
+// the scatter into the grid. The two 16-bit types differ only in the operand type of the
+// MMAs, the weight images and the activation's packed form (template DT).
 //
 // Work: rows r = (subdomain s, interior point p) of the colour, in tiles of 128 rows
 // (the M of one tcgen05.mma). Per row, the input-split first layer (Eq. 8) is
@@ -59,22 +60,36 @@ struct Bf16Params {
   unsigned int* sync;    // barrier counter, zero at launch
 };
 
-// Activation of two FP32 pre-activations, packed as BF16x2. tanh: the hardware tanh on
-// the BF16 pair. GELU: its tanh form 0.5 x (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3)))
-// (Hendrycks and Gimpel) with the FP32 hardware tanh, so that 1 + tanh keeps its
-// accuracy for negative x; both forms cost one tanh per element on the MUFU unit.
-template <int ACT>
-__device__ __forceinline__ uint32_t act_bf16x2(float a0, float a1) {
+// Activation of two FP32 pre-activations, packed as a 16-bit pair of the kernel's operand
+// type DT (kDtBf16 or kDtF16). tanh: the hardware tanh on the packed pair. GELU: its tanh
+// form 0.5 x (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3))) (Hendrycks and Gimpel) with the
+// FP32 hardware tanh, so that 1 + tanh keeps its accuracy for negative x; both forms cost
+// one tanh per element on the MUFU unit.
+constexpr int kDtBf16 = 0, kDtF16 = 1;
+template <int ACT, int DT>
+__device__ __forceinline__ uint32_t act16x2(float a0, float a1) {
   if constexpr (ACT == kActTanh) {
-    return tanh_bf16x2(pack_bf16x2(a0, a1));
+    if constexpr (DT == kDtF16) return tanh_f16x2(pack_f16x2(a0, a1));
+    else return tanh_bf16x2(pack_bf16x2(a0, a1));
   } else {
     constexpr float k0 = 0.7978845608028654f;  // sqrt(2 / pi)
     constexpr float k1 = k0 * 0.044715f;
     const float t0 = tanh_approx(a0 * fmaf(k1 * a0, a0, k0));
     const float t1 = tanh_approx(a1 * fmaf(k1 * a1, a1, k0));
     const float h0 = 0.5f * a0, h1 = 0.5f * a1;
-    return pack_bf16x2(fmaf(h0, t0, h0), fmaf(h1, t1, h1));
+    if constexpr (DT == kDtF16) return pack_f16x2(fmaf(h0, t0, h0), fmaf(h1, t1, h1));
+    else return pack_bf16x2(fmaf(h0, t0, h0), fmaf(h1, t1, h1));
   }
+}
+template <int DT>
+__device__ __forceinline__ float lo16(uint32_t v) {
+  if constexpr (DT == kDtF16) return f16_lo(v);
+  else return bf16_lo(v);
+}
+template <int DT>
+__device__ __forceinline__ float hi16(uint32_t v) {
+  if constexpr (DT == kDtF16) return f16_hi(v);
+  else return bf16_hi(v);
 }
 
 // ---------------------------------------------------------------- kernel
@@ -146,7 +161,7 @@ __device__ __forceinline__ bool hot_wait_warp(uint32_t bar, uint32_t parity, vol
   else return wait_warp(bar, parity, abort_flag, status);
 }
 
-template <int H, int NH, int ACT>
+template <int H, int NH, int ACT, int DT>
 __device__ __forceinline__ bool mma_issuer(const Bf16Params& P, int n_tiles, int s, uint32_t tmem, uint32_t sA,
                                            uint32_t sW, uint32_t bar_act0, uint32_t bar_act1, uint32_t bar_acc,
                                            volatile int* abort_flag, uint32_t& ph0, uint32_t& ph1) {
@@ -174,8 +189,9 @@ __device__ __forceinline__ bool mma_issuer(const Bf16Params& P, int n_tiles, int
           const int ks = h * C::kKStepsHalf + kk;
           const uint64_t ad = desc_add(a0, kstep_off(kTileRows, ks));
           const uint64_t bd = desc_add(w0, (uint32_t)(m - 1) * H * H * 2 + kstep_off(H, ks));
-          if (ks == 0) mma_ss<0>(acc, ad, bd, C::kIdesc);
-          else mma_ss<1>(acc, ad, bd, C::kIdesc);
+          constexpr uint32_t kId = DT == kDtF16 ? idesc_f16(kTileRows, H) : C::kIdesc;
+          if (ks == 0) mma_ss<0>(acc, ad, bd, kId);
+          else mma_ss<1>(acc, ad, bd, kId);
         }
       }
       if (!ok) break;
@@ -187,7 +203,7 @@ __device__ __forceinline__ bool mma_issuer(const Bf16Params& P, int n_tiles, int
 
 // Epilogue of one warp: slot s, row quadrant q (TMEM lanes / tile rows 32q..32q+31),
 // member JJ of the column pair (in K half h it owns columns h*H/2 + JJ*H/4 .. + H/4 - 1).
-template <int H, int NH, int JJ, int ACT, bool kMulti>
+template <int H, int NH, int JJ, int ACT, bool kMulti, int DT>
 __device__ __forceinline__ bool epilogue(const Bf16Params& P, const ColourGeom& geo, int n_rows, int n_tiles, int s,
                                          int q, int lane, uint32_t tmem, uint32_t sA, uint32_t bar_act0,
                                          uint32_t bar_act1, uint32_t bar_acc, uint32_t tok_wait, uint32_t tok_give,
@@ -270,7 +286,7 @@ __device__ __forceinline__ bool epilogue(const Bf16Params& P, const ColourGeom& 
             const int col = c0 + 2 * i;
             const float a0 = fmaf(P.w2[col][1], y, fmaf(P.w2[col][0], x, bb[i].x));
             const float a1 = fmaf(P.w2[col + 1][1], y, fmaf(P.w2[col + 1][0], x, bb[i].y));
-            pk[i] = act_bf16x2<ACT>(a0, a1);
+            pk[i] = act16x2<ACT, DT>(a0, a1);
           }
           put(c0, pk);
           signal(h == 0 ? bar_act0 : bar_act1);
@@ -302,7 +318,7 @@ __device__ __forceinline__ bool epilogue(const Bf16Params& P, const ColourGeom& 
           if (h == 1 && i == CW / 4) give_turn();
           const float a0 = __uint_as_float(v[2 * i]) + P.bias[m - 1][c0 + 2 * i];
           const float a1 = __uint_as_float(v[2 * i + 1]) + P.bias[m - 1][c0 + 2 * i + 1];
-          pk[i] = act_bf16x2<ACT>(a0, a1);
+          pk[i] = act16x2<ACT, DT>(a0, a1);
         }
         if (h == 1) tc_fence_before();
         if (m < NH) {
@@ -311,8 +327,8 @@ __device__ __forceinline__ bool epilogue(const Bf16Params& P, const ColourGeom& 
         } else {
 #pragma unroll
           for (int i = 0; i < CW / 2; ++i) {
-            uacc = fmaf(bf16_lo(pk[i]), P.wout[c0 + 2 * i], uacc);
-            uacc = fmaf(bf16_hi(pk[i]), P.wout[c0 + 2 * i + 1], uacc);
+            uacc = fmaf(lo16<DT>(pk[i]), P.wout[c0 + 2 * i], uacc);
+            uacc = fmaf(hi16<DT>(pk[i]), P.wout[c0 + 2 * i + 1], uacc);
           }
         }
       }
@@ -434,7 +450,7 @@ __device__ __forceinline__ void gather_pass(const Bf16Params& P, const ColourGeo
   }
 }
 
-template <int H, int NH, int ACT, bool kMulti>
+template <int H, int NH, int ACT, bool kMulti, int DT>
 __global__ void __launch_bounds__(kThreadsBf16, 1) mlp_bf16_kernel(const __grid_constant__ Bf16Params P) {
   using C = Bf16Cfg<H, NH>;
   extern __shared__ uint8_t smem_raw[];
@@ -487,10 +503,10 @@ __global__ void __launch_bounds__(kThreadsBf16, 1) mlp_bf16_kernel(const __grid_
         if constexpr (kMulti) {
           bool ok = true;
           for (int c = 0; ok && c < P.n_col; ++c)
-            ok = mma_issuer<H, NH, ACT>(P, P.n_tiles_c[c], s, tmem, sA, sW, bar(1 + 2 * s), bar(2 + 2 * s),
+            ok = mma_issuer<H, NH, ACT, DT>(P, P.n_tiles_c[c], s, tmem, sA, sW, bar(1 + 2 * s), bar(2 + 2 * s),
                                         bar(5 + s), abort_flag, ph0, ph1);
         } else {
-          mma_issuer<H, NH, ACT>(P, P.n_tiles, s, tmem, sA, sW, bar(1 + 2 * s), bar(2 + 2 * s), bar(5 + s),
+          mma_issuer<H, NH, ACT, DT>(P, P.n_tiles, s, tmem, sA, sW, bar(1 + 2 * s), bar(2 + 2 * s), bar(5 + s),
                                  abort_flag, ph0, ph1);
         }
       }
@@ -504,11 +520,11 @@ __global__ void __launch_bounds__(kThreadsBf16, 1) mlp_bf16_kernel(const __grid_
     uint32_t acc_ph = 0u, tok_ph = 0u;
     auto run = [&](const ColourGeom& geo, int n_rows, int n_tiles) {
       if (jj == 0)
-        epilogue<H, NH, 0, ACT, kMulti>(P, geo, n_rows, n_tiles, s, q, lane, tmem, sA, bar(1 + 2 * s), bar(2 + 2 * s),
+        epilogue<H, NH, 0, ACT, kMulti, DT>(P, geo, n_rows, n_tiles, s, q, lane, tmem, sA, bar(1 + 2 * s), bar(2 + 2 * s),
                                         bar(5 + s), bar(9 + s), bar(10 - s), half_sum, pair_ok, abort_flag, acc_ph,
                                         tok_ph);
       else
-        epilogue<H, NH, 1, ACT, kMulti>(P, geo, n_rows, n_tiles, s, q, lane, tmem, sA, bar(1 + 2 * s), bar(2 + 2 * s),
+        epilogue<H, NH, 1, ACT, kMulti, DT>(P, geo, n_rows, n_tiles, s, q, lane, tmem, sA, bar(1 + 2 * s), bar(2 + 2 * s),
                                         bar(5 + s), bar(9 + s), bar(10 - s), half_sum, pair_ok, abort_flag, acc_ph,
                                         tok_ph);
     };
@@ -559,7 +575,7 @@ __global__ void __launch_bounds__(kThreadsBf16, 1) mlp_bf16_kernel(const __grid_
   }
 }
 
-template <int H, int NH, int ACT, bool kMulti>
+template <int H, int NH, int ACT, bool kMulti, int DT>
 cudaError_t launch_t(const Bf16Params& p, cudaStream_t st) {
   using C = Bf16Cfg<H, NH>;
   // per device: the dynamic shared memory to request and the grid cap (resident CTAs)
@@ -567,13 +583,13 @@ cudaError_t launch_t(const Bf16Params& p, cudaStream_t st) {
   int grid_cap = 0;
   size_t smem_bytes = 0;
   cudaError_t e0 = per_device(pd, [](int dev, int* cap, size_t* smem) {
-    cudaError_t e = cudaFuncSetAttribute(mlp_bf16_kernel<H, NH, ACT, kMulti>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(mlp_bf16_kernel<H, NH, ACT, kMulti, DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)C::kSmem);
     if (e != cudaSuccess) return e;
     int sms = 0, per_sm = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_bf16_kernel<H, NH, ACT, kMulti>, kThreadsBf16, C::kSmem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_bf16_kernel<H, NH, ACT, kMulti, DT>, kThreadsBf16, C::kSmem);
     if (e != cudaSuccess) return e;
     // every resident CTA must be able to hold its tensor memory at once (512 columns):
     // if shared memory alone would admit more CTAs per SM, request more of it
@@ -583,9 +599,9 @@ cudaError_t launch_t(const Bf16Params& p, cudaStream_t st) {
       int smem_sm = 0;
       cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
       *smem = (size_t)smem_sm / (size_t)(tmem_cap + 1) + 1024;
-      e = cudaFuncSetAttribute(mlp_bf16_kernel<H, NH, ACT, kMulti>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
+      e = cudaFuncSetAttribute(mlp_bf16_kernel<H, NH, ACT, kMulti, DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
       if (e != cudaSuccess) return e;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_bf16_kernel<H, NH, ACT, kMulti>, kThreadsBf16, *smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_bf16_kernel<H, NH, ACT, kMulti, DT>, kThreadsBf16, *smem);
       if (e != cudaSuccess) return e;
     }
     if (per_sm > tmem_cap || per_sm < 1) return cudaErrorInvalidConfiguration;
@@ -604,34 +620,34 @@ cudaError_t launch_t(const Bf16Params& p, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(p.sync, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
     void* args[] = {const_cast<Bf16Params*>(&p)};
-    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&mlp_bf16_kernel<H, NH, ACT, true>),
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&mlp_bf16_kernel<H, NH, ACT, true, DT>),
                                        dim3(grid), dim3(kThreadsBf16), args, smem_bytes, st);
   } else {
     int grid = (p.n_tiles + kSlots - 1) / kSlots;
     if (grid > grid_cap) grid = grid_cap;
     if (grid < 1) return cudaSuccess;
-    mlp_bf16_kernel<H, NH, ACT, false><<<grid, kThreadsBf16, smem_bytes, st>>>(p);
+    mlp_bf16_kernel<H, NH, ACT, false, DT><<<grid, kThreadsBf16, smem_bytes, st>>>(p);
     return cudaGetLastError();
   }
 }
 
-template <int ACT, bool kMulti>
+template <int ACT, bool kMulti, int DT>
 cudaError_t dispatch(const DevNet& net, const Bf16Params& p, cudaStream_t st) {
   if (net.width == 128) {
     switch (net.n_hidden) {
-      case 1: return launch_t<128, 1, ACT, kMulti>(p, st);
-      case 2: return launch_t<128, 2, ACT, kMulti>(p, st);
-      case 3: return launch_t<128, 3, ACT, kMulti>(p, st);
-      case 4: return launch_t<128, 4, ACT, kMulti>(p, st);
-      default: return launch_t<128, 5, ACT, kMulti>(p, st);
+      case 1: return launch_t<128, 1, ACT, kMulti, DT>(p, st);
+      case 2: return launch_t<128, 2, ACT, kMulti, DT>(p, st);
+      case 3: return launch_t<128, 3, ACT, kMulti, DT>(p, st);
+      case 4: return launch_t<128, 4, ACT, kMulti, DT>(p, st);
+      default: return launch_t<128, 5, ACT, kMulti, DT>(p, st);
     }
   }
   switch (net.n_hidden) {
-    case 1: return launch_t<64, 1, ACT, kMulti>(p, st);
-    case 2: return launch_t<64, 2, ACT, kMulti>(p, st);
-    case 3: return launch_t<64, 3, ACT, kMulti>(p, st);
-    case 4: return launch_t<64, 4, ACT, kMulti>(p, st);
-    default: return launch_t<64, 5, ACT, kMulti>(p, st);
+    case 1: return launch_t<64, 1, ACT, kMulti, DT>(p, st);
+    case 2: return launch_t<64, 2, ACT, kMulti, DT>(p, st);
+    case 3: return launch_t<64, 3, ACT, kMulti, DT>(p, st);
+    case 4: return launch_t<64, 4, ACT, kMulti, DT>(p, st);
+    default: return launch_t<64, 5, ACT, kMulti, DT>(p, st);
   }
 }
 
@@ -653,10 +669,12 @@ bool bf16_supported(const DevNet& net) {
   return (net.width == 64 || net.width == 128) && net.n_hidden >= 1 && net.n_hidden <= kMaxHidden;
 }
 
+bool f16_supported(const DevNet& net) { return bf16_supported(net) && net.wimg_f16s != nullptr; }
+
 cudaError_t launch_mlp_bf16(const float* B, const ColourGeom& g, const DevNet& net, float* u, int additive,
-                            int* dev_status, cudaStream_t st) {
+                            int* dev_status, cudaStream_t st, bool f16) {
   if (g.n_c <= 0) return cudaSuccess;
-  if (!bf16_supported(net)) return cudaErrorNotSupported;
+  if (!bf16_supported(net) || (f16 && !f16_supported(net))) return cudaErrorNotSupported;
   Bf16Params p{};
   p.B = B;
   p.u = u;
@@ -666,8 +684,13 @@ cudaError_t launch_mlp_bf16(const float* B, const ColourGeom& g, const DevNet& n
   p.n_tiles = (p.n_rows + kTileRows - 1) / kTileRows;
   p.additive = additive;
   fill_net(net, p);
-  if (net.act == kActGelu) return dispatch<kActGelu, false>(net, p, st);
-  return dispatch<kActTanh, false>(net, p, st);
+  if (f16) {
+    p.wimg = static_cast<const uint8_t*>(net.wimg_f16s);
+    if (net.act == kActGelu) return dispatch<kActGelu, false, kDtF16>(net, p, st);
+    return dispatch<kActTanh, false, kDtF16>(net, p, st);
+  }
+  if (net.act == kActGelu) return dispatch<kActGelu, false, kDtBf16>(net, p, st);
+  return dispatch<kActTanh, false, kDtBf16>(net, p, st);
 }
 
 bool bf16_sweep_supported(const DevNet& net) { return bf16_supported(net) && net.embed_c == 0; }
@@ -691,8 +714,8 @@ cudaError_t launch_mlp_bf16_sweep(const ColourGeom* gc, int n_col, const DevNet&
   p.b0 = net.b0;
   p.sync = sync;
   fill_net(net, p);
-  if (net.act == kActGelu) return dispatch<kActGelu, true>(net, p, st);
-  return dispatch<kActTanh, true>(net, p, st);
+  if (net.act == kActGelu) return dispatch<kActGelu, true, kDtBf16>(net, p, st);
+  return dispatch<kActTanh, true, kDtBf16>(net, p, st);
 }
 
 }  // namespace mf

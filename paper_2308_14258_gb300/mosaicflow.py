@@ -24,7 +24,7 @@ MF_ERR_DIVERGED = -4
 MF_ERR_TIMEOUT = -5
 MF_ERR_UNSUPPORTED = -6
 
-PREC = {"fp32": 0, "bf16": 1, "mixed": 2, "fp32_simt": 3}
+PREC = {"fp32": 0, "bf16": 1, "mixed": 2, "fp32_simt": 3, "f16": 4}
 SCHEDULE = {"M": 0, "multiplicative": 0, "A": 1, "additive": 1}
 QUERY = {"full": 0, "centre": 1, "center": 1}
 OPTIMIZER = {"sgd": 0, "lamb": 1}

@@ -74,3 +74,17 @@ def test_mid_mixed_refinement_reaches_oracle_fixed_point(m, mid_oracle, eps_coar
     g2 = m.Grid(p.lx, p.ly, p.bc)
     g2.sweep(net, 40, "M", "bf16")
     assert rel(g2.download(), ref) <= 3e-2
+
+
+def test_mid_f16_alone_reaches_oracle_fixed_point(m, mid_oracle):
+    """F16 sweeps alone (MF_PREC_F16, no FP32 refinement) to their own fixed point: the
+    field within 1e-3 of the FP64 oracle's converged field. F16 rounds activations and
+    weights to 11 significant bits against BF16's 8, the error floor of BF16 sweeps
+    alone being above 1e-3 on the benchmark grid."""
+    p, weights, ref, _ = mid_oracle
+    net = m.SDNet(weights, 128, 6)
+    g = m.Grid(p.lx, p.ly, p.bc)
+    out = g.sweep(net, 40, "M", "f16", eps=0.0)
+    assert out.sweeps_done == 40
+    err = rel(g.download(), ref)
+    assert err <= 1e-3, err
