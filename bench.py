@@ -312,7 +312,8 @@ def measure_converged(m, I, torch, np, net, p, weights, stream, rank, with_oracl
     * mixed: MF_PREC_MIXED, BF16 sweeps until delta < 1e-2 or until a BF16 sweep stops
       reducing delta (its rounding floor, about 1.2e-2 on this grid), then FP32 sweeps
       until delta < 1e-5;
-    * bf16: BF16 sweeps alone (40, well past their plateau).
+    * bf16: BF16 sweeps alone (40, well past their plateau);
+    * f16: F16 sweeps alone (MF_PREC_F16, 40), the other 16-bit type on the same kernel.
     The stop value 1e-5 lies above the FP32 rounding floor of delta on this grid
     (about 1.5e-6). Each field is compared with the FP32 fixed point (FP32 sweeps to
     250, where delta sits at its floor), as max |u - u_ref| / max |u_ref|.
@@ -329,7 +330,8 @@ def measure_converged(m, I, torch, np, net, p, weights, stream, rank, with_oracl
     del g
     scale = float(np.abs(ref).max())
     res["reference"] = {"what": "FP32 sweeps to 250 from the zero interior", "delta": o.delta}
-    runs = (("fp32", "fp32", 400, 1e-5, 0.0), ("mixed", "mixed", 400, 1e-5, 1e-2), ("bf16", "bf16", 40, 0.0, 0.0))
+    runs = (("fp32", "fp32", 400, 1e-5, 0.0), ("mixed", "mixed", 400, 1e-5, 1e-2), ("bf16", "bf16", 40, 0.0, 0.0),
+            ("f16", "f16", 40, 0.0, 0.0))
     for name, prec, n, eps, eps_c in runs:
         g = m.Grid(p.lx, p.ly, p.bc)
         torch.cuda.synchronize()
@@ -340,8 +342,9 @@ def measure_converged(m, I, torch, np, net, p, weights, stream, rank, with_oracl
         e1.record(stream)
         e1.synchronize()
         fields[name] = g.download(stream=stream).astype(np.float64)
-        res[name] = {"sweeps": o.sweeps_done, "sweeps_bf16": o.sweeps_bf16,
-                     "sweeps_fp32": o.sweeps_done - o.sweeps_bf16, "delta": o.delta,
+        n16 = o.sweeps_done if prec == "f16" else 0
+        res[name] = {"sweeps": o.sweeps_done, "sweeps_bf16": o.sweeps_bf16, "sweeps_f16": n16,
+                     "sweeps_fp32": o.sweeps_done - o.sweeps_bf16 - n16, "delta": o.delta,
                      "ms": e0.elapsed_time(e1),
                      "max_rel_err_vs_fp32_fixed_point": float(np.abs(fields[name] - ref).max() / scale)}
         del g
@@ -358,7 +361,7 @@ def measure_converged(m, I, torch, np, net, p, weights, stream, rank, with_oracl
         e1.record(stream)
         e1.synchronize()
         return e0.elapsed_time(e1) / 4
-    t32, t16 = sweep_ms("fp32"), sweep_ms("bf16")
+    t32, t16, th = sweep_ms("fp32"), sweep_ms("bf16"), sweep_ms("f16")
     cur = torch.empty_like(ref_t)
 
     def err_now(g):
@@ -367,7 +370,7 @@ def measure_converged(m, I, torch, np, net, p, weights, stream, rank, with_oracl
             e = float((cur - ref_t).abs().max()) / scale
         return e
 
-    to = {"target": 1e-3, "ms_per_sweep": {"fp32": t32, "bf16": t16}}
+    to = {"target": 1e-3, "ms_per_sweep": {"fp32": t32, "bf16": t16, "f16": th}}
     g = m.Grid(p.lx, p.ly, p.bc)
     n32 = None
     for k in range(1, 201):
@@ -396,6 +399,17 @@ def measure_converged(m, I, torch, np, net, p, weights, stream, rank, with_oracl
                    "ms": nb * t16 + nf * t32}
     if to["fp32"]["ms"] and to["mixed"]["ms"]:
         to["speedup_mixed_over_fp32"] = to["fp32"]["ms"] / to["mixed"]["ms"]
+    # F16 sweeps alone
+    g = m.Grid(p.lx, p.ly, p.bc)
+    nh = None
+    for k in range(1, 61):
+        g.sweep(net, 1, "M", "f16", stream=stream)
+        if err_now(g) <= 1e-3:
+            nh = k
+            break
+    to["f16"] = {"sweeps": nh, "ms": nh * th if nh else None}
+    if to["fp32"]["ms"] and to["f16"]["ms"]:
+        to["speedup_f16_over_fp32"] = to["fp32"]["ms"] / to["f16"]["ms"]
     del g
     res["to_1e-3"] = to
     res["workload"] = "large_L64 grid from the zero interior, SDNet 6x128 (seed 2), multiplicative schedule"
@@ -593,6 +607,7 @@ def main():
     for _ in range(args.warmup):
         grid.sweep(net, 1, "M", "bf16", stream=stream)
     grid.sweep(net, 1, "M", "fp32", stream=stream)
+    grid.sweep(net, 1, "M", "f16", stream=stream)
     sampler = ClockSampler(local)
     torch.cuda.synchronize()
     barrier(world)
@@ -611,6 +626,10 @@ def main():
     fp32_value = evals_per_sweep * k32 / (sum(ms32) / 1e3) if k32 > 0 else None
     ks = 2 if args.fp32_steps < 0 else min(2, args.fp32_steps)
     ms32s, _, _, _ = timed_steps("fp32_simt", ks)
+    # the F16 path (the same kernel with the other 16-bit operand type)
+    kh = max(3, args.steps // 4)
+    msh, mlph, mlph_launch, _ = timed_steps("f16", kh)
+    f16_value = evals_per_sweep * kh / (sum(msh) / 1e3)
     fp32_simt_value = evals_per_sweep * ks / (sum(ms32s) / 1e3) if ks > 0 else None
 
     # centre-line (interface-only) sweeps of the same grid: Algorithm 2's per-iteration work
@@ -767,6 +786,8 @@ def main():
                  "speedup_bf16_over_fp32": value / world / fp32_value if fp32_value else None},
         "fp32_simt": {"value": fp32_simt_value, "unit": UNIT, "ms_per_step": sum(ms32s) / ks if ks else None,
                       "kernel": "mlp_fp32_kernel: FFMA and tanhf on the CUDA cores"},
+        "f16": {"value": f16_value, "unit": UNIT, "ms_per_step": sum(msh) / kh, "per_launch_ms": mlph / max(1, mlph_launch),
+                "kernel": "mlp_bf16_kernel with F16 operands (MF_PREC_F16): same MMAs, 11-bit significands"},
         "err_vs_oracle_bf16_sweep": err,
         "convergence_norms": norms,
         "centre_lines": {"sweeps_per_s": 1e3 * k_c / sum(cl_ms), "ms_per_sweep": sum(cl_ms) / k_c,
