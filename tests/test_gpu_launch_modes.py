@@ -127,7 +127,7 @@ def test_launch_mode_validation(m):
     bc = I.bc_values(2, 2, I.mode_field(I.mode_coeffs(67), 2, 2))
     g = m.Grid(2, 2, bc)
     for mode, prec, code in (("sweep", "fp32", m.MF_ERR_UNSUPPORTED), ("graph", "bf16", m.MF_ERR_INVALID_ARG),
-                             ("auto", "bf16", m.MF_ERR_INVALID_ARG)):
+                             ("auto", "bf16", m.MF_ERR_INVALID_ARG), ("sweep", "f16", m.MF_ERR_UNSUPPORTED)):
         with pytest.raises(m.MFError) as e:
             g.sweep(net, 1, "M", prec, launch_mode=mode)
         assert e.value.status == code
