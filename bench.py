@@ -42,14 +42,14 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # DRAM traffic of one SDNet (tensor-core) launch from an ncu capture, valid only while
 # the kernel source is unchanged (keyed by the source hash).
 NCU_TRAFFIC = {
-    # ncu --set full, colour 0 of the L = 64 grid: dram__bytes_read 2.636 MB + write 0.312 MB
-    "49df8b9f8596f8af": 2948096,
+    # ncu --set full, colour 2 of the L = 64 grid: dram__bytes_read 2.640 MB + write 0.316 MB
+    "81be73928d336f0a": 2955776,
 }
 # The unit that bounds the same kernel, from the same capture: the MUFU pipe (tanh),
 # sm__pipe_xu_cycles_active of elapsed; the tanh floor is 98,304 tanh per 128-row tile
 # at 16 per clock per SM.
 NCU_MUFU_BUSY = {
-    "49df8b9f8596f8af": 0.7275,
+    "81be73928d336f0a": 0.6912,
 }
 
 
