@@ -132,7 +132,7 @@ typedef struct {
 /* Message describing the calling thread's most recent failed call ("" if none). */
 const char* mf_last_error(void);
 
-/* Library version as major*10000 + minor*100 + patch. */
+/* Library version as major*10000 + minor*100 + patch (0.3.0: MF_PREC_F16). */
 int mf_version(void);
 
 /* mf_ctx_create -- the execution context of the Laplace problems of Section 2.1 (Eq. 2)

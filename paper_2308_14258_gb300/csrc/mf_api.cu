@@ -155,7 +155,7 @@ extern "C" {
 
 const char* mf_last_error(void) { return g_err.c_str(); }
 
-int mf_version(void) { return 200; }
+int mf_version(void) { return 300; }
 
 mf_status mf_ctx_create(int device, mf_ctx** out) {
   if (!out) return fail(MF_ERR_INVALID_ARG, "mf_ctx_create: null argument");

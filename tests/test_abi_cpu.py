@@ -36,7 +36,7 @@ def test_exports_every_declared_symbol(m):
     assert sorted(m.EXPORTS) == decl
     for name in decl:
         assert getattr(lib, name) is not None
-    assert lib.mf_version() == 200
+    assert lib.mf_version() == 300
 
 
 @needs_nvcc
