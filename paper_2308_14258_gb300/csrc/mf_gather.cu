@@ -24,7 +24,7 @@ template <int H, int kSubPerBlock>
 __global__ void __launch_bounds__(kGatherThreads)
 gather_boundary_kernel(const float* __restrict__ u, ColourGeom g, const float* __restrict__ W1t,
                        const float* __restrict__ b0, float* __restrict__ B) {
-  __shared__ float gs[kSubPerBlock][kNbdry];
+  __shared__ __align__(16) float gs[kSubPerBlock][kNbdry];
   extern __shared__ float4 w1s4[];  // [128][H / 4]
   const float* w1s = reinterpret_cast<const float*>(w1s4);
   const int s0 = blockIdx.x * kSubPerBlock;
@@ -61,13 +61,22 @@ gather_boundary_kernel(const float* __restrict__ u, ColourGeom g, const float* _
   float acc[kPer];
 #pragma unroll
   for (int i = 0; i < kPer; ++i) acc[i] = 0.f;
-#pragma unroll 4
-  for (int k = 0; k < kNbdry; ++k) {
-    const float w = w1s[k * H + j];
+  // four boundary values of a subdomain per shared-memory read (the sum still runs over k
+  // in order)
+#pragma unroll 2
+  for (int k = 0; k < kNbdry; k += 4) {
+    const float w0 = w1s[k * H + j], w1 = w1s[(k + 1) * H + j];
+    const float w2 = w1s[(k + 2) * H + j], w3 = w1s[(k + 3) * H + j];
 #pragma unroll
     for (int i = 0; i < kPer; ++i) {
       const int sl = grp + i * kGroups;
-      if (sl < kSubPerBlock) acc[i] = fmaf(w, gs[sl][k], acc[i]);
+      if (sl < kSubPerBlock) {
+        const float4 g4 = *reinterpret_cast<const float4*>(&gs[sl][k]);
+        acc[i] = fmaf(w0, g4.x, acc[i]);
+        acc[i] = fmaf(w1, g4.y, acc[i]);
+        acc[i] = fmaf(w2, g4.z, acc[i]);
+        acc[i] = fmaf(w3, g4.w, acc[i]);
+      }
     }
   }
   const float bj = __ldg(b0 + j);
