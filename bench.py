@@ -497,13 +497,22 @@ def measure_train(args, m, I, torch, np, stream, rank):
     peaks, psrc = load_peaks()
     tpeak = peaks.get("bf16_tflops")
     traffic = train_tile_traffic(F, Nc, Nb, NH)
-    train["roofline"] = {"bound": "tensor", "achieved": train["gemm_tflops_achieved"], "peak": tpeak,
-                         "unit": "TFLOP/s", "frac": train["gemm_tflops_achieved"] / tpeak,
-                         "peak_source": f"{psrc} bf16_tflops (burst: the timed region is {1e3 * t:.0f} ms)",
-                         "note": "whole step: layer-GEMM flops / step time; the fused layer kernels stream "
-                                 "BF16 activation and gradient tiles through HBM",
+    hpeak = peaks.get("hbm_gbs")
+    achieved_gbs = traffic / (t / kt) / 1e9
+    # the fused engine moves 19 passes of its 1.1 GB tile buffer per step (activation and
+    # gradient tiles between layers): the step is bound by HBM, the layer GEMMs keep the
+    # tensor pipe a quarter busy
+    train["roofline"] = {"bound": "hbm", "achieved": achieved_gbs, "peak": hpeak, "unit": "GB/s",
+                         "frac": achieved_gbs / hpeak, "traffic": None,
+                         "peak_source": f"{psrc} hbm_gbs",
+                         "note": "whole step: algorithmic tile bytes (tile_bytes_per_step) / step time; ncu DRAM "
+                                 "counters on a 256-function batch show each layer kernel moving its algorithmic "
+                                 "bytes (profiles/train_bf16_F256_ncu_mem.md)",
                          "tile_bytes_per_step": traffic,
-                         "hbm_frac_of_step": traffic / (t / kt) / (peaks.get("hbm_gbs") * 1e9)}
+                         "tensor": {"achieved": train["gemm_tflops_achieved"], "peak": tpeak, "unit": "TFLOP/s",
+                                    "frac": train["gemm_tflops_achieved"] / tpeak,
+                                    "peak_source": f"{psrc} bf16_tflops (burst: the timed region is "
+                                                   f"{1e3 * t:.0f} ms)"}}
     del tr
     torch.cuda.empty_cache()
     # FP32 mode on the same batch (the GEMM engine's FP32 layer GEMMs), fewer steps
