@@ -298,8 +298,8 @@ mf_status mf_batch_residual(const mf_batch* batch, int problem, double* max_abs,
  * Memory: nothing is allocated. All scratch lives in one fixed array of about 4.7 MB
  * that every GPU using this library holds until the process exits; grids are limited
  * to 1 <= lx, ly <= 32 (larger sizes return MF_ERR_INVALID_ARG). The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress); make that first
- * call before any stream capture. All calls share the one array, so calls whose work
+ * device looks up that array's device address (cudaGetSymbolAddress) and keeps it for
+ * later calls. All calls share the one array, so calls whose work
  * overlaps on the GPU (other streams, other host threads) race and must not be issued.
  * Errors: as mf_sweep. */
 mf_status mf_sweep_noalloc(float* u, int lx, int ly, const mf_sdnet* net, int precision, int n_sweeps,
