@@ -59,7 +59,7 @@ def test_batch_sweep_equals_each_problem(m, prec, query):
     assert abs(out.delta - np.sqrt(num / den)) <= 1e-5 * np.sqrt(num / den)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "f16"])
 def test_graph_replay_matches_plain_sweeps(m, prec):
     w = I.xavier_sdnet(I.SDNetShape(64, 4), 32, bias_scale=0.1)
     net = m.SDNet(w, 64, 4)

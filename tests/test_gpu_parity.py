@@ -242,7 +242,7 @@ def test_mixed_precision_refinement_reaches_converged_field(m):
     assert rel_err(g2.download(), ref) <= 3e-2
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "f16"])
 def test_centre_line_sweeps_and_assembly(m, prec):
     """Interface-only sweeps (61 centre-cross points per subdomain, Algorithm 2's
     iterations) then the averaged full assembly, against the oracle; points off the
@@ -293,7 +293,7 @@ def _coordinate_only_weights(width, depth, ax, by, c):
     return w
 
 
-@pytest.mark.parametrize("prec,tol", [("fp32", 1e-6), ("bf16", 1e-2)])
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-6), ("bf16", 1e-2), ("f16", 5e-3)])
 @pytest.mark.parametrize("width", [64, 128])
 def test_coordinate_only_sdnet_sweep_closed_form(m, prec, tol, width):
     """Independent of the oracle: after one multiplicative sweep with a network that
