@@ -91,18 +91,22 @@ __device__ __forceinline__ float rcp_fast(float x) {
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
-// tanh from e = 2^(-2 |z| / ln 2) = exp(-2 |z|) in (0, 1]: no overflow for any z.
-// (Measured: the hardware reciprocal beats two Newton steps on the FMA pipe here.)
+// tanh(z) = 1 - 2 / (1 + e), e = 2^(2 z / ln 2) = exp(2 z): e overflows to +inf for large
+// z (then 1 - 2 / inf = 1) and flushes to 0 for very negative z (then -1); about 1e-7
+// absolute error, from the rounding of 1 - 2 r. (Measured: the hardware reciprocal beats
+// two Newton steps on the FMA pipe here.)
+constexpr float kTwoLog2e = 2.8853900817779268f;  // 2 / ln 2
 __device__ __forceinline__ float tanh_acc(float z) {
-  const float e = ex2_fast(-2.8853900817779268f * fabsf(z));
-  return copysignf((1.0f - e) * rcp_fast(1.0f + e), z);
+  const float e = ex2_fast(kTwoLog2e * z);
+  return fmaf(-2.0f, rcp_fast(1.0f + e), 1.0f);
 }
 // (hi, lo) F16 pairs of two FP32 values: hi = f16(a), lo = f16(a - hi), packed with the
 // first value in the low half
 __device__ __forceinline__ void split2(float a0, float a1, uint32_t& hi, uint32_t& lo) {
   const __half2 h = __floats2half2_rn(a0, a1);
-  const float2 back = __half22float2(h);
-  const __half2 l = __floats2half2_rn(a0 - back.x, a1 - back.y);
+  // a - f32(hi) for both values in one packed FMA (exact: the difference is representable)
+  const float2 r = __ffma2_rn(__half22float2(h), make_float2(-1.0f, -1.0f), make_float2(a0, a1));
+  const __half2 l = __floats2half2_rn(r.x, r.y);
   hi = *reinterpret_cast<const uint32_t*>(&h);
   lo = *reinterpret_cast<const uint32_t*>(&l);
 }
@@ -362,19 +366,28 @@ __global__ void __launch_bounds__(kThreadsT, 1) mlp_f32tc_kernel(const __grid_co
         tmem_ld16(tacc, v);
         tmem_ld16(tacc + 16u, v + 16);
         tmem_wait_ld();
-        const float bj = P.bias[m - 1][j];
+        // t = (v + b) 2 / ln 2 for two rows per packed FMA
+        const float2 k2 = make_float2(kTwoLog2e, kTwoLog2e);
+        const float bk = P.bias[m - 1][j] * kTwoLog2e;
+        const float2 bk2 = make_float2(bk, bk);
         // the 32 values in stages (all exponentials, then all reciprocals), so that the
         // transcendental unit's latency is covered by independent work of this thread
         float a[32];
 #pragma unroll
         for (int h2 = 0; h2 < 2; ++h2) {
-          float e[16];
+          float2 d[8];
 #pragma unroll
-          for (int i = 0; i < 16; ++i) e[i] = ex2_fast(-2.8853900817779268f * fabsf(__uint_as_float(v[16 * h2 + i]) + bj));
+          for (int i = 0; i < 8; ++i) {
+            const float2 t = __ffma2_rn(make_float2(__uint_as_float(v[16 * h2 + 2 * i]), __uint_as_float(v[16 * h2 + 2 * i + 1])),
+                                        k2, bk2);
+            d[i] = __fadd2_rn(make_float2(ex2_fast(t.x), ex2_fast(t.y)), make_float2(1.0f, 1.0f));
+          }
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const float z = __uint_as_float(v[16 * h2 + i]) + bj;
-            a[16 * h2 + i] = copysignf((1.0f - e[i]) * rcp_fast(1.0f + e[i]), z);
+          for (int i = 0; i < 8; ++i) {
+            const float2 r = __ffma2_rn(make_float2(rcp_fast(d[i].x), rcp_fast(d[i].y)), make_float2(-2.0f, -2.0f),
+                                        make_float2(1.0f, 1.0f));
+            a[16 * h2 + 2 * i] = r.x;
+            a[16 * h2 + 2 * i + 1] = r.y;
           }
         }
         if (m < NH) {
