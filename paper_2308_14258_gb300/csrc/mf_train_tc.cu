@@ -161,6 +161,26 @@ __device__ __forceinline__ void tanh_sech2(float z, float& a, float& s) {
   s = 4.0f * e * r * r;
 }
 
+// Packed FP32 arithmetic, two points per instruction (the epilogues that use it are
+// bound by their instruction issue).
+__device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float2 f2(uint32_t x, uint32_t y) { return make_float2(__uint_as_float(x), __uint_as_float(y)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// tanh_sech2 of two pre-activations. The exponential is taken as 4 e = 2^(2 - 2|z|/ln 2),
+// so that s = (4 e) r^2 and 1 +- e = 1 +- (4 e) / 4 cost one packed operation each.
+__device__ __forceinline__ void tanh_sech2_x2(float2 z, float2& a, float2& s) {
+  const float2 e4 = make_float2(ex2_approx(fmaf(-2.8853900817779268f, fabsf(z.x), 2.0f)),
+                                ex2_approx(fmaf(-2.8853900817779268f, fabsf(z.y), 2.0f)));
+  const float2 d = fma2(e4, f2(0.25f), f2(1.0f));
+  const float2 r = make_float2(rcp_approx(d.x), rcp_approx(d.y));
+  const float2 m = mul2(fma2(e4, f2(-0.25f), f2(1.0f)), r);
+  a = make_float2(copysignf(m.x, z.x), copysignf(m.y, z.y));
+  s = mul2(mul2(e4, r), r);
+}
+
 // Columns [16 cq, 16 cq + 16) of this warp's 32 TMEM lanes <- K elements [32 cq, 32 cq + 32)
 // of rows 32 q .. 32 q + 31 of a 128 x 128 BF16 image in the K-major 128-byte-swizzled
 // layout (global memory): the A operand of tcgen05.mma held in tensor memory.
@@ -204,21 +224,17 @@ enum { kFInF = 1, kFInE = 6, kFAccF = 11, kFAccE = 13, kFDrain = 15 };
 __device__ __forceinline__ void fwd_taylor8(const uint32_t (&v)[4][8], float bj, uint32_t stage, int j, int c0) {
   uint32_t w[4][4];
 #pragma unroll
-  for (int i = 0; i < 8; i += 2) {
-    float o[4][2];
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const float z = __uint_as_float(v[0][i + u]) + bj;
-      const float zx = __uint_as_float(v[1][i + u]), zy = __uint_as_float(v[2][i + u]), zl = __uint_as_float(v[3][i + u]);
-      float a, sd;
-      tanh_sech2(z, a, sd);
-      o[0][u] = a;
-      o[1][u] = sd * zx;
-      o[2][u] = sd * zy;
-      o[3][u] = fmaf(-2.0f * a * sd, zx * zx + zy * zy, sd * zl);
-    }
-#pragma unroll
-    for (int ch = 0; ch < 4; ++ch) w[ch][i >> 1] = pack2(o[ch][0], o[ch][1]);
+  for (int i = 0; i < 8; i += 2) {  // points i and i + 1
+    const float2 z = add2(f2(v[0][i], v[0][i + 1]), f2(bj));
+    const float2 zx = f2(v[1][i], v[1][i + 1]), zy = f2(v[2][i], v[2][i + 1]), zl = f2(v[3][i], v[3][i + 1]);
+    float2 a, sd;
+    tanh_sech2_x2(z, a, sd);
+    const float2 o1 = mul2(sd, zx), o2 = mul2(sd, zy);
+    const float2 o3 = fma2(mul2(mul2(a, f2(-2.0f)), sd), fma2(zx, zx, mul2(zy, zy)), mul2(sd, zl));
+    w[0][i >> 1] = pack2(a.x, a.y);
+    w[1][i >> 1] = pack2(o1.x, o1.y);
+    w[2][i >> 1] = pack2(o2.x, o2.y);
+    w[3][i >> 1] = pack2(o3.x, o3.y);
   }
   // channel ch of points 8 c0 .. 8 c0 + 7: chunk 4 ch + c0
 #pragma unroll
@@ -1084,39 +1100,76 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
         if (ok) ok = wait_gz_empty(it);
         if (ok) {
           uint32_t w[4][4];
+          if constexpr (kTop || kFirst) {
+            // the top and layer 1 are bound by their epilogues' instruction issue: two
+            // points per packed instruction
 #pragma unroll
-          for (int i = 0; i < 8; i += 2) {
-            float o[4][2];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-              const int k = i + u;
-              float a, sd;
-              if (top) {
-                a = ta[k];
-                sd = ts[k];
+            for (int i = 0; i < 8; i += 2) {  // points i and i + 1
+              float2 a, sd, ga3;
+              [[maybe_unused]] float2 ga0, ga1, ga2;  // zero at the top
+              if constexpr (kTop) {
+                a = make_float2(ta[i], ta[i + 1]);
+                sd = make_float2(ts[i], ts[i + 1]);
+                ga3 = make_float2(gu[i], gu[i + 1]);  // the top's gradient reaches Delta a only
               } else {
-                tanh_sech2(__uint_as_float(v[0][k]) + bj, a, sd);
+                tanh_sech2_x2(add2(f2(v[0][i], v[0][i + 1]), f2(bj)), a, sd);
+                ga0 = make_float2(bf16_word(gin[0], i), bf16_word(gin[0], i + 1));
+                ga1 = make_float2(bf16_word(gin[1], i), bf16_word(gin[1], i + 1));
+                ga2 = make_float2(bf16_word(gin[2], i), bf16_word(gin[2], i + 1));
+                ga3 = make_float2(bf16_word(gin[3], i), bf16_word(gin[3], i + 1));
               }
-              const float zx = __uint_as_float(v[1][k]), zy = __uint_as_float(v[2][k]), zl = __uint_as_float(v[3][k]);
-              float ga[4];
-              if (top) {
-                ga[0] = 0.f; ga[1] = 0.f; ga[2] = 0.f; ga[3] = gu[k];
+              const float2 zx = f2(v[1][i], v[1][i + 1]), zy = f2(v[2][i], v[2][i + 1]), zl = f2(v[3][i], v[3][i + 1]);
+              // td = tanh''(z) = -2 a s and tp = tanh'''(z) = s (4 a^2 - 2 s)
+              const float2 td = mul2(mul2(a, f2(-2.0f)), sd);
+              const float2 tp = mul2(sd, fma2(mul2(a, a), f2(4.0f), mul2(sd, f2(-2.0f))));
+              const float2 q2 = fma2(zx, zx, mul2(zy, zy));
+              const float2 lap = fma2(tp, q2, mul2(td, zl));
+              const float2 t2 = mul2(mul2(ga3, td), f2(2.0f));
+              float2 g0, o1, o2;
+              if constexpr (kTop) {
+                g0 = mul2(ga3, lap);
+                o1 = mul2(t2, zx);
+                o2 = mul2(t2, zy);
               } else {
+                g0 = fma2(ga0, sd, fma2(fma2(ga1, zx, mul2(ga2, zy)), td, mul2(ga3, lap)));
+                o1 = fma2(ga1, sd, mul2(t2, zx));
+                o2 = fma2(ga2, sd, mul2(t2, zy));
+              }
+              const float2 o3 = mul2(ga3, sd);
+              gb += g0.x;
+              gb += g0.y;
+              w[0][i >> 1] = pack2(g0.x, g0.y);
+              w[1][i >> 1] = pack2(o1.x, o1.y);
+              w[2][i >> 1] = pack2(o2.x, o2.y);
+              w[3][i >> 1] = pack2(o3.x, o3.y);
+            }
+          } else {
+            // hidden layers are bound by DRAM; the scalar form needs fewer registers
+#pragma unroll
+            for (int i = 0; i < 8; i += 2) {
+              float o[4][2];
+#pragma unroll
+              for (int u = 0; u < 2; ++u) {
+                const int k = i + u;
+                float a, sd;
+                tanh_sech2(__uint_as_float(v[0][k]) + bj, a, sd);
+                const float zx = __uint_as_float(v[1][k]), zy = __uint_as_float(v[2][k]), zl = __uint_as_float(v[3][k]);
+                float ga[4];
 #pragma unroll
                 for (int ch = 0; ch < 4; ++ch) ga[ch] = bf16_word(gin[ch], k);
+                const float td = -2.0f * a * sd;
+                const float tp = -2.0f * sd * sd + 4.0f * a * a * sd;
+                const float q2 = zx * zx + zy * zy;
+                const float g0 = ga[0] * sd + (ga[1] * zx + ga[2] * zy) * td + ga[3] * fmaf(tp, q2, td * zl);
+                o[0][u] = g0;
+                o[1][u] = fmaf(ga[1], sd, 2.0f * ga[3] * td * zx);
+                o[2][u] = fmaf(ga[2], sd, 2.0f * ga[3] * td * zy);
+                o[3][u] = ga[3] * sd;
+                gb += g0;
               }
-              const float td = -2.0f * a * sd;
-              const float tp = -2.0f * sd * sd + 4.0f * a * a * sd;
-              const float q2 = zx * zx + zy * zy;
-              const float g0 = ga[0] * sd + (ga[1] * zx + ga[2] * zy) * td + ga[3] * fmaf(tp, q2, td * zl);
-              o[0][u] = g0;
-              o[1][u] = fmaf(ga[1], sd, 2.0f * ga[3] * td * zx);
-              o[2][u] = fmaf(ga[2], sd, 2.0f * ga[3] * td * zy);
-              o[3][u] = ga[3] * sd;
-              gb += g0;
-            }
 #pragma unroll
-            for (int ch = 0; ch < 4; ++ch) w[ch][i >> 1] = pack2(o[ch][0], o[ch][1]);
+              for (int ch = 0; ch < 4; ++ch) w[ch][i >> 1] = pack2(o[ch][0], o[ch][1]);
+          }
           }
 #pragma unroll
           for (int ch = 0; ch < 4; ++ch)
@@ -1256,25 +1309,38 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
           float xy[16];
 #pragma unroll
           for (int u = 0; u < 16; ++u) xy[u] = xyb[16 * g8 + u];
+          if constexpr (C == 4) {
+            // two points per packed instruction, even and odd points in separate partial
+            // sums (added after the group)
+            float2 s02 = f2(0.f), sx2 = f2(0.f), sy2 = f2(0.f);
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const float x = xy[2 * i], y = xy[2 * i + 1];
-            float a, sd;
-            tanh_sech2(fmaf(w2y, y, fmaf(w2x, x, bk)), a, sd);
-            if constexpr (C == 4) {
-              const float g0 = __uint_as_float(v[0][i]), g1 = __uint_as_float(v[1][i]);
-              const float g2 = __uint_as_float(v[2][i]), g3 = __uint_as_float(v[3][i]);
+            for (int i = 0; i < 8; i += 2) {
+              const float2 x = make_float2(xy[2 * i], xy[2 * i + 2]), y = make_float2(xy[2 * i + 1], xy[2 * i + 3]);
+              float2 a, sd;
+              tanh_sech2_x2(fma2(f2(w2y), y, fma2(f2(w2x), x, f2(bk))), a, sd);
+              const float2 g0 = f2(v[0][i], v[0][i + 1]), g1 = f2(v[1][i], v[1][i + 1]);
+              const float2 g2 = f2(v[2][i], v[2][i + 1]), g3 = f2(v[3][i], v[3][i + 1]);
               // with s = sech^2 z, ds/dz = -2 tanh z s and d(-2 tanh z s)/dz = s (6 tanh^2 z - 2):
               //   g_z = s (g0 - 2 a (g1 w2x + g2 w2y) + g3 |w2|^2 (6 a^2 - 2)),
               //   g_w2x += g_z x + s (g1 - 4 a g3 w2x), g_w2y likewise
-              const float gw = fmaf(g1, w2x, g2 * w2y);
-              const float q = fmaf(lap6, a * a, lapm2);
-              const float gz = sd * fmaf(-2.0f * a, gw, fmaf(g3, q, g0));
-              const float t3 = g3 * a;
-              s0 += gz;
-              sx = fmaf(sd, fmaf(t3, m4w2x, g1), fmaf(gz, x, sx));
-              sy = fmaf(sd, fmaf(t3, m4w2y, g2), fmaf(gz, y, sy));
-            } else {
+              const float2 gw = fma2(g1, f2(w2x), mul2(g2, f2(w2y)));
+              const float2 q = fma2(f2(lap6), mul2(a, a), f2(lapm2));
+              const float2 gz = mul2(sd, fma2(mul2(a, f2(-2.0f)), gw, fma2(g3, q, g0)));
+              const float2 t3 = mul2(g3, a);
+              s02 = add2(s02, gz);
+              sx2 = fma2(sd, fma2(t3, f2(m4w2x), g1), fma2(gz, x, sx2));
+              sy2 = fma2(sd, fma2(t3, f2(m4w2y), g2), fma2(gz, y, sy2));
+            }
+            s0 += s02.x + s02.y;
+            sx += sx2.x + sx2.y;
+            sy += sy2.x + sy2.y;
+          }
+          if constexpr (C == 1) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const float x = xy[2 * i], y = xy[2 * i + 1];
+              float a, sd;
+              tanh_sech2(fmaf(w2y, y, fmaf(w2x, x, bk)), a, sd);
               const float gz = __uint_as_float(v[0][8 * g8 + i]) * sd;
               s0 += gz;
               sx = fmaf(gz, x, sx);
