@@ -128,3 +128,32 @@ def test_out_of_f16_range_weights_fall_back(m):
     g.upload(u0)
     g.sweep(net, 1, "M", "fp32_simt")
     assert np.array_equal(a, g.download())
+
+
+def test_fp32_tensor_path_saturated_units(m):
+    """Pre-activations of +-60 in every layer (biases), where e = exp(2 z) of the kernel's
+    tanh overflows to infinity or flushes to zero: those units must give exactly +-1 and
+    the sweep must still match the oracle and the SIMT kernel."""
+    H, depth = 128, 4
+    w, bc, u0 = case(2, 2, depth, 95)
+    o = H * 130
+    w[o:o + 16] = 60.0            # first layer: b0
+    w[o + 16:o + 32] = -60.0
+    o += H
+    for _ in range(depth - 1):    # hidden layers: biases after W_l
+        b = o + H * H
+        w[b:b + 32] = 60.0
+        w[b + 32:b + 64] = -60.0
+        o = b + H
+    net = m.SDNet(w, H, depth)
+    solver = orc.Solver(orc.unpack_sdnet(w, H, depth))
+    g = m.Grid(2, 2, bc)
+    g.upload(u0)
+    g.sweep(net, 1, "M", "fp32")
+    got = g.download()
+    assert np.isfinite(got).all()
+    ref = orc.sweep_multiplicative(u0.astype(np.float64), 2, 2, solver)
+    assert rel(got, ref) <= TOL
+    g.upload(u0)
+    g.sweep(net, 1, "M", "fp32_simt")
+    assert rel(got, g.download().astype(np.float64)) <= 3e-6
