@@ -1352,12 +1352,14 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
       if constexpr (C == 4) {
         // the tile's 32 points are one group: the four point quarters are added through
         // shared memory (the idle staging tile), alternating halves so that one barrier
-        // per tile suffices
+        // per tile suffices. Only the four warps of this lane quadrant (features
+        // 32 q .. 32 q + 31, one warp per point quarter) touch these entries, so the
+        // barrier is theirs alone (ids 7 + q).
         float* r2 = reinterpret_cast<float*>(gen + (sOut - base)) + (it & 1) * (4 * 3 * kW);
         r2[(pq * 3 + 0) * kW + j] = s0;
         r2[(pq * 3 + 1) * kW + j] = sx;
         r2[(pq * 3 + 2) * kW + j] = sy;
-        named_barrier_sync(1, kEpiB * 32);
+        named_barrier_sync(7 + q, 128);
         if (pq == 0 && ok) {
           float* o = T.part32 + (size_t)tl * 3 * kW;
 #pragma unroll
