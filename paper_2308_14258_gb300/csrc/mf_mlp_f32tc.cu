@@ -17,8 +17,10 @@
 // new activations are contiguous along the rows of the next layer's B operand (MN-major,
 // 128-byte swizzle: feature j owns 128 bytes of 64 rows, 16-byte chunk c at c ^ (j mod 8),
 // 8-feature groups 1 KB apart), written with 16-byte stores.
-// tanh(z) = sign(z) (1 - e) / (1 + e) with e = exp(-2|z|) (hardware base-2 exponential
-// and reciprocal): absolute error about 1e-7, enough for FP32 accuracy of what follows.
+// tanh(z) = 1 - 2 / (1 + e) with e = exp(2 z) (hardware base-2 exponential and
+// reciprocal; e overflows to infinity or flushes to zero at the ends): absolute error
+// about 1e-7, enough for FP32 accuracy of what follows. The epilogue arithmetic uses
+// the packed FP32 operations, two rows per instruction.
 // The output layer u = w_out . h + b_out is a sum over features, i.e. over the lanes of
 // four warps: each warp reduces its 32 features x 32 rows by a shuffle reduce-scatter
 // (lane l ends with row l's sum), and the four quadrant sums are added in a fixed order.
