@@ -49,8 +49,9 @@ typedef int mf_status;
 #define MF_ERR_TIMEOUT (-5)      /* a bounded wait inside a kernel gave up; results invalid */
 #define MF_ERR_UNSUPPORTED (-6)  /* valid request this build or device cannot serve */
 
-#define MF_PREC_FP32 0  /* FP32 accuracy: width-128 tanh SDNets on the tensor cores, each hidden product split
-                           in three F16 products with FP32 accumulation; other SDNets as MF_PREC_FP32_SIMT */
+#define MF_PREC_FP32 0  /* FP32 accuracy: width-128 SDNets (tanh or GELU) on the tensor cores, each hidden
+                           product split in three F16 products with FP32 accumulation; other SDNets as
+                           MF_PREC_FP32_SIMT */
 #define MF_PREC_BF16 1  /* BF16 weights/activations on tcgen05 tensor cores, FP32 accumulate */
 #define MF_PREC_MIXED 2 /* BF16 sweeps until delta < eps_coarse or stalls, then FP32 refinement */
 #define MF_PREC_FP32_SIMT 3 /* FP32 weights and activations on the CUDA cores (FMA), accurate tanh */

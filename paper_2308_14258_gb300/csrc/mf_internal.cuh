@@ -195,7 +195,8 @@ bool bf16_supported(const DevNet& net);
 bool f16_supported(const DevNet& net);
 
 // K3t: the FP32 SDNet on the tensor cores, each hidden product split in three F16
-// products with FP32 accumulation (width 128, tanh); same contract as launch_mlp_fp32.
+// products with FP32 accumulation (width 128, tanh or GELU); same contract as
+// launch_mlp_fp32.
 cudaError_t launch_mlp_f32tc(const float* B, const ColourGeom& g, const DevNet& net, float* u, int additive,
                              int* dev_status, cudaStream_t st);
 bool f32tc_supported(const DevNet& net);

@@ -102,6 +102,11 @@ __device__ __forceinline__ float tanh_acc(float z) {
   const float e = ex2_fast(kTwoLog2e * z);
   return fmaf(-2.0f, rcp_fast(1.0f + e), 1.0f);
 }
+template <int ACT>
+__device__ __forceinline__ float first_act(float z) {
+  if constexpr (ACT == kActGelu) return act_exact<kActGelu>(z);
+  else return tanh_acc(z);
+}
 // (hi, lo) F16 pairs of two FP32 values: hi = f16(a), lo = f16(a - hi), packed with the
 // first value in the low half
 __device__ __forceinline__ void split2(float a0, float a1, uint32_t& hi, uint32_t& lo) {
@@ -144,7 +149,8 @@ __device__ __forceinline__ int t_tile(int round, int slot) {
   return (round * (int)gridDim.x + (int)blockIdx.x) * kTSlots + slot;
 }
 
-template <int NH>
+// ACT: kActTanh, or kActGelu (the exact x Phi(x) with CUDA's erff, as the SIMT kernel).
+template <int NH, int ACT>
 __global__ void __launch_bounds__(kThreadsT, 1) mlp_f32tc_kernel(const __grid_constant__ F32tcParams P) {
   constexpr int kSL = smem_layers(NH);
   constexpr int kTL = NH < kTmemLayers ? NH : kTmemLayers;
@@ -319,7 +325,7 @@ __global__ void __launch_bounds__(kThreadsT, 1) mlp_f32tc_kernel(const __grid_co
             const int px = pt < kNi ? pt : kNi / 2;
             const int py = pt < kNi ? kNi / 2 : (qq < kNi / 2 ? qq : qq + 1);
             const float x = (float)(px + 1) * (1.0f / kPts), y = (float)(py + 1) * (1.0f / kPts);
-            a[i] = tanh_acc(fmaf(w2y, y, fmaf(w2x, x, b_cur)));
+            a[i] = first_act<ACT>(fmaf(w2y, y, fmaf(w2x, x, b_cur)));
             if (++pt == rps) {
               pt = 0;
               ++sc;
@@ -332,7 +338,7 @@ __global__ void __launch_bounds__(kThreadsT, 1) mlp_f32tc_kernel(const __grid_co
           float x = (float)(px + 1) * (1.0f / kPts), y = (float)(pt / kNi + 1) * (1.0f / kPts);
 #pragma unroll
           for (int i = 0; i < 32; ++i) {
-            a[i] = tanh_acc(fmaf(w2y, y, fmaf(w2x, x, b_cur)));
+            a[i] = first_act<ACT>(fmaf(w2y, y, fmaf(w2x, x, b_cur)));
             x += 1.0f / kPts;
             if (++px == kNi) {
               px = 0;
@@ -368,13 +374,17 @@ __global__ void __launch_bounds__(kThreadsT, 1) mlp_f32tc_kernel(const __grid_co
         tmem_ld16(tacc, v);
         tmem_ld16(tacc + 16u, v + 16);
         tmem_wait_ld();
+        float a[32];
+        if constexpr (ACT == kActGelu) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) a[i] = act_exact<kActGelu>(__uint_as_float(v[i]) + P.bias[m - 1][j]);
+        } else {
         // t = (v + b) 2 / ln 2 for two rows per packed FMA
         const float2 k2 = make_float2(kTwoLog2e, kTwoLog2e);
         const float bk = P.bias[m - 1][j] * kTwoLog2e;
         const float2 bk2 = make_float2(bk, bk);
         // the 32 values in stages (all exponentials, then all reciprocals), so that the
         // transcendental unit's latency is covered by independent work of this thread
-        float a[32];
 #pragma unroll
         for (int h2 = 0; h2 < 2; ++h2) {
           float2 d[8];
@@ -391,6 +401,7 @@ __global__ void __launch_bounds__(kThreadsT, 1) mlp_f32tc_kernel(const __grid_co
             a[16 * h2 + 2 * i] = r.x;
             a[16 * h2 + 2 * i + 1] = r.y;
           }
+        }
         }
         if (m < NH) {
           give_turn();
@@ -442,18 +453,18 @@ __global__ void __launch_bounds__(kThreadsT, 1) mlp_f32tc_kernel(const __grid_co
   }
 }
 
-template <int NH>
+template <int NH, int ACT>
 cudaError_t launch_nh(const F32tcParams& p, cudaStream_t st) {
   static PerDevice pd;
   int grid_cap = 0;
   cudaError_t e = per_device(pd, [](int dev, int* cap, size_t*) {
-    cudaError_t e1 = cudaFuncSetAttribute(mlp_f32tc_kernel<NH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e1 = cudaFuncSetAttribute(mlp_f32tc_kernel<NH, ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)f32tc_smem(NH));
     if (e1 != cudaSuccess) return e1;
     int sms = 0, per_sm = 0;
     e1 = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e1 != cudaSuccess) return e1;
-    e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_f32tc_kernel<NH>, kThreadsT, f32tc_smem(NH));
+    e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_f32tc_kernel<NH, ACT>, kThreadsT, f32tc_smem(NH));
     if (e1 != cudaSuccess) return e1;
     // a CTA takes all 512 TMEM columns: one resident CTA per SM
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
@@ -474,11 +485,11 @@ cudaError_t launch_nh(const F32tcParams& p, cudaStream_t st) {
     smem = (size_t)smem_sm / 2 + 1024;
     static PerDevice pd2;
     e = per_device(pd2, [smem](int, int*, size_t*) {
-      return cudaFuncSetAttribute(mlp_f32tc_kernel<NH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      return cudaFuncSetAttribute(mlp_f32tc_kernel<NH, ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     });
     if (e != cudaSuccess) return e;
   }
-  mlp_f32tc_kernel<NH><<<grid, kThreadsT, smem, st>>>(p);
+  mlp_f32tc_kernel<NH, ACT><<<grid, kThreadsT, smem, st>>>(p);
   return cudaGetLastError();
 }
 
@@ -502,8 +513,7 @@ __global__ void pack_f16_split_kernel(const float* __restrict__ WhT, int n_hidde
 }  // namespace
 
 bool f32tc_supported(const DevNet& net) {
-  return net.width == kH && net.act == kActTanh && net.n_hidden >= 1 && net.n_hidden <= kMaxHid &&
-         net.wimg_f16 != nullptr;
+  return net.width == kH && net.n_hidden >= 1 && net.n_hidden <= kMaxHid && net.wimg_f16 != nullptr;
 }
 
 size_t f32tc_image_bytes(int n_hidden) { return (size_t)n_hidden * 2 * kImg; }
@@ -535,12 +545,21 @@ cudaError_t launch_mlp_f32tc(const float* B, const ColourGeom& g, const DevNet& 
     p.w2[j][0] = net.h_W2[2 * j];
     p.w2[j][1] = net.h_W2[2 * j + 1];
   }
+  if (net.act == kActGelu) {
+    switch (net.n_hidden) {
+      case 1: return launch_nh<1, kActGelu>(p, st);
+      case 2: return launch_nh<2, kActGelu>(p, st);
+      case 3: return launch_nh<3, kActGelu>(p, st);
+      case 4: return launch_nh<4, kActGelu>(p, st);
+      default: return launch_nh<5, kActGelu>(p, st);
+    }
+  }
   switch (net.n_hidden) {
-    case 1: return launch_nh<1>(p, st);
-    case 2: return launch_nh<2>(p, st);
-    case 3: return launch_nh<3>(p, st);
-    case 4: return launch_nh<4>(p, st);
-    default: return launch_nh<5>(p, st);
+    case 1: return launch_nh<1, kActTanh>(p, st);
+    case 2: return launch_nh<2, kActTanh>(p, st);
+    case 3: return launch_nh<3, kActTanh>(p, st);
+    case 4: return launch_nh<4, kActTanh>(p, st);
+    default: return launch_nh<5, kActTanh>(p, st);
   }
 }
 

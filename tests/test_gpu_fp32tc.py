@@ -1,7 +1,7 @@
-"""The FP32 path on the tensor cores (MF_PREC_FP32 for width-128 tanh SDNets: every
-hidden product split in three F16 products with FP32 accumulation) against the FP64
-oracle at the FP32 tolerance, and against the FP32 SIMT kernel (MF_PREC_FP32_SIMT) on
-the same state. Shapes cover every split of the hidden weights between tensor memory
+"""The FP32 path on the tensor cores (MF_PREC_FP32 for width-128 SDNets, tanh here and
+GELU in the variant tests: every hidden product split in three F16 products with FP32
+accumulation) against the FP64 oracle at the FP32 tolerance, and against the FP32 SIMT
+kernel (MF_PREC_FP32_SIMT) on the same state. Shapes cover every split of the hidden weights between tensor memory
 (layers 1-3) and shared memory (layers 4-5), ragged last tiles (rows not a multiple of
 64), the additive schedule, centre-line queries and batches."""
 import numpy as np

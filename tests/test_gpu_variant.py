@@ -155,3 +155,22 @@ def test_invalid_variant_options(m):
     import ctypes as C
     h = C.c_void_p()
     assert m.load().mf_load_sdnet_ex(m.default_context()._h, C.byref(d), w.ctypes.data, C.byref(h)) == m.MF_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("v", [VARIANTS[0], VARIANTS[3]])
+def test_fp32_tensor_path_matches_simt(m, v):
+    """Width-128 GELU SDNets take the FP32 tensor-core kernel (three-term F16 products,
+    the exact GELU with erff in its epilogue); it matches the oracle and agrees with the
+    CUDA-core FP32 kernel far inside the FP32 tolerance."""
+    lx, ly = 2, 2
+    net, solver, bc, u0 = setup(m, lx, ly, v, 4)
+    g = m.Grid(lx, ly, bc)
+    g.upload(u0)
+    g.sweep(net, 1, "M", "fp32")
+    a = g.download()
+    g.upload(u0)
+    g.sweep(net, 1, "M", "fp32_simt")
+    b = g.download()
+    ref = orc.sweep_multiplicative(u0.astype(np.float64), lx, ly, solver)
+    assert rel_err(a, ref) <= TOL["fp32"]
+    assert rel_err(a, b.astype(np.float64)) <= 3e-6
