@@ -1106,7 +1106,7 @@ __global__ void __launch_bounds__(kThreadsB, 1) tc_bwd_kernel(const __grid_const
 #pragma unroll
             for (int i = 0; i < 8; i += 2) {  // points i and i + 1
               float2 a, sd, ga3;
-              [[maybe_unused]] float2 ga0, ga1, ga2;  // zero at the top
+              [[maybe_unused]] float2 ga0, ga1, ga2;  // not used at the top
               if constexpr (kTop) {
                 a = make_float2(ta[i], ta[i + 1]);
                 sd = make_float2(ts[i], ts[i + 1]);
